@@ -1,0 +1,765 @@
+/*
+ * FP64 CPU oracle for Maximal Center Gauge (MCG) fixing with stout and
+ * over-improved stout preconditioning (O Cais, Kamleh, Langfeld, Lasscock,
+ * Leinweber, Moran, Sternbeck, von Smekal 2008).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg load this library.  It shares no code, header
+ * or table with the CUDA path: it is a plain, slow, sequential-per-site
+ * restatement of what the method computes, written for reading against the
+ * paper.  Every loop over sites may run under OpenMP; results do not depend on
+ * the thread count (same-parity site updates touch disjoint links, reductions
+ * sum fixed chunks in index order).
+ *
+ * Layout (canonical host layout): site index i = x + Nx*(y + Ny*(z + Nz*t)),
+ *   U[(i*4 + mu)*9 + 3*row + col]   complex double, mu = 0..3 is x,y,z,t
+ *   G[i*9 + 3*row + col]            complex double (gauge transform Omega(x))
+ *   m[i*4 + mu]                     int8 center sector in {-1, 0, +1}
+ *
+ * Readings where the paper is silent (each stated where it is used):
+ *   - the site update maximises the local functional exactly over the three
+ *     SU(2) subgroups (0,1), (0,2), (1,2) in that order, one hit each,
+ *     even sites then odd sites;
+ *   - the stop rule is V_U(k) - V_U(k-1) < tol on the normalised functional;
+ *   - links and Omega are re-unitarised every reunit_every sweeps;
+ *   - stout smearing is isotropic in 4D and updates all links at once.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+#define NCHUNK 256 /* fixed reduction chunking: result independent of threads */
+
+/* ------------------------------------------------------------------ */
+/* lattice geometry                                                     */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int n[4];
+    long vol;
+} geom;
+
+static geom make_geom(const int* dims) {
+    geom g;
+    for (int d = 0; d < 4; ++d) g.n[d] = dims[d];
+    g.vol = (long)dims[0] * dims[1] * dims[2] * dims[3];
+    return g;
+}
+
+static void coords_of(const geom* g, long i, int* c) {
+    for (int d = 0; d < 4; ++d) {
+        c[d] = (int)(i % g->n[d]);
+        i /= g->n[d];
+    }
+}
+
+static long index_of(const geom* g, const int* c) {
+    return c[0] + (long)g->n[0] * (c[1] + (long)g->n[1] * (c[2] + (long)g->n[2] * c[3]));
+}
+
+/* site i displaced by `step` lattice units along direction mu, periodic */
+static long shift(const geom* g, long i, int mu, int step) {
+    int c[4];
+    coords_of(g, i, c);
+    c[mu] = ((c[mu] + step) % g->n[mu] + g->n[mu]) % g->n[mu];
+    return index_of(g, c);
+}
+
+static int parity_of(const geom* g, long i) {
+    int c[4];
+    coords_of(g, i, c);
+    return (c[0] + c[1] + c[2] + c[3]) & 1;
+}
+
+/* ------------------------------------------------------------------ */
+/* 3x3 complex matrices                                                 */
+/* ------------------------------------------------------------------ */
+static void m_mul(cplx* r, const cplx* a, const cplx* b) { /* r = a b */
+    cplx t[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            cplx s = 0;
+            for (int k = 0; k < 3; ++k) s += a[3 * i + k] * b[3 * k + j];
+            t[3 * i + j] = s;
+        }
+    memcpy(r, t, sizeof t);
+}
+
+static void m_mul_nd(cplx* r, const cplx* a, const cplx* b) { /* r = a b^dag */
+    cplx t[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            cplx s = 0;
+            for (int k = 0; k < 3; ++k) s += a[3 * i + k] * conj(b[3 * j + k]);
+            t[3 * i + j] = s;
+        }
+    memcpy(r, t, sizeof t);
+}
+
+static void m_mul_dn(cplx* r, const cplx* a, const cplx* b) { /* r = a^dag b */
+    cplx t[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            cplx s = 0;
+            for (int k = 0; k < 3; ++k) s += conj(a[3 * k + i]) * b[3 * k + j];
+            t[3 * i + j] = s;
+        }
+    memcpy(r, t, sizeof t);
+}
+
+static void m_dag(cplx* r, const cplx* a) {
+    cplx t[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) t[3 * i + j] = conj(a[3 * j + i]);
+    memcpy(r, t, sizeof t);
+}
+
+static cplx m_trace(const cplx* a) { return (a[0] + a[4]) + a[8]; }
+
+static void m_set_identity(cplx* a) {
+    for (int k = 0; k < 9; ++k) a[k] = 0;
+    a[0] = a[4] = a[8] = 1;
+}
+
+static double m_fnorm(const cplx* a) {
+    double s = 0;
+    for (int k = 0; k < 9; ++k) s += creal(a[k] * conj(a[k]));
+    return sqrt(s);
+}
+
+/* Project a near-SU(3) matrix back onto SU(3): normalise row 0; remove its
+ * component from row 1 and normalise; row 2 = conj(row0 x row1). */
+static void m_reunitarise(cplx* a) {
+    cplx* r0 = a;
+    cplx* r1 = a + 3;
+    cplx* r2 = a + 6;
+    double n0 = sqrt(creal(r0[0] * conj(r0[0]) + r0[1] * conj(r0[1]) + r0[2] * conj(r0[2])));
+    for (int k = 0; k < 3; ++k) r0[k] /= n0;
+    cplx p = conj(r0[0]) * r1[0] + conj(r0[1]) * r1[1] + conj(r0[2]) * r1[2];
+    for (int k = 0; k < 3; ++k) r1[k] -= p * r0[k];
+    double n1 = sqrt(creal(r1[0] * conj(r1[0]) + r1[1] * conj(r1[1]) + r1[2] * conj(r1[2])));
+    for (int k = 0; k < 3; ++k) r1[k] /= n1;
+    r2[0] = conj(r0[1] * r1[2] - r0[2] * r1[1]);
+    r2[1] = conj(r0[2] * r1[0] - r0[0] * r1[2]);
+    r2[2] = conj(r0[0] * r1[1] - r0[1] * r1[0]);
+}
+
+static inline cplx* link(cplx* U, long i, int mu) { return U + (i * 4 + mu) * 9; }
+static inline const cplx* clink(const cplx* U, long i, int mu) { return U + (i * 4 + mu) * 9; }
+
+/* ------------------------------------------------------------------ */
+/* Observables                                                          */
+/* ------------------------------------------------------------------ */
+
+/* Gauge functional R = sum_{x,mu} |tr U_mu(x)|^2; V_U = R / (9 * 4V)
+ * (Sec. II.A, the MCG condition V_U[Omega]). */
+double orc_functional_R(const int* dims, const cplx* U) {
+    geom g = make_geom(dims);
+    long nl = g.vol * 4;
+    double part[NCHUNK];
+#pragma omp parallel for schedule(static)
+    for (int ch = 0; ch < NCHUNK; ++ch) {
+        long lo = nl * ch / NCHUNK, hi = nl * (ch + 1) / NCHUNK;
+        double s = 0;
+        for (long l = lo; l < hi; ++l) {
+            cplx t = m_trace(U + l * 9);
+            s += creal(t) * creal(t) + cimag(t) * cimag(t);
+        }
+        part[ch] = s;
+    }
+    double r = 0;
+    for (int ch = 0; ch < NCHUNK; ++ch) r += part[ch];
+    return r;
+}
+
+/* Mean plaquette <(1/3) Re tr U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag>
+ * over the 6V plaquettes; gauge invariant (Sec. III.A). */
+double orc_plaquette(const int* dims, const cplx* U) {
+    geom g = make_geom(dims);
+    double part[NCHUNK];
+#pragma omp parallel for schedule(static)
+    for (int ch = 0; ch < NCHUNK; ++ch) {
+        long lo = g.vol * ch / NCHUNK, hi = g.vol * (ch + 1) / NCHUNK;
+        double s = 0;
+        for (long i = lo; i < hi; ++i)
+            for (int mu = 0; mu < 4; ++mu)
+                for (int nu = mu + 1; nu < 4; ++nu) {
+                    cplx a[9], b[9];
+                    m_mul(a, clink(U, i, mu), clink(U, shift(&g, i, mu, 1), nu));
+                    m_mul_nd(b, a, clink(U, shift(&g, i, nu, 1), mu));
+                    m_mul_nd(a, b, clink(U, i, nu));
+                    s += creal(m_trace(a)) / 3.0;
+                }
+        part[ch] = s;
+    }
+    double r = 0;
+    for (int ch = 0; ch < NCHUNK; ++ch) r += part[ch];
+    return r / (6.0 * (double)g.vol);
+}
+
+/* U_mu(x) <- Omega(x) U_mu(x) Omega(x+mu)^dag, in place (Sec. II.A/II.B:
+ * the gauge-transformed field U^Omega). */
+void orc_apply_gauge(const int* dims, cplx* U, const cplx* G) {
+    geom g = make_geom(dims);
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < g.vol; ++i)
+        for (int mu = 0; mu < 4; ++mu) {
+            cplx t[9];
+            m_mul(t, G + i * 9, link(U, i, mu));
+            m_mul_nd(link(U, i, mu), t, G + shift(&g, i, mu, 1) * 9);
+        }
+}
+
+void orc_reunitarise_field(long nmat, cplx* M) {
+#pragma omp parallel for schedule(static)
+    for (long k = 0; k < nmat; ++k) m_reunitarise(M + k * 9);
+}
+
+/* Omega_out(x) = Omega_b(x) Omega_a(x), composition of two transforms. */
+void orc_compose_gauge(long vol, const cplx* Gb, const cplx* Ga, cplx* Gout) {
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < vol; ++i) m_mul(Gout + i * 9, Gb + i * 9, Ga + i * 9);
+}
+
+/* ------------------------------------------------------------------ */
+/* Local SU(2)-subgroup maximisation                                    */
+/* ------------------------------------------------------------------ */
+
+/* Cyclic Jacobi diagonalisation of a symmetric 4x4 matrix: A = V diag(al) V^T,
+ * columns of V are eigenvectors.  Runs until the off-diagonal norm is below
+ * 1e-15 of the Frobenius norm (or 60 sweeps). */
+static void jacobi4(const double* Ain, double* V, double* al) {
+    double A[4][4];
+    double fro = 0;
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            A[i][j] = 0.5 * (Ain[4 * i + j] + Ain[4 * j + i]);
+            fro += A[i][j] * A[i][j];
+            V[4 * i + j] = (i == j) ? 1.0 : 0.0;
+        }
+    fro = sqrt(fro);
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0;
+        for (int p = 0; p < 4; ++p)
+            for (int q = p + 1; q < 4; ++q) off += 2 * A[p][q] * A[p][q];
+        if (sqrt(off) <= 1e-15 * fro || off == 0) break;
+        for (int p = 0; p < 4; ++p)
+            for (int q = p + 1; q < 4; ++q) {
+                if (A[p][q] == 0) continue;
+                /* rotation angle that zeroes A[p][q] */
+                double theta = (A[q][q] - A[p][p]) / (2 * A[p][q]);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1));
+                double c = 1 / sqrt(t * t + 1), s = t * c;
+                for (int k = 0; k < 4; ++k) { /* A <- A J */
+                    double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = c * akp - s * akq;
+                    A[k][q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < 4; ++k) { /* A <- J^T A */
+                    double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = c * apk - s * aqk;
+                    A[q][k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < 4; ++k) { /* V <- V J */
+                    double vkp = V[4 * k + p], vkq = V[4 * k + q];
+                    V[4 * k + p] = c * vkp - s * vkq;
+                    V[4 * k + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    for (int i = 0; i < 4; ++i) al[i] = A[i][i];
+}
+
+/*
+ * Maximise F(a) = a^T A a + 2 b^T a over the unit sphere |a| = 1 in R^4
+ * (A symmetric 4x4 row-major, b in R^4).  The global maximiser satisfies
+ * (mu I - A) a = b with mu >= alpha_max (the trust-region optimality
+ * condition).  Easy case: mu is the root right of alpha_max of
+ * ||a(mu)|| = 1, a(mu) = sum_i beta_i / (mu - alpha_i) v_i, beta_i = v_i . b,
+ * found by Newton on 1/||a(mu)|| - 1 from the left end of the bracket
+ * [alpha_max + |beta_top|, alpha_max + ||b||] (beta_top: the component of b
+ * in the top eigenspace) with bisection as a safeguard.
+ * Hard case (b has no component along the top eigenspace and the rest of the
+ * solution has norm < 1): mu = alpha_max and a = partial + t v_max with t > 0
+ * after fixing the sign of v_max so that its largest-magnitude component is
+ * positive.  The paper is silent on this degenerate case; several maximisers
+ * are equally correct there.
+ * Returns 0 (easy case) or 1 (hard case); a is normalised to |a| = 1.
+ */
+int orc_trs_solve(const double* A, const double* b, double* a) {
+    double V[16], al[4];
+    jacobi4(A, V, al);
+    double scale = 0;
+    for (int i = 0; i < 4; ++i) scale = fmax(scale, fabs(al[i]));
+    double bn = sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2] + b[3] * b[3]);
+    scale = fmax(scale, bn);
+    if (scale == 0) { /* F constant on the sphere: keep the identity */
+        a[0] = 1; a[1] = a[2] = a[3] = 0;
+        return 1;
+    }
+    int imax = 0;
+    for (int i = 1; i < 4; ++i)
+        if (al[i] > al[imax]) imax = i;
+    double amax = al[imax];
+    double beta[4];
+    for (int i = 0; i < 4; ++i)
+        beta[i] = V[0 * 4 + i] * b[0] + V[1 * 4 + i] * b[1] + V[2 * 4 + i] * b[2] + V[3 * 4 + i] * b[3];
+
+    /* top eigenspace: eigenvalues within 1e-13*scale of the largest */
+    int top[4];
+    double btop = 0;
+    for (int i = 0; i < 4; ++i) {
+        top[i] = (amax - al[i]) <= 1e-13 * scale;
+        if (top[i]) btop += beta[i] * beta[i];
+    }
+    btop = sqrt(btop);
+    if (btop <= 1e-14 * scale) {
+        double pn2 = 0, coef[4];
+        for (int i = 0; i < 4; ++i) {
+            coef[i] = top[i] ? 0.0 : beta[i] / (amax - al[i]);
+            pn2 += coef[i] * coef[i];
+        }
+        if (pn2 < 1.0) {
+            double vm[4];
+            for (int k = 0; k < 4; ++k) vm[k] = V[4 * k + imax];
+            int kbig = 0;
+            for (int k = 1; k < 4; ++k)
+                if (fabs(vm[k]) > fabs(vm[kbig])) kbig = k;
+            double sgn = vm[kbig] >= 0 ? 1.0 : -1.0;
+            double t = sqrt(1.0 - pn2);
+            for (int k = 0; k < 4; ++k) {
+                double s = 0;
+                for (int i = 0; i < 4; ++i) s += V[4 * k + i] * coef[i];
+                a[k] = s + t * sgn * vm[k];
+            }
+            double an = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
+            for (int k = 0; k < 4; ++k) a[k] /= an;
+            return 1;
+        }
+    }
+
+    /* bracket: ||a(mu)|| >= btop / (mu - alpha_max), so mu = alpha_max + btop
+     * lies left of the root; ||a(mu)|| <= ||b|| / (mu - alpha_max), so
+     * mu = alpha_max + ||b|| lies right of it */
+    double lo = amax + btop, hi = amax + bn;
+    double mu = lo;
+    for (int it = 0; it < 200; ++it) {
+        double s2 = 0, s3 = 0;
+        for (int i = 0; i < 4; ++i) {
+            double d = mu - al[i];
+            double q = beta[i] * beta[i] / (d * d);
+            s2 += q;
+            s3 += q / d;
+        }
+        double n = sqrt(s2);
+        if (n >= 1.0) lo = fmax(lo, mu);
+        else hi = fmin(hi, mu);
+        double next = mu + (n - 1.0) * s2 / s3; /* Newton on 1/n - 1 */
+        if (!(next > lo && next < hi)) next = 0.5 * (lo + hi);
+        if (next == mu || fabs(next - mu) <= 1e-16 * fabs(mu)) {
+            mu = next;
+            break;
+        }
+        mu = next;
+        if (hi - lo <= 4e-16 * fabs(mu)) break;
+    }
+    double an2 = 0;
+    for (int k = 0; k < 4; ++k) {
+        double s = 0;
+        for (int i = 0; i < 4; ++i) s += V[4 * k + i] * beta[i] / (mu - al[i]);
+        a[k] = s;
+        an2 += s * s;
+    }
+    double an = sqrt(an2);
+    for (int k = 0; k < 4; ++k) a[k] /= an;
+    return 0;
+}
+
+/* Coefficients of tr(G M) as an affine function of the SU(2) parameter a,
+ * for G the subgroup (p,q) embedding of g = a0 + i a.sigma:
+ *   tr(G M) = M_rr + sum_k w_k a_k,
+ *   w = (m11 + m22, i(m21 + m12), m21 - m12, i(m11 - m22)),
+ * with m the (p,q) block of M.  For a backward link B (which becomes B G^dag)
+ * tr(B G^dag) = tr(G^dag B) takes the same form with a_1..a_3 negated. */
+static void subgroup_coeffs(const cplx* M, int p, int q, int r, int backward, cplx* c, cplx* w) {
+    cplx m11 = M[3 * p + p], m12 = M[3 * p + q], m21 = M[3 * q + p], m22 = M[3 * q + q];
+    *c = M[3 * r + r];
+    w[0] = m11 + m22;
+    w[1] = I * (m21 + m12);
+    w[2] = m21 - m12;
+    w[3] = I * (m11 - m22);
+    if (backward) {
+        w[1] = -w[1];
+        w[2] = -w[2];
+        w[3] = -w[3];
+    }
+}
+
+/* One site update at x: for (p,q) = (0,1), (0,2), (1,2), choose the SU(2)
+ * subgroup element G maximising sum over the 8 links at x of |tr|^2, then
+ * U_mu(x) <- G U_mu(x), U_mu(x-mu) <- U_mu(x-mu) G^dag, Omega(x) <- G Omega(x).
+ * Returns the number of hard-case solves. */
+static int site_update(const geom* g, cplx* U, cplx* Om, long x) {
+    static const int PQ[3][3] = {{0, 1, 2}, {0, 2, 1}, {1, 2, 0}};
+    int hard = 0;
+    cplx* F[4];
+    cplx* B[4];
+    for (int mu = 0; mu < 4; ++mu) {
+        F[mu] = link(U, x, mu);
+        B[mu] = link(U, shift(g, x, mu, -1), mu);
+    }
+    for (int s = 0; s < 3; ++s) {
+        int p = PQ[s][0], q = PQ[s][1], r = PQ[s][2];
+        double A[16] = {0}, b[4] = {0};
+        for (int l = 0; l < 8; ++l) {
+            cplx c, w[4];
+            subgroup_coeffs(l < 4 ? F[l] : B[l - 4], p, q, r, l >= 4, &c, w);
+            for (int k = 0; k < 4; ++k) {
+                b[k] += creal(conj(c) * w[k]);
+                for (int j = 0; j < 4; ++j) A[4 * k + j] += creal(conj(w[k]) * w[j]);
+            }
+        }
+        double a[4];
+        hard += orc_trs_solve(A, b, a);
+        cplx g11 = a[0] + I * a[3], g12 = a[2] + I * a[1];
+        cplx g21 = -a[2] + I * a[1], g22 = a[0] - I * a[3];
+        for (int mu = 0; mu < 4; ++mu) {
+            cplx* f = F[mu];
+            for (int k = 0; k < 3; ++k) { /* rows p, q of G F */
+                cplx xp = f[3 * p + k], xq = f[3 * q + k];
+                f[3 * p + k] = g11 * xp + g12 * xq;
+                f[3 * q + k] = g21 * xp + g22 * xq;
+            }
+            cplx* bb = B[mu];
+            for (int k = 0; k < 3; ++k) { /* columns p, q of B G^dag */
+                cplx xp = bb[3 * k + p], xq = bb[3 * k + q];
+                bb[3 * k + p] = xp * conj(g11) + xq * conj(g12);
+                bb[3 * k + q] = xp * conj(g21) + xq * conj(g22);
+            }
+        }
+        cplx* o = Om + x * 9;
+        for (int k = 0; k < 3; ++k) {
+            cplx xp = o[3 * p + k], xq = o[3 * q + k];
+            o[3 * p + k] = g11 * xp + g12 * xq;
+            o[3 * q + k] = g21 * xp + g22 * xq;
+        }
+    }
+    return hard;
+}
+
+/* Update every site of one parity (0: x+y+z+t even).  Same-parity sites share
+ * no link, so the order within the parity does not matter.  Returns the number
+ * of hard-case local solves. */
+long orc_halfsweep(const int* dims, cplx* U, cplx* Om, int parity) {
+    geom g = make_geom(dims);
+    long hard = 0;
+#pragma omp parallel for schedule(static) reduction(+ : hard)
+    for (long x = 0; x < g.vol; ++x)
+        if (parity_of(&g, x) == parity) hard += site_update(&g, U, Om, x);
+    return hard;
+}
+
+/*
+ * MCG relaxation (Sec. II.A, II.B): full sweeps (even then odd half-sweep)
+ * until V_U(k) - V_U(k-1) < tol or max_sweeps, where V_U = R / (9 * 4V).
+ * Every reunit_every sweeps (if > 0) links and Omega are re-unitarised.
+ * R_hist[0..sweeps] receives R before the first sweep and after each sweep.
+ * Returns 0 if converged, 1 if max_sweeps was reached.
+ */
+int orc_fix(const int* dims, cplx* U, cplx* Om, double tol, int max_sweeps, int reunit_every,
+            double* R_hist, int* sweeps_out, long* hard_out) {
+    geom g = make_geom(dims);
+    double norm = 1.0 / (9.0 * 4.0 * (double)g.vol);
+    double Rprev = orc_functional_R(dims, U);
+    if (R_hist) R_hist[0] = Rprev;
+    long hard = 0;
+    int k;
+    for (k = 1; k <= max_sweeps; ++k) {
+        hard += orc_halfsweep(dims, U, Om, 0);
+        hard += orc_halfsweep(dims, U, Om, 1);
+        if (reunit_every > 0 && k % reunit_every == 0) {
+            orc_reunitarise_field(g.vol * 4, U);
+            orc_reunitarise_field(g.vol, Om);
+        }
+        double R = orc_functional_R(dims, U);
+        if (R_hist) R_hist[k] = R;
+        if ((R - Rprev) * norm < tol) {
+            *sweeps_out = k;
+            if (hard_out) *hard_out = hard;
+            return 0;
+        }
+        Rprev = R;
+    }
+    *sweeps_out = max_sweeps;
+    if (hard_out) *hard_out = hard;
+    return 1;
+}
+
+/* ------------------------------------------------------------------ */
+/* Stout and over-improved stout smearing                               */
+/* ------------------------------------------------------------------ */
+
+/* exp(X) for a 3x3 complex X by Taylor series with scaling and squaring:
+ * X / 2^s has Frobenius norm <= 1/4, the series runs until a term falls below
+ * 1e-18, then the result is squared s times. */
+void orc_expm(const cplx* X, cplx* E) {
+    double nrm = m_fnorm(X);
+    int s = 0;
+    while (nrm > 0.25) {
+        nrm *= 0.5;
+        ++s;
+    }
+    double sc = ldexp(1.0, -s);
+    cplx Y[9], term[9], t2[9];
+    for (int k = 0; k < 9; ++k) Y[k] = X[k] * sc;
+    m_set_identity(E);
+    m_set_identity(term);
+    for (int n = 1; n < 40; ++n) {
+        m_mul(t2, term, Y);
+        for (int k = 0; k < 9; ++k) term[k] = t2[k] / (double)n;
+        for (int k = 0; k < 9; ++k) E[k] += term[k];
+        if (m_fnorm(term) < 1e-18) break;
+    }
+    for (int j = 0; j < s; ++j) m_mul(E, E, E);
+}
+
+/* Staple sum of U_mu(x) with plaquette weight cp and rectangle weight cr:
+ * cp * (2 plaquette staples per nu) + cr * (6 rectangle staples per nu:
+ * two 1x2 with the link on the short side, four 2x1 with the link on a long
+ * side), summed over nu != mu.  Every staple is a path from x to x+mu. */
+static void staple_sum(const geom* g, const cplx* U, long x, int mu, double cp, double cr, cplx* C) {
+    for (int k = 0; k < 9; ++k) C[k] = 0;
+    long xpm = shift(g, x, mu, 1);
+    for (int nu = 0; nu < 4; ++nu) {
+        if (nu == mu) continue;
+        cplx a[9], b[9];
+        long xpn = shift(g, x, nu, 1), xmn = shift(g, x, nu, -1);
+        long xmn_pm = shift(g, xmn, mu, 1);
+        /* upper: U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag */
+        m_mul(a, clink(U, x, nu), clink(U, xpn, mu));
+        m_mul_nd(b, a, clink(U, xpm, nu));
+        for (int k = 0; k < 9; ++k) C[k] += cp * b[k];
+        /* lower: U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu) */
+        m_mul_dn(a, clink(U, xmn, nu), clink(U, xmn, mu));
+        m_mul(b, a, clink(U, xmn_pm, nu));
+        for (int k = 0; k < 9; ++k) C[k] += cp * b[k];
+        if (cr == 0) continue;
+        long xp2n = shift(g, xpn, nu, 1), xm2n = shift(g, xmn, nu, -1);
+        long xmm = shift(g, x, mu, -1);
+        cplx r[9];
+        /* 1x2 up: U_nu(x) U_nu(x+nu) U_mu(x+2nu) U_nu(x+mu+nu)^dag U_nu(x+mu)^dag */
+        m_mul(a, clink(U, x, nu), clink(U, xpn, nu));
+        m_mul(b, a, clink(U, xp2n, mu));
+        m_mul_nd(a, b, clink(U, shift(g, xpm, nu, 1), nu));
+        m_mul_nd(r, a, clink(U, xpm, nu));
+        for (int k = 0; k < 9; ++k) C[k] += cr * r[k];
+        /* 1x2 down: U_nu(x-nu)^dag U_nu(x-2nu)^dag U_mu(x-2nu) U_nu(x-2nu+mu) U_nu(x-nu+mu) */
+        {
+            /* (U_nu(x-2nu) U_nu(x-nu))^dag = U_nu(x-nu)^dag U_nu(x-2nu)^dag */
+            cplx p2[9];
+            m_mul(p2, clink(U, xm2n, nu), clink(U, xmn, nu));
+            m_dag(a, p2);
+        }
+        m_mul(b, a, clink(U, xm2n, mu));
+        m_mul(a, b, clink(U, shift(g, xm2n, mu, 1), nu));
+        m_mul(r, a, clink(U, xmn_pm, nu));
+        for (int k = 0; k < 9; ++k) C[k] += cr * r[k];
+        /* 2x1 forward up: U_nu(x) U_mu(x+nu) U_mu(x+nu+mu) U_nu(x+2mu)^dag U_mu(x+mu)^dag */
+        long xp2m = shift(g, xpm, mu, 1);
+        m_mul(a, clink(U, x, nu), clink(U, xpn, mu));
+        m_mul(b, a, clink(U, shift(g, xpn, mu, 1), mu));
+        m_mul_nd(a, b, clink(U, xp2m, nu));
+        m_mul_nd(r, a, clink(U, xpm, mu));
+        for (int k = 0; k < 9; ++k) C[k] += cr * r[k];
+        /* 2x1 forward down: U_nu(x-nu)^dag U_mu(x-nu) U_mu(x-nu+mu) U_nu(x-nu+2mu) U_mu(x+mu)^dag */
+        m_mul_dn(a, clink(U, xmn, nu), clink(U, xmn, mu));
+        m_mul(b, a, clink(U, xmn_pm, mu));
+        m_mul(a, b, clink(U, shift(g, xmn_pm, mu, 1), nu));
+        m_mul_nd(r, a, clink(U, xpm, mu));
+        for (int k = 0; k < 9; ++k) C[k] += cr * r[k];
+        /* 2x1 backward up: U_mu(x-mu)^dag U_nu(x-mu) U_mu(x-mu+nu) U_mu(x+nu) U_nu(x+mu)^dag */
+        m_mul_dn(a, clink(U, xmm, mu), clink(U, xmm, nu));
+        m_mul(b, a, clink(U, shift(g, xmm, nu, 1), mu));
+        m_mul(a, b, clink(U, xpn, mu));
+        m_mul_nd(r, a, clink(U, xpm, nu));
+        for (int k = 0; k < 9; ++k) C[k] += cr * r[k];
+        /* 2x1 backward down: U_mu(x-mu)^dag U_nu(x-mu-nu)^dag U_mu(x-mu-nu) U_mu(x-nu) U_nu(x-nu+mu) */
+        {
+            long xmm_mn = shift(g, xmm, nu, -1);
+            cplx p2[9];
+            m_mul(p2, clink(U, xmm_mn, nu), clink(U, xmm, mu)); /* U_nu(x-mu-nu) U_mu(x-mu) */
+            m_dag(a, p2);                                         /* U_mu(x-mu)^dag U_nu(x-mu-nu)^dag */
+            m_mul(b, a, clink(U, xmm_mn, mu));
+            m_mul(a, b, clink(U, xmn, mu));
+            m_mul(r, a, clink(U, xmn_pm, nu));
+        }
+        for (int k = 0; k < 9; ++k) C[k] += cr * r[k];
+    }
+}
+
+/*
+ * One smearing step, all links at once from the old field:
+ *   C_mu(x) = rho * S_mu(x),  Om = C_mu(x) U_mu(x)^dag,
+ *   Q = (i/2)(Om^dag - Om) - (i/6) tr(Om^dag - Om),  U' = exp(iQ) U.
+ * S is the staple sum of the over-improved action with weights
+ * (5 - 2 eps)/3 on plaquette staples and -(1 - eps)/12 on rectangle staples;
+ * eps = 1 is plain stout smearing (weights 1 and 0).  (Sec. II.B: stout and
+ * over-improved stout smearing as cited there.)
+ */
+void orc_smear_step(const int* dims, const cplx* Uin, cplx* Uout, double rho, double eps) {
+    geom g = make_geom(dims);
+    double cp = (5.0 - 2.0 * eps) / 3.0;
+    double cr = -(1.0 - eps) / 12.0;
+#pragma omp parallel for schedule(static)
+    for (long x = 0; x < g.vol; ++x)
+        for (int mu = 0; mu < 4; ++mu) {
+            cplx C[9], Om[9], Q[9], X[9], E[9];
+            staple_sum(&g, Uin, x, mu, cp, cr, C);
+            for (int k = 0; k < 9; ++k) C[k] *= rho;
+            m_mul_nd(Om, C, clink(Uin, x, mu));
+            cplx tr = 0;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    cplx d = conj(Om[3 * j + i]) - Om[3 * i + j]; /* (Om^dag - Om)_ij */
+                    Q[3 * i + j] = 0.5 * I * d;
+                    if (i == j) tr += d;
+                }
+            for (int i = 0; i < 3; ++i) Q[4 * i] -= (I / 6.0) * tr;
+            for (int k = 0; k < 9; ++k) X[k] = I * Q[k];
+            orc_expm(X, E);
+            m_mul(link(Uout, x, mu), E, clink(Uin, x, mu));
+        }
+}
+
+void orc_smear(const int* dims, const cplx* Uin, cplx* Uout, double rho, double eps, int nsteps) {
+    geom g = make_geom(dims);
+    size_t bytes = (size_t)g.vol * 4 * 9 * sizeof(cplx);
+    if (nsteps <= 0) {
+        memcpy(Uout, Uin, bytes);
+        return;
+    }
+    cplx* tmp = (cplx*)malloc(bytes);
+    const cplx* src = Uin;
+    for (int s = 0; s < nsteps; ++s) {
+        /* ping-pong so that the last step writes Uout */
+        cplx* dst = ((nsteps - 1 - s) % 2 == 0) ? Uout : tmp;
+        orc_smear_step(dims, src, dst, rho, eps);
+        src = dst;
+    }
+    free(tmp);
+}
+
+/* ------------------------------------------------------------------ */
+/* Center projection and P-vortices                                     */
+/* ------------------------------------------------------------------ */
+
+/* Center sector of a link (Sec. II.A): the phase of tr U nearest to
+ * 2 pi m / 3, m in {-1, 0, +1}.  Decided by exact comparisons:
+ *   m = 0  if Re t >= 0 and |Im t| <= sqrt(3) Re t   (|phi| <= pi/3),
+ *   m = +1 else if Im t >= 0                         (pi/3 < phi <= pi),
+ *   m = -1 otherwise.
+ * t = (U00 + U11) + U22.  This is also the center element Z closest to U on
+ * the group manifold, since Re tr(Z^dag U) = |t| cos(phi - 2 pi m / 3). */
+void orc_center_project(const int* dims, const cplx* U, int8_t* m) {
+    geom g = make_geom(dims);
+    const double sqrt3 = 1.7320508075688772;
+#pragma omp parallel for schedule(static)
+    for (long l = 0; l < g.vol * 4; ++l) {
+        const cplx* u = U + l * 9;
+        double re = (creal(u[0]) + creal(u[4])) + creal(u[8]);
+        double im = (cimag(u[0]) + cimag(u[4])) + cimag(u[8]);
+        volatile double lim = sqrt3 * re; /* a plain product, never fused */
+        int8_t s;
+        if (re >= 0 && fabs(im) <= lim) s = 0;
+        else if (im >= 0) s = 1;
+        else s = -1;
+        m[l] = s;
+    }
+}
+
+/* Count P-vortices (Sec. II.A): a plaquette is pierced when the product of its
+ * four center links is non-trivial, i.e. when
+ * (m_mu(x) + m_nu(x+mu) - m_mu(x+nu) - m_nu(x)) mod 3 != 0.
+ * per_plane[6] (may be NULL) receives the count for planes 01,02,03,12,13,23.
+ * Returns the total. */
+long long orc_vortex_count(const int* dims, const int8_t* m, long long* per_plane) {
+    geom g = make_geom(dims);
+    long long cnt[6] = {0};
+    for (long x = 0; x < g.vol; ++x) {
+        int pl = 0;
+        for (int mu = 0; mu < 4; ++mu)
+            for (int nu = mu + 1; nu < 4; ++nu, ++pl) {
+                int n = m[x * 4 + mu] + m[shift(&g, x, mu, 1) * 4 + nu] - m[shift(&g, x, nu, 1) * 4 + mu] -
+                        m[x * 4 + nu];
+                if (((n % 3) + 3) % 3 != 0) cnt[pl]++;
+            }
+    }
+    long long tot = 0;
+    for (int p = 0; p < 6; ++p) {
+        if (per_plane) per_plane[p] = cnt[p];
+        tot += cnt[p];
+    }
+    return tot;
+}
+
+/* ------------------------------------------------------------------ */
+/* Gradient of R with respect to the gauge transform                    */
+/* ------------------------------------------------------------------ */
+
+/* The eight SU(3) generators T_a = lambda_a / 2 (Gell-Mann matrices,
+ * tr(lambda_a lambda_b) = 2 delta_ab), row-major 3x3. */
+static void gell_mann_half(cplx T[8][9]) {
+    for (int a = 0; a < 8; ++a)
+        for (int k = 0; k < 9; ++k) T[a][k] = 0;
+    T[0][1] = T[0][3] = 0.5;
+    T[1][1] = -0.5 * I;
+    T[1][3] = 0.5 * I;
+    T[2][0] = 0.5;
+    T[2][4] = -0.5;
+    T[3][2] = T[3][6] = 0.5;
+    T[4][2] = -0.5 * I;
+    T[4][6] = 0.5 * I;
+    T[5][5] = T[5][7] = 0.5;
+    T[6][5] = -0.5 * I;
+    T[6][7] = 0.5 * I;
+    T[7][0] = T[7][4] = 0.5 / sqrt(3.0);
+    T[7][8] = -1.0 / sqrt(3.0);
+}
+
+void orc_generators(cplx* out) {
+    cplx T[8][9];
+    gell_mann_half(T);
+    memcpy(out, T, sizeof T);
+}
+
+/* d R / d eps_a at eps = 0 for Omega(x) -> exp(i eps T_a) Omega(x):
+ * U_mu(x) -> (1 + i eps T_a) U_mu(x) and U_mu(x-mu) -> U_mu(x-mu)(1 - i eps T_a),
+ * so with t_f = tr U_mu(x), t_b = tr U_mu(x-mu):
+ *   dR_a(x) = sum_mu 2 Re[conj(t_f) i tr(T_a U_mu(x))]
+ *           + 2 Re[conj(t_b) (-i) tr(T_a U_mu(x-mu))].
+ * grad is V x 8. */
+void orc_grad_R(const int* dims, const cplx* U, double* grad) {
+    geom g = make_geom(dims);
+    cplx T[8][9];
+    gell_mann_half(T);
+#pragma omp parallel for schedule(static)
+    for (long x = 0; x < g.vol; ++x) {
+        for (int a = 0; a < 8; ++a) grad[x * 8 + a] = 0;
+        for (int mu = 0; mu < 4; ++mu) {
+            const cplx* F = clink(U, x, mu);
+            const cplx* B = clink(U, shift(&g, x, mu, -1), mu);
+            cplx tf = m_trace(F), tb = m_trace(B);
+            for (int a = 0; a < 8; ++a) {
+                cplx t1[9], t2[9];
+                m_mul(t1, T[a], F);
+                m_mul(t2, T[a], B);
+                grad[x * 8 + a] += 2.0 * creal(conj(tf) * I * m_trace(t1)) + 2.0 * creal(conj(tb) * (-I) * m_trace(t2));
+            }
+        }
+    }
+}
+
+int orc_version(void) { return 1; }
