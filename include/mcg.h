@@ -1,0 +1,213 @@
+/*
+ * libmcg — Maximal Center Gauge (MCG) fixing of 4D SU(3) lattice gauge fields
+ * with stout / over-improved stout preconditioning, Z3 center projection and
+ * P-vortex counting, on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: A. O Cais et al., "Preconditioning Maximal Center Gauge with Stout
+ * Link Smearing in SU(3)" (2008).  Sec. II.A defines the MCG functional, the
+ * center projection and P-vortices; Sec. II.B the preconditioning pipeline;
+ * Sec. III the smearing parameters.
+ *
+ * CONVENTIONS (every entry point)
+ *  - Pointers named U, G, Z, S, grad are DEVICE pointers to caller-owned
+ *    memory; pointers named *_out, *_host or counts are HOST pointers.
+ *  - Calls are asynchronous on `stream` unless they return scalars through
+ *    host pointers, in which case they synchronise `stream` before returning.
+ *    `stream` may be 0 (the legacy default stream).
+ *  - Return value: MCG_OK (0) or an mcg_status code; the message of the last
+ *    failure on the calling thread is mcg_last_error().  No C++ exception
+ *    crosses this boundary.
+ *  - The library allocates only internal scratch (device work buffers, pinned
+ *    host staging), cached across calls and freed by mcg_release().
+ *
+ * LAYOUT (device, "even/odd SoA"), for a lattice Nx x Ny x Nz x Nt with every
+ * extent even and >= 2, V = Nx Ny Nz Nt, Vh = V / 2:
+ *   site x = (x,y,z,t), lexicographic index i = x + Nx (y + Ny (z + Nz t)),
+ *   parity p = (x+y+z+t) mod 2, in-parity index s = i / 2;
+ *   a complex number is (re, im) interleaved, in the field's precision;
+ *   links  U_mu(x)[row][col]: complex element ((mu*2 + p)*9 + 3*row + col)*Vh + s
+ *   gauge  Omega(x)[row][col]: complex element (p*9 + 3*row + col)*Vh + s
+ *   center sector of U_mu(x): int8 element (mu*2 + p)*Vh + s, value in {-1,0,1}
+ * A batch of `nfields` fields of the same dims is stored back to back
+ * (field f starts at complex element f*72*Vh for links, f*18*Vh for gauge).
+ * mu = 0,1,2,3 is the x,y,z,t direction.
+ *
+ * CANONICAL host layout (accepted by the pack/unpack calls): complex double
+ * U[i][mu][row][col] and Omega[i][row][col], i lexicographic as above.
+ */
+#ifndef MCG_H
+#define MCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MCG_OK = 0,
+    MCG_NOT_CONVERGED = 1, /* max_sweeps reached; results are valid          */
+    MCG_BAD_DIMS = 2,      /* an extent is odd or < 2, or nfields < 1        */
+    MCG_BAD_ARG = 3,       /* null pointer, aliasing, out-of-range parameter */
+    MCG_BAD_INPUT = 4,     /* non-finite or non-unitary input field          */
+    MCG_CUDA_ERROR = 5,    /* a CUDA runtime call failed                     */
+    MCG_WAIT_TIMEOUT = 6   /* a bounded device-side wait gave up             */
+} mcg_status;
+
+typedef enum { MCG_F64 = 0, MCG_F32 = 1 } mcg_precision;
+
+typedef struct {
+    int dims[4];   /* Nx, Ny, Nz, Nt: each even and >= 2                        */
+    int nfields;   /* fields of these dims stored back to back (>= 1)           */
+    int precision; /* MCG_F64 or MCG_F32: element type of U / G arrays          */
+} mcg_lattice;
+
+/*
+ * Parameters of the MCG relaxation (Sec. II.A).  The paper does not state its
+ * stop rule (it counts blocks of 50 iterations); this library stops a field
+ * at the first sweep k with V_U(k) - V_U(k-1) < tol, where
+ * V_U = R / (9 * 4V), R = sum_{x,mu} |tr U_mu(x)|^2.
+ */
+typedef struct {
+    double tol;        /* stop threshold on the per-sweep change of V_U (1e-10) */
+    int max_sweeps;    /* upper bound on full sweeps (even + odd half-sweep)    */
+    int check_every;   /* sweeps between host-side convergence polls (>= 1)     */
+    int reunit_every;  /* re-unitarise links and Omega every n sweeps (0: off)  */
+    int fp32_sweeps;   /* MCG_F64 fields only: run up to this many sweeps in a  */
+                       /* FP32 phase before the FP64 sweeps (0: plain FP64)     */
+    double fp32_tol;   /* FP32 phase stops early when its dV_U < fp32_tol       */
+    int fp32_reunit_every; /* FP32 phase: re-unitarise every n sweeps          */
+} mcg_params;
+
+/* Per-field result of mcg_precondition_fix (Sec. II.B pipeline). */
+typedef struct {
+    double V_smeared;      /* V_U reached on the smeared field (0 if nsmear=0) */
+    double V_fixed;        /* V_U reached on the preconditioned original field */
+    double plaquette_in;   /* mean plaquette of the input field                */
+    double plaquette_out;  /* mean plaquette of the final field (gauge inv.)   */
+    long long vortices;    /* P-vortex plaquettes of the center projection     */
+    double vortex_density; /* vortices / (6 V)                                  */
+    int sweeps_smeared;    /* sweeps spent fixing the smeared field            */
+    int sweeps_fixed;      /* sweeps spent fixing the preconditioned field     */
+    int sweeps_fp32;       /* of those, sweeps run in the FP32 phase           */
+    int status;            /* MCG_OK or MCG_NOT_CONVERGED                       */
+} mcg_precond_result;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int mcg_version(void);
+
+/* Message describing the last failure on this thread ("" if none). */
+const char* mcg_last_error(void);
+
+/* Free all cached scratch (device and pinned host).  Safe to call any time
+ * no libmcg call is in flight; later calls re-create what they need. */
+int mcg_release(void);
+
+/* ---- layout conversion ---------------------------------------------------
+ * Canonical (complex double, device) <-> even/odd SoA in lat->precision.
+ * canon and U/G must not overlap. */
+int mcg_pack_links(const double* canon, void* U, const mcg_lattice* lat, cudaStream_t stream);
+int mcg_unpack_links(const void* U, double* canon, const mcg_lattice* lat, cudaStream_t stream);
+int mcg_pack_gauge(const double* canon, void* G, const mcg_lattice* lat, cudaStream_t stream);
+int mcg_unpack_gauge(const void* G, double* canon, const mcg_lattice* lat, cudaStream_t stream);
+/* int8 center sectors, SoA -> canonical Z[i][mu]. */
+int mcg_unpack_center(const int8_t* Z, int8_t* canon, const mcg_lattice* lat, cudaStream_t stream);
+
+/* Element-wise precision conversion of n complex numbers (SoA to SoA, same
+ * layout).  src_prec/dst_prec are mcg_precision values. */
+int mcg_convert(const void* src, int src_prec, void* dst, int dst_prec, size_t n_complex, cudaStream_t stream);
+
+/* Omega(x) = 1 for every site. */
+int mcg_set_identity_gauge(void* G, const mcg_lattice* lat, cudaStream_t stream);
+
+/* ---- observables ---------------------------------------------------------- */
+
+/* Mean plaquette <(1/3) Re tr U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag>
+ * over 6V plaquettes, per field (Sec. III.A: gauge invariant).
+ * out: host, nfields doubles.  Synchronises. */
+int mcg_plaquette(const void* U, double* out, const mcg_lattice* lat, cudaStream_t stream);
+
+/* MCG functional R = sum_{x,mu} |tr U_mu(x)|^2 per field (Sec. II.A; the
+ * paper's V_U = R / (9 * 4V)).  R_out: host, nfields doubles.  Synchronises. */
+int mcg_functional(const void* U, double* R_out, const mcg_lattice* lat, cudaStream_t stream);
+
+/* ---- gauge transforms ----------------------------------------------------- */
+
+/* U_mu(x) <- Omega(x) U_mu(x) Omega(x+mu)^dag in place (Sec. II.B: the
+ * preconditioning transform applied to the original links). */
+int mcg_apply_gauge(void* U, const void* G, const mcg_lattice* lat, cudaStream_t stream);
+
+/* Project every link (which=0) or every Omega (which=1) back onto SU(3)
+ * (Gram-Schmidt on rows 0,1; row 2 = conj(row0 x row1)); arithmetic in FP64. */
+int mcg_reunitarise(void* M, int which, const mcg_lattice* lat, cudaStream_t stream);
+
+/* ---- the method ----------------------------------------------------------- */
+
+/*
+ * n steps of stout smearing (eps = 1) or over-improved stout smearing
+ * (Sec. II.B and III: stout rho = 0.1; over-improved rho = 0.06, eps = -0.25).
+ * Each step updates all links at once from the old field:
+ *   C_mu(x) = rho * [ (5-2eps)/3 * (plaquette staples) - (1-eps)/12 * (2x1 and
+ *             1x2 rectangle staples) ],  Omega = C U^dag,
+ *   Q = (i/2)(Omega^dag - Omega) - (i/6) tr(Omega^dag - Omega),  U' = exp(iQ) U.
+ * U_in and U_out are fields of lat (U_out must not overlap U_in); n = 0 copies.
+ */
+int mcg_smear(const void* U_in, void* U_out, const mcg_lattice* lat, double rho, double eps, int n,
+              cudaStream_t stream);
+
+/*
+ * MCG relaxation (Sec. II.A; "as outlined in Langfeld 2003", not reproduced in
+ * the paper): full sweeps = even then odd checkerboard half-sweep; each site
+ * update picks, for the SU(2) subgroups (0,1), (0,2), (1,2) in turn, the
+ * subgroup element G that exactly maximises sum over the 8 links at x of
+ * |tr|^2, then U_mu(x) <- G U_mu(x), U_mu(x-mu) <- U_mu(x-mu) G^dag and
+ * Omega(x) <- G Omega(x).  In place on U and G (pass G = identity to start
+ * fresh, or a random transform for a Gribov copy).  Per field, stops at the
+ * first sweep with dV_U < params->tol, or at params->max_sweeps.
+ * With lat->precision = MCG_F64 and params->fp32_sweeps > 0 the early sweeps
+ * run in FP32 (links and the transform of this call in FP32, R accumulated in
+ * FP64); the FP32 transform is then re-unitarised in FP64 and applied to the
+ * FP64 links, which keeps them on the gauge orbit, and FP64 sweeps finish.
+ * R_out (host, nfields, may be NULL): R after the last sweep.
+ * sweeps_out (host, nfields, may be NULL): sweeps performed (FP32 + FP64).
+ * R_hist (host, nfields x (max_sweeps+1), may be NULL): R before the first
+ *   sweep and after each sweep (entries past the last sweep are 0).
+ * Returns MCG_OK when every field converged, else MCG_NOT_CONVERGED.
+ * Synchronises.
+ */
+int mcg_fix(void* U, void* G, const mcg_lattice* lat, const mcg_params* params, double* R_out,
+            int* sweeps_out, double* R_hist, cudaStream_t stream);
+
+/* Z3 center projection (Sec. II.A): m_mu(x) in {-1,0,1} is the sector of
+ * phi = arg tr U_mu(x) nearest 2 pi m / 3 (equivalently the closest center
+ * element on the group manifold); ties on |phi| = pi/3 go to 0, phi = pi to
+ * +1.  The decision is taken in FP64 for both precisions.  Then P-vortices:
+ * a plaquette is pierced when (m_mu(x) + m_nu(x+mu) - m_mu(x+nu) - m_nu(x))
+ * mod 3 != 0.  Z: device int8 (layout above).  counts: host, 7 x nfields
+ * long long: [total, planes 01, 02, 03, 12, 13, 23] per field.  Synchronises. */
+int mcg_center_project(const void* U, int8_t* Z, long long* counts, const mcg_lattice* lat,
+                       cudaStream_t stream);
+
+/*
+ * The preconditioning pipeline of Sec. II.B for every field of the batch:
+ * S = smear(U, rho, eps, nsmear); fix S (transform Omega_1 from identity);
+ * apply Omega_1 (re-unitarised) to the original U; fix that field (transform
+ * Omega_2); center-project and count P-vortices.  nsmear = 0 skips smearing
+ * and the first fix (plain MCG).  On return U holds the fixed field and G
+ * the total transform Omega_2 Omega_1, so U_out = U_in^G.  smear_precision
+ * selects FP64 or FP32 smearing (the smeared field only builds Omega_1).
+ * Z (device int8, may be NULL): center sectors of the final field.
+ * results: host, nfields entries.  Returns MCG_OK or MCG_NOT_CONVERGED.
+ */
+int mcg_precondition_fix(void* U, void* G, int8_t* Z, const mcg_lattice* lat, const mcg_params* params,
+                         double rho, double eps, int nsmear, int smear_precision, mcg_precond_result* results,
+                         cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCG_H */

@@ -1,0 +1,472 @@
+// The extern "C" boundary of libmcg (declared in include/mcg.h): argument
+// validation, error reporting, scratch management and the host-side
+// orchestration of the MCG relaxation and the preconditioning pipeline.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/mcg.h"
+#include "mcg_common.cuh"
+#include "mcg_internal.h"
+
+namespace mcg {
+
+int launch_pack(const double* canon, void* soa, int prec, const Geom& g, int nfields, int what, int unpack,
+                cudaStream_t st);
+int launch_unpack_center(const int8_t* Z, int8_t* canon, const Geom& g, int nfields, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int fail(int code, const std::string& msg) {
+    set_error(msg);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    set_error(buf);
+    return MCG_CUDA_ERROR;
+}
+
+// ---------------------------------------------------------------------------
+// scratch: grow-only named buffers per device
+// ---------------------------------------------------------------------------
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+struct DeviceScratch {
+    std::map<std::string, Buf> dev, host;
+    cudaStream_t cap = nullptr;
+};
+static std::mutex g_mu;
+static std::map<int, DeviceScratch> g_scratch;
+
+static DeviceScratch& cur(int* rc) {
+    int d = 0;
+    cudaError_t e = cudaGetDevice(&d);
+    if (e != cudaSuccess) *rc = cuda_fail(e, "cudaGetDevice");
+    return g_scratch[d];
+}
+
+void* scratch_device(const char* name, size_t bytes, int* rc) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceScratch& ds = cur(rc);
+    if (*rc) return nullptr;
+    Buf& b = ds.dev[name];
+    if (b.bytes < bytes) {
+        if (b.p) {
+            cudaDeviceSynchronize();
+            cudaFree(b.p);
+            b.p = nullptr;
+            b.bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&b.p, std::max<size_t>(bytes, 256));
+        if (e != cudaSuccess) {
+            *rc = cuda_fail(e, "cudaMalloc(scratch)");
+            return nullptr;
+        }
+        b.bytes = std::max<size_t>(bytes, 256);
+    }
+    return b.p;
+}
+
+void* scratch_host(const char* name, size_t bytes, int* rc) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceScratch& ds = cur(rc);
+    if (*rc) return nullptr;
+    Buf& b = ds.host[name];
+    if (b.bytes < bytes) {
+        if (b.p) {
+            cudaDeviceSynchronize();
+            cudaFreeHost(b.p);
+            b.p = nullptr;
+            b.bytes = 0;
+        }
+        cudaError_t e = cudaMallocHost(&b.p, std::max<size_t>(bytes, 256));
+        if (e != cudaSuccess) {
+            *rc = cuda_fail(e, "cudaMallocHost(scratch)");
+            return nullptr;
+        }
+        b.bytes = std::max<size_t>(bytes, 256);
+    }
+    return b.p;
+}
+
+cudaStream_t capture_stream(int* rc) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceScratch& ds = cur(rc);
+    if (*rc) return nullptr;
+    if (!ds.cap) {
+        cudaError_t e = cudaStreamCreateWithFlags(&ds.cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            *rc = cuda_fail(e, "cudaStreamCreate");
+            return nullptr;
+        }
+    }
+    return ds.cap;
+}
+
+void release_all() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (auto& kv : g_scratch) {
+        cudaSetDevice(kv.first);
+        cudaDeviceSynchronize();
+        for (auto& b : kv.second.dev)
+            if (b.second.p) cudaFree(b.second.p);
+        for (auto& b : kv.second.host)
+            if (b.second.p) cudaFreeHost(b.second.p);
+        if (kv.second.cap) cudaStreamDestroy(kv.second.cap);
+    }
+    g_scratch.clear();
+    cudaSetDevice(dev);
+}
+
+// ---------------------------------------------------------------------------
+// validation helpers
+// ---------------------------------------------------------------------------
+static int check_lat(const mcg_lattice* lat, Geom* g) {
+    if (!lat) return fail(MCG_BAD_ARG, "lattice descriptor is NULL");
+    for (int d = 0; d < 4; ++d)
+        if (lat->dims[d] < 2 || (lat->dims[d] & 1))
+            return fail(MCG_BAD_DIMS, "every lattice extent must be even and >= 2");
+    if (lat->nfields < 1) return fail(MCG_BAD_DIMS, "nfields must be >= 1");
+    if (lat->precision != MCG_F64 && lat->precision != MCG_F32)
+        return fail(MCG_BAD_ARG, "precision must be MCG_F64 or MCG_F32");
+    const long long V = (long long)lat->dims[0] * lat->dims[1] * lat->dims[2] * lat->dims[3];
+    if (V / 2 > (1LL << 30)) return fail(MCG_BAD_DIMS, "lattice too large");
+    for (int d = 0; d < 4; ++d) g->n[d] = lat->dims[d];
+    g->vh = (int)(V / 2);
+    return 0;
+}
+
+static size_t elem_bytes(int prec) { return prec == MCG_F64 ? 16 : 8; }
+
+static bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+    const char* pa = (const char*)a;
+    const char* pb = (const char*)b;
+    return pa < pb + nb && pb < pa + na;
+}
+
+static int check_params(const mcg_params* p) {
+    if (!p) return fail(MCG_BAD_ARG, "params is NULL");
+    if (p->max_sweeps < 0) return fail(MCG_BAD_ARG, "max_sweeps must be >= 0");
+    if (p->check_every < 1) return fail(MCG_BAD_ARG, "check_every must be >= 1");
+    if (p->reunit_every < 0 || p->fp32_sweeps < 0 || p->fp32_reunit_every < 0)
+        return fail(MCG_BAD_ARG, "negative schedule parameter");
+    if (!(p->tol == p->tol)) return fail(MCG_BAD_ARG, "tol is NaN");
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// MCG fix orchestration
+// ---------------------------------------------------------------------------
+static int fix_impl(void* U, void* G, const mcg_lattice* lat, const Geom& g, const mcg_params* prm, double* R_out,
+                    int* sweeps_out, int* sweeps32_out, double* R_hist, cudaStream_t st) {
+    const int nf = lat->nfields;
+    int rc = 0;
+    FieldState* d_state = (FieldState*)scratch_device("fix.state", sizeof(FieldState) * nf, &rc);
+    if (rc) return rc;
+    FieldState* h_state = (FieldState*)scratch_host("fix.state", sizeof(FieldState) * nf, &rc);
+    if (rc) return rc;
+    const int hist_len = prm->max_sweeps + 1;
+    double* d_hist = nullptr;
+    if (R_hist) {
+        d_hist = (double*)scratch_device("fix.hist", sizeof(double) * hist_len * (size_t)nf, &rc);
+        if (rc) return rc;
+        MCG_CK(cudaMemsetAsync(d_hist, 0, sizeof(double) * hist_len * (size_t)nf, st));
+    }
+    const double norm = 1.0 / (9.0 * 8.0 * g.vh);
+    const size_t le = link_elems(g), ge = gauge_elems(g);
+    std::vector<int> s32(nf, 0);
+    bool fresh = true;
+
+    if (lat->precision == MCG_F64 && prm->fp32_sweeps > 0) {
+        // FP32 phase on a copy of the links and the transform of this call
+        void* U32 = scratch_device("fix.U32", 8 * le * nf, &rc);
+        if (rc) return rc;
+        void* W32 = scratch_device("fix.W32", 8 * ge * nf, &rc);
+        if (rc) return rc;
+        if ((rc = launch_convert(U, MCG_F64, U32, MCG_F32, le * nf, st))) return rc;
+        if ((rc = launch_identity_gauge(W32, MCG_F32, g, nf, st))) return rc;
+        std::vector<FieldDesc> fds(nf);
+        for (int f = 0; f < nf; ++f) {
+            fds[f].U = (char*)U32 + 8 * le * f;
+            fds[f].G = (char*)W32 + 8 * ge * f;
+            fds[f].geo = g;
+            fds[f].norm = norm;
+        }
+        const int cap = std::min(prm->fp32_sweeps, prm->max_sweeps);
+        rc = run_fix_phase<float>(fds, d_state, h_state, d_hist, hist_len, prm->fp32_tol, prm->fp32_reunit_every, cap,
+                                  prm->check_every, true, st);
+        if (rc) return rc;
+        for (int f = 0; f < nf; ++f) s32[f] = h_state[f].sweep;
+        // hand-off: FP64 re-unitarised transform applied to the FP64 links
+        if ((rc = launch_handoff(W32, (double*)U, (double*)G, g, nf, st))) return rc;
+        fresh = false;
+    }
+    std::vector<FieldDesc> fds(nf);
+    for (int f = 0; f < nf; ++f) {
+        fds[f].U = (char*)U + elem_bytes(lat->precision) * le * f;
+        fds[f].G = (char*)G + elem_bytes(lat->precision) * ge * f;
+        fds[f].geo = g;
+        fds[f].norm = norm;
+    }
+    if (lat->precision == MCG_F64)
+        rc = run_fix_phase<double>(fds, d_state, h_state, d_hist, hist_len, prm->tol, prm->reunit_every,
+                                   prm->max_sweeps, prm->check_every, fresh, st);
+    else
+        rc = run_fix_phase<float>(fds, d_state, h_state, d_hist, hist_len, prm->tol, prm->reunit_every,
+                                  prm->max_sweeps, prm->check_every, fresh, st);
+    if (rc) return rc;
+    bool all = true;
+    for (int f = 0; f < nf; ++f) {
+        if (R_out) R_out[f] = h_state[f].R_last;
+        if (sweeps_out) sweeps_out[f] = h_state[f].sweep;
+        if (sweeps32_out) sweeps32_out[f] = s32[f];
+        all = all && h_state[f].done == 1;
+    }
+    if (R_hist) {
+        MCG_CK(cudaMemcpyAsync(R_hist, d_hist, sizeof(double) * hist_len * (size_t)nf, cudaMemcpyDeviceToHost, st));
+        MCG_CK(cudaStreamSynchronize(st));
+    }
+    return all ? MCG_OK : MCG_NOT_CONVERGED;
+}
+
+}  // namespace mcg
+
+using namespace mcg;
+
+// ---------------------------------------------------------------------------
+// extern "C" entry points
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int mcg_version(void) { return 10000; }
+
+const char* mcg_last_error(void) { return g_last_error.c_str(); }
+
+int mcg_release(void) {
+    release_all();
+    return MCG_OK;
+}
+
+int mcg_pack_links(const double* canon, void* U, const mcg_lattice* lat, cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if (!canon || !U) return fail(MCG_BAD_ARG, "null pointer");
+    set_error("");
+    return launch_pack(canon, U, lat->precision, g, lat->nfields, 0, 0, stream);
+}
+
+int mcg_unpack_links(const void* U, double* canon, const mcg_lattice* lat, cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if (!canon || !U) return fail(MCG_BAD_ARG, "null pointer");
+    return launch_pack(canon, const_cast<void*>(U), lat->precision, g, lat->nfields, 0, 1, stream);
+}
+
+int mcg_pack_gauge(const double* canon, void* G, const mcg_lattice* lat, cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if (!canon || !G) return fail(MCG_BAD_ARG, "null pointer");
+    return launch_pack(canon, G, lat->precision, g, lat->nfields, 1, 0, stream);
+}
+
+int mcg_unpack_gauge(const void* G, double* canon, const mcg_lattice* lat, cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if (!canon || !G) return fail(MCG_BAD_ARG, "null pointer");
+    return launch_pack(canon, const_cast<void*>(G), lat->precision, g, lat->nfields, 1, 1, stream);
+}
+
+int mcg_unpack_center(const int8_t* Z, int8_t* canon, const mcg_lattice* lat, cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if (!canon || !Z) return fail(MCG_BAD_ARG, "null pointer");
+    return launch_unpack_center(Z, canon, g, lat->nfields, stream);
+}
+
+int mcg_convert(const void* src, int src_prec, void* dst, int dst_prec, size_t n_complex, cudaStream_t stream) {
+    if (!src || !dst) return fail(MCG_BAD_ARG, "null pointer");
+    if ((src_prec != MCG_F64 && src_prec != MCG_F32) || (dst_prec != MCG_F64 && dst_prec != MCG_F32))
+        return fail(MCG_BAD_ARG, "bad precision");
+    if (overlap(src, n_complex * elem_bytes(src_prec), dst, n_complex * elem_bytes(dst_prec)) && src != dst)
+        return fail(MCG_BAD_ARG, "src and dst overlap");
+    return launch_convert(src, src_prec, dst, dst_prec, n_complex, stream);
+}
+
+int mcg_set_identity_gauge(void* G, const mcg_lattice* lat, cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if (!G) return fail(MCG_BAD_ARG, "null pointer");
+    return launch_identity_gauge(G, lat->precision, g, lat->nfields, stream);
+}
+
+int mcg_plaquette(const void* U, double* out, const mcg_lattice* lat, cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if (!U || !out) return fail(MCG_BAD_ARG, "null pointer");
+    return compute_plaquette(U, lat->precision, g, lat->nfields, out, stream);
+}
+
+int mcg_functional(const void* U, double* R_out, const mcg_lattice* lat, cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if (!U || !R_out) return fail(MCG_BAD_ARG, "null pointer");
+    return compute_functional(U, lat->precision, g, lat->nfields, R_out, stream);
+}
+
+int mcg_apply_gauge(void* U, const void* G, const mcg_lattice* lat, cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if (!U || !G) return fail(MCG_BAD_ARG, "null pointer");
+    const size_t eb = elem_bytes(lat->precision);
+    if (overlap(U, eb * link_elems(g) * lat->nfields, G, eb * gauge_elems(g) * lat->nfields))
+        return fail(MCG_BAD_ARG, "U and G overlap");
+    return launch_apply_gauge(U, G, lat->precision, g, lat->nfields, stream);
+}
+
+int mcg_reunitarise(void* M, int which, const mcg_lattice* lat, cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if (!M) return fail(MCG_BAD_ARG, "null pointer");
+    if (which != 0 && which != 1) return fail(MCG_BAD_ARG, "which must be 0 (links) or 1 (gauge)");
+    return launch_reunitarise(M, which, lat->precision, g, lat->nfields, stream);
+}
+
+int mcg_smear(const void* U_in, void* U_out, const mcg_lattice* lat, double rho, double eps, int n,
+              cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if (!U_in || !U_out) return fail(MCG_BAD_ARG, "null pointer");
+    if (n < 0) return fail(MCG_BAD_ARG, "n must be >= 0");
+    if (!(std::isfinite(rho) && std::isfinite(eps))) return fail(MCG_BAD_ARG, "rho/eps not finite");
+    const size_t bytes = elem_bytes(lat->precision) * link_elems(g) * lat->nfields;
+    if (overlap(U_in, bytes, U_out, bytes)) return fail(MCG_BAD_ARG, "U_in and U_out overlap");
+    return run_smear(U_in, U_out, lat->precision, g, lat->nfields, rho, eps, n, stream);
+}
+
+int mcg_fix(void* U, void* G, const mcg_lattice* lat, const mcg_params* params, double* R_out, int* sweeps_out,
+            double* R_hist, cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if ((rc = check_params(params))) return rc;
+    if (!U || !G) return fail(MCG_BAD_ARG, "null pointer");
+    const size_t eb = elem_bytes(lat->precision);
+    if (overlap(U, eb * link_elems(g) * lat->nfields, G, eb * gauge_elems(g) * lat->nfields))
+        return fail(MCG_BAD_ARG, "U and G overlap");
+    return fix_impl(U, G, lat, g, params, R_out, sweeps_out, nullptr, R_hist, stream);
+}
+
+int mcg_center_project(const void* U, int8_t* Z, long long* counts, const mcg_lattice* lat, cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if (!U || !Z) return fail(MCG_BAD_ARG, "null pointer");
+    return compute_center(U, lat->precision, Z, g, lat->nfields, counts, stream);
+}
+
+int mcg_precondition_fix(void* U, void* G, int8_t* Z, const mcg_lattice* lat, const mcg_params* params, double rho,
+                         double eps, int nsmear, int smear_precision, mcg_precond_result* results,
+                         cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if ((rc = check_params(params))) return rc;
+    if (!U || !G || !results) return fail(MCG_BAD_ARG, "null pointer");
+    if (nsmear < 0) return fail(MCG_BAD_ARG, "nsmear must be >= 0");
+    if (smear_precision != MCG_F64 && smear_precision != MCG_F32) return fail(MCG_BAD_ARG, "bad smear precision");
+    const int nf = lat->nfields, prec = lat->precision;
+    const size_t le = link_elems(g), ge = gauge_elems(g), eb = elem_bytes(prec);
+    std::vector<double> plaq_in(nf), plaq_out(nf), Rs(nf, 0.0), Rf(nf);
+    std::vector<int> sw_s(nf, 0), sw_f(nf), sw32_s(nf, 0), sw32_f(nf, 0);
+    std::vector<long long> counts(7 * (size_t)nf);
+    if ((rc = compute_plaquette(U, prec, g, nf, plaq_in.data(), stream))) return rc;
+    int status = MCG_OK;
+    const double norm = 1.0 / (9.0 * 8.0 * g.vh);
+    if ((rc = launch_identity_gauge(G, prec, g, nf, stream))) return rc;
+    if (nsmear > 0) {
+        // S = smear(U) in the smear precision; the smeared field is then fixed
+        // in the field's precision with the caller's schedule (transform W)
+        const size_t seb = elem_bytes(smear_precision);
+        void* Uc = scratch_device("pre.Uconv", seb * le * nf, &rc);
+        if (rc) return rc;
+        void* S = scratch_device("pre.S", seb * le * nf, &rc);
+        if (rc) return rc;
+        void* Sp = scratch_device("pre.Sp", eb * le * nf, &rc);
+        if (rc) return rc;
+        void* W = scratch_device("pre.W", eb * ge * nf, &rc);
+        if (rc) return rc;
+        const void* src = U;
+        if (smear_precision != prec) {
+            if ((rc = launch_convert(U, prec, Uc, smear_precision, le * nf, stream))) return rc;
+            src = Uc;
+        }
+        if ((rc = run_smear(src, S, smear_precision, g, nf, rho, eps, nsmear, stream))) return rc;
+        if ((rc = launch_convert(S, smear_precision, Sp, prec, le * nf, stream))) return rc;
+        if (smear_precision != prec && (rc = launch_reunitarise(Sp, 0, prec, g, nf, stream))) return rc;
+        if ((rc = launch_identity_gauge(W, prec, g, nf, stream))) return rc;
+        rc = fix_impl(Sp, W, lat, g, params, Rs.data(), sw_s.data(), sw32_s.data(), nullptr, stream);
+        if (rc != MCG_OK && rc != MCG_NOT_CONVERGED) return rc;
+        if (rc == MCG_NOT_CONVERGED) status = MCG_NOT_CONVERGED;
+        // G <- reunit(W), then U <- U^G (the preconditioning transform)
+        MCG_CK(cudaMemcpyAsync(G, W, eb * ge * nf, cudaMemcpyDeviceToDevice, stream));
+        if ((rc = launch_reunitarise(G, 1, prec, g, nf, stream))) return rc;
+        if ((rc = launch_apply_gauge(U, G, prec, g, nf, stream))) return rc;
+    }
+    // fix the preconditioned original field, accumulating into G
+    rc = fix_impl(U, G, lat, g, params, Rf.data(), sw_f.data(), sw32_f.data(), nullptr, stream);
+    if (rc != MCG_OK && rc != MCG_NOT_CONVERGED) return rc;
+    if (rc == MCG_NOT_CONVERGED) status = MCG_NOT_CONVERGED;
+    int8_t* Zb = Z;
+    if (!Zb) {
+        Zb = (int8_t*)scratch_device("pre.Z", 8 * (size_t)g.vh * nf, &rc);
+        if (rc) return rc;
+    }
+    if ((rc = compute_center(U, prec, Zb, g, nf, counts.data(), stream))) return rc;
+    if ((rc = compute_plaquette(U, prec, g, nf, plaq_out.data(), stream))) return rc;
+    for (int f = 0; f < nf; ++f) {
+        mcg_precond_result& r = results[f];
+        r.V_smeared = Rs[f] * norm;
+        r.V_fixed = Rf[f] * norm;
+        r.plaquette_in = plaq_in[f];
+        r.plaquette_out = plaq_out[f];
+        r.vortices = counts[7 * f];
+        r.vortex_density = (double)counts[7 * f] / (6.0 * 2.0 * g.vh);
+        r.sweeps_smeared = sw_s[f];
+        r.sweeps_fixed = sw_f[f];
+        r.sweeps_fp32 = sw32_s[f] + sw32_f[f];
+        r.status = status;
+    }
+    return status;
+}
+
+}  // extern "C"

@@ -1,0 +1,270 @@
+// Device-side building blocks shared by the libmcg kernels: complex numbers,
+// 3x3 complex matrix helpers, the even/odd SoA field layout and lattice
+// geometry.  Everything here is for sm_103a; none of it is used by the CPU
+// oracle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mcg.h"
+
+namespace mcg {
+
+// ---------------------------------------------------------------------------
+// complex arithmetic (vector-aligned so a link element is one 8/16-byte load)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct alignas(2 * sizeof(T)) cplx {
+    T x, y;
+};
+
+template <typename T>
+__device__ __forceinline__ cplx<T> mk(T x, T y) {
+    cplx<T> r;
+    r.x = x;
+    r.y = y;
+    return r;
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> cadd(cplx<T> a, cplx<T> b) {
+    return mk(a.x + b.x, a.y + b.y);
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> csub(cplx<T> a, cplx<T> b) {
+    return mk(a.x - b.x, a.y - b.y);
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
+    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename T>
+__device__ __forceinline__ cplx<T> cmulc(cplx<T> a, cplx<T> b) {
+    return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+// acc + a * b
+template <typename T>
+__device__ __forceinline__ cplx<T> cfma(cplx<T> a, cplx<T> b, cplx<T> acc) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+    return acc;
+}
+// acc + a * conj(b)
+template <typename T>
+__device__ __forceinline__ cplx<T> cfmac(cplx<T> a, cplx<T> b, cplx<T> acc) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.y, b.x, acc.y);
+    acc.y = fma(-a.x, b.y, acc.y);
+    return acc;
+}
+// acc + conj(a) * b
+template <typename T>
+__device__ __forceinline__ cplx<T> cfmaca(cplx<T> a, cplx<T> b, cplx<T> acc) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+    return acc;
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> cscale(cplx<T> a, T s) {
+    return mk(a.x * s, a.y * s);
+}
+template <typename T>
+__device__ __forceinline__ T cnorm2(cplx<T> a) {
+    return a.x * a.x + a.y * a.y;
+}
+
+// ---------------------------------------------------------------------------
+// 3x3 complex matrices held in registers, row-major m[3*i + j]
+// ---------------------------------------------------------------------------
+template <typename T>
+struct M3 {
+    cplx<T> m[9];
+};
+
+template <typename T>
+__device__ __forceinline__ void m3_mul(const cplx<T>* a, const cplx<T>* b, cplx<T>* r) {  // r = a b
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            cplx<T> s = cmul(a[3 * i], b[j]);
+            s = cfma(a[3 * i + 1], b[3 + j], s);
+            s = cfma(a[3 * i + 2], b[6 + j], s);
+            r[3 * i + j] = s;
+        }
+}
+template <typename T>
+__device__ __forceinline__ void m3_mul_nd(const cplx<T>* a, const cplx<T>* b, cplx<T>* r) {  // r = a b^dag
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            cplx<T> s = cmulc(a[3 * i], b[3 * j]);
+            s = cfmac(a[3 * i + 1], b[3 * j + 1], s);
+            s = cfmac(a[3 * i + 2], b[3 * j + 2], s);
+            r[3 * i + j] = s;
+        }
+}
+template <typename T>
+__device__ __forceinline__ void m3_mul_dn(const cplx<T>* a, const cplx<T>* b, cplx<T>* r) {  // r = a^dag b
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            cplx<T> s = mk(a[i].x * b[j].x + a[i].y * b[j].y, a[i].x * b[j].y - a[i].y * b[j].x);
+            s = cfmaca(a[3 + i], b[3 + j], s);
+            s = cfmaca(a[6 + i], b[6 + j], s);
+            r[3 * i + j] = s;
+        }
+}
+
+// Re-unitarise in place: normalise row 0, orthogonalise and normalise row 1,
+// row 2 = conj(row0 x row1).  Arithmetic in double whatever T is.
+template <typename T>
+__device__ __forceinline__ void m3_reunitarise(cplx<T>* a) {
+    double r0x[3], r0y[3], r1x[3], r1y[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        r0x[k] = (double)a[k].x;
+        r0y[k] = (double)a[k].y;
+        r1x[k] = (double)a[3 + k].x;
+        r1y[k] = (double)a[3 + k].y;
+    }
+    double n0 = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) n0 += r0x[k] * r0x[k] + r0y[k] * r0y[k];
+    n0 = rsqrt(n0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        r0x[k] *= n0;
+        r0y[k] *= n0;
+    }
+    double px = 0, py = 0;  // conj(r0) . r1
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        px += r0x[k] * r1x[k] + r0y[k] * r1y[k];
+        py += r0x[k] * r1y[k] - r0y[k] * r1x[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        r1x[k] -= px * r0x[k] - py * r0y[k];
+        r1y[k] -= px * r0y[k] + py * r0x[k];
+    }
+    double n1 = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) n1 += r1x[k] * r1x[k] + r1y[k] * r1y[k];
+    n1 = rsqrt(n1);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        r1x[k] *= n1;
+        r1y[k] *= n1;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        a[k] = mk((T)r0x[k], (T)r0y[k]);
+        a[3 + k] = mk((T)r1x[k], (T)r1y[k]);
+    }
+    // row 2 = conj(r0 x r1): (r0_1 r1_2 - r0_2 r1_1)^*, ...
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        int i = (k + 1) % 3, j = (k + 2) % 3;
+        double cx = (r0x[i] * r1x[j] - r0y[i] * r1y[j]) - (r0x[j] * r1x[i] - r0y[j] * r1y[i]);
+        double cy = (r0x[i] * r1y[j] + r0y[i] * r1x[j]) - (r0x[j] * r1y[i] + r0y[j] * r1x[i]);
+        a[6 + k] = mk((T)cx, (T)(-cy));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Field layout (the C-ABI contract, see include/mcg.h):
+//   site s of parity p (in-parity index s = lexicographic index / 2),
+//   link U_mu entry e = 3*row+col:  U[((mu*2 + p)*9 + e)*Vh + s]
+//   gauge Omega entry e:            G[(p*9 + e)*Vh + s]
+//   center sector of U_mu:          Z[(mu*2 + p)*Vh + s]
+// ---------------------------------------------------------------------------
+struct Geom {
+    int n[4];
+    int vh;  // V / 2
+};
+
+__host__ __device__ __forceinline__ size_t link_elems(const Geom& g) { return (size_t)72 * g.vh; }
+__host__ __device__ __forceinline__ size_t gauge_elems(const Geom& g) { return (size_t)18 * g.vh; }
+
+__device__ __forceinline__ size_t lidx(const Geom& g, int mu, int p, int e, int s) {
+    return ((size_t)((mu * 2 + p) * 9 + e)) * g.vh + s;
+}
+__device__ __forceinline__ size_t gidx(const Geom& g, int p, int e, int s) {
+    return ((size_t)(p * 9 + e)) * g.vh + s;
+}
+
+// coordinates (x,y,z,t) of site s in parity p
+__device__ __forceinline__ void eo_coords(const Geom& g, int p, int s, int c[4]) {
+    int i2 = 2 * s;
+    int x0 = i2 % g.n[0];
+    int r = i2 / g.n[0];
+    c[1] = r % g.n[1];
+    r /= g.n[1];
+    c[2] = r % g.n[2];
+    c[3] = r / g.n[2];
+    c[0] = x0 + ((c[1] + c[2] + c[3] + p) & 1);
+}
+__device__ __forceinline__ int eo_index(const Geom& g, const int c[4]) {
+    return (c[0] + g.n[0] * (c[1] + g.n[1] * (c[2] + g.n[2] * c[3]))) >> 1;
+}
+// in-parity index of the neighbour c +- mu (step = +1 or -1), periodic
+__device__ __forceinline__ int eo_neighbor(const Geom& g, const int c[4], int mu, int step) {
+    int d[4] = {c[0], c[1], c[2], c[3]};
+    int v = d[mu] + step;
+    d[mu] = v < 0 ? v + g.n[mu] : (v >= g.n[mu] ? v - g.n[mu] : v);
+    return eo_index(g, d);
+}
+
+template <typename T>
+__device__ __forceinline__ void load_link(const cplx<T>* __restrict__ U, const Geom& g, int mu, int p, int s,
+                                          cplx<T>* m) {
+#pragma unroll
+    for (int e = 0; e < 9; ++e) m[e] = U[lidx(g, mu, p, e, s)];
+}
+template <typename T>
+__device__ __forceinline__ void store_link(cplx<T>* __restrict__ U, const Geom& g, int mu, int p, int s,
+                                           const cplx<T>* m) {
+#pragma unroll
+    for (int e = 0; e < 9; ++e) U[lidx(g, mu, p, e, s)] = m[e];
+}
+
+// ---------------------------------------------------------------------------
+// reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum (deterministic for a fixed block size); result valid in
+// thread 0.  scratch must hold blockDim.x/32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* scratch) {
+    v = warp_sum(v);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) scratch[w] = v;
+    __syncthreads();
+    double r = 0;
+    if (threadIdx.x == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        for (int k = 0; k < nw; ++k) r += scratch[k];
+    }
+    __syncthreads();
+    return r;
+}
+
+}  // namespace mcg

@@ -1,0 +1,549 @@
+// Field-level kernels: layout conversion, gauge transforms, re-unitarisation,
+// plaquette, the MCG functional, Z3 center projection and P-vortex counting.
+// All are HBM-bound streaming kernels (one thread per site of one parity).
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "mcg_common.cuh"
+#include "mcg_internal.h"
+
+namespace mcg {
+
+constexpr int FT = 256;  // threads per block for the streaming kernels
+
+static inline int blocks_for(long long n, int nt) { return (int)((n + nt - 1) / nt); }
+
+// ---------------------------------------------------------------------------
+// canonical <-> SoA
+// ---------------------------------------------------------------------------
+// thread per (field, site lexicographic i); canonical complex128 U[i][mu][e]
+template <typename T>
+__global__ void k_pack_links(const double2* __restrict__ canon, cplx<T>* __restrict__ U, Geom g, int nfields) {
+    const long long V = 2LL * g.vh;
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= V * nfields) return;
+    const int f = (int)(id / V);
+    const int i = (int)(id - (long long)f * V);
+    int c[4];
+    int r = i;
+    c[0] = r % g.n[0];
+    r /= g.n[0];
+    c[1] = r % g.n[1];
+    r /= g.n[1];
+    c[2] = r % g.n[2];
+    c[3] = r / g.n[2];
+    const int p = (c[0] + c[1] + c[2] + c[3]) & 1, s = i >> 1;
+    const double2* src = canon + ((size_t)f * V + i) * 36;
+    cplx<T>* dst = U + (size_t)f * link_elems(g);
+    for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+            const double2 v = src[mu * 9 + e];
+            dst[lidx(g, mu, p, e, s)] = mk((T)v.x, (T)v.y);
+        }
+}
+
+template <typename T>
+__global__ void k_unpack_links(const cplx<T>* __restrict__ U, double2* __restrict__ canon, Geom g, int nfields) {
+    const long long V = 2LL * g.vh;
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= V * nfields) return;
+    const int f = (int)(id / V);
+    const int i = (int)(id - (long long)f * V);
+    int c[4];
+    int r = i;
+    c[0] = r % g.n[0];
+    r /= g.n[0];
+    c[1] = r % g.n[1];
+    r /= g.n[1];
+    c[2] = r % g.n[2];
+    c[3] = r / g.n[2];
+    const int p = (c[0] + c[1] + c[2] + c[3]) & 1, s = i >> 1;
+    double2* dst = canon + ((size_t)f * V + i) * 36;
+    const cplx<T>* src = U + (size_t)f * link_elems(g);
+    for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+            const cplx<T> v = src[lidx(g, mu, p, e, s)];
+            dst[mu * 9 + e] = make_double2((double)v.x, (double)v.y);
+        }
+}
+
+template <typename T>
+__global__ void k_pack_gauge(const double2* __restrict__ canon, cplx<T>* __restrict__ G, Geom g, int nfields,
+                             int unpack) {
+    const long long V = 2LL * g.vh;
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= V * nfields) return;
+    const int f = (int)(id / V);
+    const int i = (int)(id - (long long)f * V);
+    int c[4];
+    int r = i;
+    c[0] = r % g.n[0];
+    r /= g.n[0];
+    c[1] = r % g.n[1];
+    r /= g.n[1];
+    c[2] = r % g.n[2];
+    c[3] = r / g.n[2];
+    const int p = (c[0] + c[1] + c[2] + c[3]) & 1, s = i >> 1;
+    double2* cn = const_cast<double2*>(canon) + ((size_t)f * V + i) * 9;
+    cplx<T>* so = G + (size_t)f * gauge_elems(g);
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+        if (unpack) {
+            const cplx<T> v = so[gidx(g, p, e, s)];
+            cn[e] = make_double2((double)v.x, (double)v.y);
+        } else {
+            const double2 v = cn[e];
+            so[gidx(g, p, e, s)] = mk((T)v.x, (T)v.y);
+        }
+    }
+}
+
+__global__ void k_unpack_center(const int8_t* __restrict__ Z, int8_t* __restrict__ canon, Geom g, int nfields) {
+    const long long V = 2LL * g.vh;
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= V * nfields) return;
+    const int f = (int)(id / V);
+    const int i = (int)(id - (long long)f * V);
+    int c[4];
+    int r = i;
+    c[0] = r % g.n[0];
+    r /= g.n[0];
+    c[1] = r % g.n[1];
+    r /= g.n[1];
+    c[2] = r % g.n[2];
+    c[3] = r / g.n[2];
+    const int p = (c[0] + c[1] + c[2] + c[3]) & 1, s = i >> 1;
+    for (int mu = 0; mu < 4; ++mu) canon[((size_t)f * V + i) * 4 + mu] = Z[(size_t)f * 8 * g.vh + (size_t)(mu * 2 + p) * g.vh + s];
+}
+
+template <typename TS, typename TD>
+__global__ void k_convert(const cplx<TS>* __restrict__ src, cplx<TD>* __restrict__ dst, size_t n) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const cplx<TS> v = src[k];
+        dst[k] = mk((TD)v.x, (TD)v.y);
+    }
+}
+
+template <typename T>
+__global__ void k_identity_gauge(cplx<T>* __restrict__ G, Geom g, int nfields) {
+    const long long n = (long long)g.vh * nfields;
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n) return;
+    const int f = (int)(id / g.vh), s = (int)(id - (long long)f * g.vh);
+    cplx<T>* Gf = G + (size_t)f * gauge_elems(g);
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int e = 0; e < 9; ++e) Gf[gidx(g, p, e, s)] = mk((T)((e % 4) == 0 ? 1 : 0), (T)0);
+}
+
+// ---------------------------------------------------------------------------
+// gauge transform, in place: U_mu(x) <- Omega(x) U_mu(x) Omega(x+mu)^dag
+// thread per (field, parity, site)
+// ---------------------------------------------------------------------------
+template <typename TU, typename TG>
+__device__ __forceinline__ void apply_site(cplx<TU>* __restrict__ U, const cplx<TG>* __restrict__ G, const Geom& g,
+                                           int p, int s) {
+    int c[4];
+    eo_coords(g, p, s, c);
+    cplx<double> Om[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+        const cplx<TG> v = G[gidx(g, p, e, s)];
+        Om[e] = mk((double)v.x, (double)v.y);
+    }
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        const int sf = eo_neighbor(g, c, mu, +1);
+        cplx<double> u[9], on[9], t[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+            const cplx<TU> v = U[lidx(g, mu, p, e, s)];
+            u[e] = mk((double)v.x, (double)v.y);
+            const cplx<TG> w = G[gidx(g, p ^ 1, e, sf)];
+            on[e] = mk((double)w.x, (double)w.y);
+        }
+        m3_mul(Om, u, t);
+        m3_mul_nd(t, on, u);
+#pragma unroll
+        for (int e = 0; e < 9; ++e) U[lidx(g, mu, p, e, s)] = mk((TU)u[e].x, (TU)u[e].y);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FT) k_apply_gauge(cplx<T>* __restrict__ U, const cplx<T>* __restrict__ G, Geom g,
+                                                     int nfields) {
+    const long long n = 2LL * g.vh * nfields;
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n) return;
+    const int f = (int)(id / (2LL * g.vh));
+    const int r = (int)(id - (long long)f * 2 * g.vh);
+    const int p = r / g.vh, s = r - p * g.vh;
+    apply_site<T, T>(U + (size_t)f * link_elems(g), G + (size_t)f * gauge_elems(g), g, p, s);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FT) k_reunit_all(cplx<T>* __restrict__ M, int per_site, Geom g, int nfields) {
+    // per_site = 4 (links) or 1 (gauge): matrices of one site-parity slot
+    const long long n = 2LL * g.vh * nfields;
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n) return;
+    const int f = (int)(id / (2LL * g.vh));
+    const int r = (int)(id - (long long)f * 2 * g.vh);
+    const int p = r / g.vh, s = r - p * g.vh;
+    cplx<T>* Mf = M + (size_t)f * (per_site == 4 ? link_elems(g) : gauge_elems(g));
+    for (int mu = 0; mu < per_site; ++mu) {
+        cplx<T> m[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) m[e] = Mf[((size_t)((mu * 2 + p) * 9 + e)) * g.vh + s];
+        m3_reunitarise(m);
+#pragma unroll
+        for (int e = 0; e < 9; ++e) Mf[((size_t)((mu * 2 + p) * 9 + e)) * g.vh + s] = m[e];
+    }
+}
+
+// Mixed-precision hand-off, pass 1: W64 = reunit(W32) written to scratch,
+// G64 <- reunit(W64 G64).
+__global__ void __launch_bounds__(FT) k_handoff_gauge(const cplx<float>* __restrict__ W, cplx<double>* __restrict__ W64,
+                                                      cplx<double>* __restrict__ G, Geom g, int nfields) {
+    const long long n = 2LL * g.vh * nfields;
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n) return;
+    const int f = (int)(id / (2LL * g.vh));
+    const int r = (int)(id - (long long)f * 2 * g.vh);
+    const int p = r / g.vh, s = r - p * g.vh;
+    const size_t off = (size_t)f * gauge_elems(g);
+    cplx<double> w[9], o[9], t[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+        const cplx<float> v = W[off + gidx(g, p, e, s)];
+        w[e] = mk((double)v.x, (double)v.y);
+        o[e] = G[off + gidx(g, p, e, s)];
+    }
+    m3_reunitarise(w);
+    m3_mul(w, o, t);
+    m3_reunitarise(t);
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+        W64[off + gidx(g, p, e, s)] = w[e];
+        G[off + gidx(g, p, e, s)] = t[e];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// plaquette and functional: per-field sums via per-block partials
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(FT) k_plaquette(const cplx<T>* __restrict__ U, Geom g, int bpf,
+                                                  double* __restrict__ partial) {
+    const int f = blockIdx.x / bpf;
+    const int s2 = (blockIdx.x - f * bpf) * FT + threadIdx.x;  // 0 .. 2*vh-1
+    const cplx<T>* Uf = U + (size_t)f * link_elems(g);
+    double acc = 0.0;
+    if (s2 < 2 * g.vh) {
+        const int p = s2 / g.vh, s = s2 - p * g.vh;
+        int c[4];
+        eo_coords(g, p, s, c);
+        for (int mu = 0; mu < 4; ++mu) {
+            const int smu = eo_neighbor(g, c, mu, +1);
+            cplx<double> a[9], t[9];
+#pragma unroll
+            for (int e = 0; e < 9; ++e) {
+                const cplx<T> v = Uf[lidx(g, mu, p, e, s)];
+                a[e] = mk((double)v.x, (double)v.y);
+            }
+            for (int nu = mu + 1; nu < 4; ++nu) {
+                const int snu = eo_neighbor(g, c, nu, +1);
+                cplx<double> b[9], m[9], q[9];
+#pragma unroll
+                for (int e = 0; e < 9; ++e) {
+                    const cplx<T> v = Uf[lidx(g, nu, p ^ 1, e, smu)];
+                    b[e] = mk((double)v.x, (double)v.y);
+                }
+                m3_mul(a, b, t);  // U_mu(x) U_nu(x+mu)
+#pragma unroll
+                for (int e = 0; e < 9; ++e) {
+                    const cplx<T> v = Uf[lidx(g, mu, p ^ 1, e, snu)];
+                    m[e] = mk((double)v.x, (double)v.y);
+                }
+                m3_mul_nd(t, m, q);  // ... U_mu(x+nu)^dag
+#pragma unroll
+                for (int e = 0; e < 9; ++e) {
+                    const cplx<T> v = Uf[lidx(g, nu, p, e, s)];
+                    m[e] = mk((double)v.x, (double)v.y);
+                }
+                // Re tr(q m^dag) = sum_ij Re(q_ij conj(m_ij))
+                double tr = 0.0;
+#pragma unroll
+                for (int e = 0; e < 9; ++e) tr += q[e].x * m[e].x + q[e].y * m[e].y;
+                acc += tr / 3.0;
+            }
+        }
+    }
+    __shared__ double red[FT / 32];
+    const double tot = block_sum(acc, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FT) k_functional_all(const cplx<T>* __restrict__ U, Geom g, int bpf,
+                                                       double* __restrict__ partial) {
+    const int f = blockIdx.x / bpf;
+    const int s2 = (blockIdx.x - f * bpf) * FT + threadIdx.x;
+    const cplx<T>* Uf = U + (size_t)f * link_elems(g);
+    double acc = 0.0;
+    if (s2 < 2 * g.vh) {
+        const int p = s2 / g.vh, s = s2 - p * g.vh;
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            const cplx<T> a = Uf[lidx(g, mu, p, 0, s)], b = Uf[lidx(g, mu, p, 4, s)], c = Uf[lidx(g, mu, p, 8, s)];
+            const double tr = (double)(a.x + b.x + c.x), ti = (double)(a.y + b.y + c.y);
+            acc += tr * tr + ti * ti;
+        }
+    }
+    __shared__ double red[FT / 32];
+    const double tot = block_sum(acc, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+__global__ void k_sum_partials(const double* __restrict__ partial, int bpf, double* __restrict__ out) {
+    const int f = blockIdx.x;
+    double v = 0.0;
+    for (int k = threadIdx.x; k < bpf; k += blockDim.x) v += partial[(size_t)f * bpf + k];
+    __shared__ double red[8];
+    const double tot = block_sum(v, red);
+    if (threadIdx.x == 0) out[f] = tot;
+}
+
+// ---------------------------------------------------------------------------
+// center projection (decision in FP64, exact comparisons) and vortex counting
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(FT) k_center_project(const cplx<T>* __restrict__ U, int8_t* __restrict__ Z, Geom g,
+                                                       int nfields) {
+    const long long n = 2LL * g.vh * nfields;
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n) return;
+    const int f = (int)(id / (2LL * g.vh));
+    const int r = (int)(id - (long long)f * 2 * g.vh);
+    const int p = r / g.vh, s = r - p * g.vh;
+    const cplx<T>* Uf = U + (size_t)f * link_elems(g);
+    int8_t* Zf = Z + (size_t)f * 8 * g.vh;
+    const double sqrt3 = 1.7320508075688772;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        const cplx<T> a = Uf[lidx(g, mu, p, 0, s)], b = Uf[lidx(g, mu, p, 4, s)], c = Uf[lidx(g, mu, p, 8, s)];
+        const double re = __dadd_rn(__dadd_rn((double)a.x, (double)b.x), (double)c.x);
+        const double im = __dadd_rn(__dadd_rn((double)a.y, (double)b.y), (double)c.y);
+        const double lim = __dmul_rn(sqrt3, re);
+        int8_t m;
+        if (re >= 0.0 && fabs(im) <= lim)
+            m = 0;
+        else if (im >= 0.0)
+            m = 1;
+        else
+            m = -1;
+        Zf[(size_t)(mu * 2 + p) * g.vh + s] = m;
+    }
+}
+
+// per (field, parity, site): 6 plaquettes; counts[f*7 + 1 + plane]
+__global__ void __launch_bounds__(FT) k_vortex_count(const int8_t* __restrict__ Z, Geom g, int nfields,
+                                                     unsigned long long* __restrict__ counts) {
+    const long long n = 2LL * g.vh * nfields;
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int cnt[6] = {0, 0, 0, 0, 0, 0};
+    int f = 0;
+    if (id < n) {
+        f = (int)(id / (2LL * g.vh));
+        const int r = (int)(id - (long long)f * 2 * g.vh);
+        const int p = r / g.vh, s = r - p * g.vh;
+        const int8_t* Zf = Z + (size_t)f * 8 * g.vh;
+        int c[4];
+        eo_coords(g, p, s, c);
+        int pl = 0;
+        for (int mu = 0; mu < 4; ++mu) {
+            const int smu = eo_neighbor(g, c, mu, +1);
+            for (int nu = mu + 1; nu < 4; ++nu, ++pl) {
+                const int snu = eo_neighbor(g, c, nu, +1);
+                const int v = Zf[(size_t)(mu * 2 + p) * g.vh + s] + Zf[(size_t)(nu * 2 + (p ^ 1)) * g.vh + smu] -
+                              Zf[(size_t)(mu * 2 + (p ^ 1)) * g.vh + snu] - Zf[(size_t)(nu * 2 + p) * g.vh + s];
+                cnt[pl] = (((v % 3) + 3) % 3) != 0;
+            }
+        }
+    }
+    // a block may straddle two fields only at field boundaries: reduce per warp
+    // on the warp's first field and fall back to per-thread atomics otherwise
+    const int f0 = __shfl_sync(0xffffffffu, f, 0);
+    const bool uniform = __all_sync(0xffffffffu, f == f0 || id >= n);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        if (uniform) {
+            const int w = __reduce_add_sync(0xffffffffu, cnt[k]);
+            if ((threadIdx.x & 31) == 0 && w) atomicAdd(&counts[(size_t)f0 * 7 + 1 + k], (unsigned long long)w);
+        } else if (cnt[k]) {
+            atomicAdd(&counts[(size_t)f * 7 + 1 + k], 1ULL);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+int launch_convert(const void* src, int sp, void* dst, int dp, size_t n, cudaStream_t st) {
+    const int nb = (int)std::min<size_t>((n + FT - 1) / FT, 152 * 64);
+    if (n == 0) return 0;
+    if (sp == MCG_F64 && dp == MCG_F32)
+        k_convert<double, float><<<nb, FT, 0, st>>>((const cplx<double>*)src, (cplx<float>*)dst, n);
+    else if (sp == MCG_F32 && dp == MCG_F64)
+        k_convert<float, double><<<nb, FT, 0, st>>>((const cplx<float>*)src, (cplx<double>*)dst, n);
+    else if (sp == MCG_F64)
+        k_convert<double, double><<<nb, FT, 0, st>>>((const cplx<double>*)src, (cplx<double>*)dst, n);
+    else
+        k_convert<float, float><<<nb, FT, 0, st>>>((const cplx<float>*)src, (cplx<float>*)dst, n);
+    MCG_CK(cudaGetLastError());
+    return 0;
+}
+
+int launch_pack(const double* canon, void* soa, int prec, const Geom& g, int nfields, int what, int unpack,
+                cudaStream_t st) {
+    const long long n = 2LL * g.vh * nfields;
+    const int nb = blocks_for(n, FT);
+    if (what == 0) {
+        if (!unpack) {
+            if (prec == MCG_F64)
+                k_pack_links<double><<<nb, FT, 0, st>>>((const double2*)canon, (cplx<double>*)soa, g, nfields);
+            else
+                k_pack_links<float><<<nb, FT, 0, st>>>((const double2*)canon, (cplx<float>*)soa, g, nfields);
+        } else {
+            if (prec == MCG_F64)
+                k_unpack_links<double><<<nb, FT, 0, st>>>((const cplx<double>*)soa, (double2*)canon, g, nfields);
+            else
+                k_unpack_links<float><<<nb, FT, 0, st>>>((const cplx<float>*)soa, (double2*)canon, g, nfields);
+        }
+    } else {
+        if (prec == MCG_F64)
+            k_pack_gauge<double><<<nb, FT, 0, st>>>((const double2*)canon, (cplx<double>*)soa, g, nfields, unpack);
+        else
+            k_pack_gauge<float><<<nb, FT, 0, st>>>((const double2*)canon, (cplx<float>*)soa, g, nfields, unpack);
+    }
+    MCG_CK(cudaGetLastError());
+    return 0;
+}
+
+int launch_unpack_center(const int8_t* Z, int8_t* canon, const Geom& g, int nfields, cudaStream_t st) {
+    const long long n = 2LL * g.vh * nfields;
+    k_unpack_center<<<blocks_for(n, FT), FT, 0, st>>>(Z, canon, g, nfields);
+    MCG_CK(cudaGetLastError());
+    return 0;
+}
+
+int launch_identity_gauge(void* G, int prec, const Geom& g, int nfields, cudaStream_t st) {
+    const long long n = (long long)g.vh * nfields;
+    if (prec == MCG_F64)
+        k_identity_gauge<double><<<blocks_for(n, FT), FT, 0, st>>>((cplx<double>*)G, g, nfields);
+    else
+        k_identity_gauge<float><<<blocks_for(n, FT), FT, 0, st>>>((cplx<float>*)G, g, nfields);
+    MCG_CK(cudaGetLastError());
+    return 0;
+}
+
+int launch_apply_gauge(void* U, const void* G, int prec, const Geom& g, int nfields, cudaStream_t st) {
+    const long long n = 2LL * g.vh * nfields;
+    if (prec == MCG_F64)
+        k_apply_gauge<double><<<blocks_for(n, FT), FT, 0, st>>>((cplx<double>*)U, (const cplx<double>*)G, g, nfields);
+    else
+        k_apply_gauge<float><<<blocks_for(n, FT), FT, 0, st>>>((cplx<float>*)U, (const cplx<float>*)G, g, nfields);
+    MCG_CK(cudaGetLastError());
+    return 0;
+}
+
+int launch_reunitarise(void* M, int which, int prec, const Geom& g, int nfields, cudaStream_t st) {
+    const long long n = 2LL * g.vh * nfields;
+    const int per = which == 0 ? 4 : 1;
+    if (prec == MCG_F64)
+        k_reunit_all<double><<<blocks_for(n, FT), FT, 0, st>>>((cplx<double>*)M, per, g, nfields);
+    else
+        k_reunit_all<float><<<blocks_for(n, FT), FT, 0, st>>>((cplx<float>*)M, per, g, nfields);
+    MCG_CK(cudaGetLastError());
+    return 0;
+}
+
+static int reduce_per_field(int which, const void* U, int prec, const Geom& g, int nfields, double* out_host,
+                            cudaStream_t st) {
+    const int bpf = blocks_for(2LL * g.vh, FT);
+    int rc = 0;
+    double* partial = (double*)scratch_device("obs.partial", sizeof(double) * (size_t)bpf * nfields, &rc);
+    if (rc) return rc;
+    double* d_out = (double*)scratch_device("obs.out", sizeof(double) * nfields, &rc);
+    if (rc) return rc;
+    const int nb = bpf * nfields;
+    if (which == 0) {
+        if (prec == MCG_F64)
+            k_plaquette<double><<<nb, FT, 0, st>>>((const cplx<double>*)U, g, bpf, partial);
+        else
+            k_plaquette<float><<<nb, FT, 0, st>>>((const cplx<float>*)U, g, bpf, partial);
+    } else {
+        if (prec == MCG_F64)
+            k_functional_all<double><<<nb, FT, 0, st>>>((const cplx<double>*)U, g, bpf, partial);
+        else
+            k_functional_all<float><<<nb, FT, 0, st>>>((const cplx<float>*)U, g, bpf, partial);
+    }
+    k_sum_partials<<<nfields, 256, 0, st>>>(partial, bpf, d_out);
+    MCG_CK(cudaGetLastError());
+    MCG_CK(cudaMemcpyAsync(out_host, d_out, sizeof(double) * nfields, cudaMemcpyDeviceToHost, st));
+    MCG_CK(cudaStreamSynchronize(st));
+    if (which == 0)
+        for (int f = 0; f < nfields; ++f) out_host[f] /= 6.0 * 2.0 * g.vh;
+    return 0;
+}
+
+int compute_plaquette(const void* U, int prec, const Geom& g, int nfields, double* out_host, cudaStream_t st) {
+    return reduce_per_field(0, U, prec, g, nfields, out_host, st);
+}
+
+int compute_functional(const void* U, int prec, const Geom& g, int nfields, double* out_host, cudaStream_t st) {
+    return reduce_per_field(1, U, prec, g, nfields, out_host, st);
+}
+
+int compute_center(const void* U, int prec, int8_t* Z, const Geom& g, int nfields, long long* counts_host,
+                   cudaStream_t st) {
+    int rc = 0;
+    unsigned long long* d_counts =
+        (unsigned long long*)scratch_device("center.counts", sizeof(unsigned long long) * 7 * nfields, &rc);
+    if (rc) return rc;
+    const long long n = 2LL * g.vh * nfields;
+    if (prec == MCG_F64)
+        k_center_project<double><<<blocks_for(n, FT), FT, 0, st>>>((const cplx<double>*)U, Z, g, nfields);
+    else
+        k_center_project<float><<<blocks_for(n, FT), FT, 0, st>>>((const cplx<float>*)U, Z, g, nfields);
+    MCG_CK(cudaMemsetAsync(d_counts, 0, sizeof(unsigned long long) * 7 * nfields, st));
+    k_vortex_count<<<blocks_for(n, FT), FT, 0, st>>>(Z, g, nfields, d_counts);
+    MCG_CK(cudaGetLastError());
+    if (counts_host) {
+        MCG_CK(cudaMemcpyAsync(counts_host, d_counts, sizeof(long long) * 7 * nfields, cudaMemcpyDeviceToHost, st));
+        MCG_CK(cudaStreamSynchronize(st));
+        for (int f = 0; f < nfields; ++f) {
+            long long t = 0;
+            for (int k = 1; k < 7; ++k) t += counts_host[f * 7 + k];
+            counts_host[f * 7] = t;
+        }
+    }
+    return 0;
+}
+
+int launch_handoff(const void* W32, double* U64, double* G64, const Geom& g, int nfields, cudaStream_t st) {
+    int rc = 0;
+    cplx<double>* W64 =
+        (cplx<double>*)scratch_device("handoff.W64", sizeof(cplx<double>) * gauge_elems(g) * nfields, &rc);
+    if (rc) return rc;
+    const long long n = 2LL * g.vh * nfields;
+    k_handoff_gauge<<<blocks_for(n, FT), FT, 0, st>>>((const cplx<float>*)W32, W64, (cplx<double>*)G64, g, nfields);
+    k_apply_gauge<double><<<blocks_for(n, FT), FT, 0, st>>>((cplx<double>*)U64, W64, g, nfields);
+    MCG_CK(cudaGetLastError());
+    return 0;
+}
+
+}  // namespace mcg

@@ -1,0 +1,97 @@
+// Host-side internals shared by the libmcg translation units (not part of the
+// public C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "mcg_common.cuh"
+
+namespace mcg {
+
+// ---- error reporting ------------------------------------------------------
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define MCG_CK(call)                                          \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return ::mcg::cuda_fail(e_, #call); \
+    } while (0)
+
+// ---- scratch ----------------------------------------------------------------
+// Named, grow-only device and pinned-host buffers cached per device; freed by
+// mcg_release().
+void* scratch_device(const char* name, size_t bytes, int* rc);
+void* scratch_host(const char* name, size_t bytes, int* rc);
+cudaStream_t capture_stream(int* rc);
+void release_all();
+
+// ---- batched sweep machinery -------------------------------------------------
+struct FieldDesc {
+    void* U;      // links, precision of the sweep kernel
+    void* G;      // gauge transform, same precision
+    Geom geo;
+    int blk0;     // first block of this field in the flattened grid
+    int nblk;     // blocks of this field
+    double norm;  // 1 / (9 * 4V)
+};
+
+struct FieldState {
+    double R_prev;  // R after the previous sweep (or at phase start)
+    double R_last;  // R after the last sweep
+    int sweep;      // sweeps completed (across phases)
+    int done;       // 0 running, 1 converged, 2 sweep cap of the phase reached
+    int reunit_pending;
+    int max_sweeps;  // absolute sweep cap of the current phase
+    int fallbacks;   // local solves that needed the FP64 fallback path
+    int pad;
+};
+
+struct SweepBatch {
+    const FieldDesc* desc;
+    int nf;
+    int total_blocks;
+    FieldState* state;
+    double* partial;  // one per block
+    double* R_hist;   // nf x hist_len (may be null)
+    int hist_len;
+    double tol;
+    int reunit_every;
+};
+
+// Run MCG relaxation on a batch (all fields same precision T) until every
+// field is done: converged (dV_U < tol) or at abs_cap sweeps counted from the
+// start of the history.  `fresh`: start a new history (sweep = 0); otherwise
+// continue the sweep count in `state` (a new phase).  Returns 0 or an error.
+template <typename T>
+int run_fix_phase(const std::vector<FieldDesc>& fields, FieldState* d_state, FieldState* h_state, double* d_hist,
+                  int hist_len, double tol, int reunit_every, int abs_cap, int check_every, bool fresh,
+                  cudaStream_t stream);
+
+template <typename T>
+constexpr int sweep_threads() {
+    return sizeof(T) == 8 ? 64 : 128;
+}
+
+// ---- field kernels (mcg_field.cu) -------------------------------------------
+int launch_convert(const void* src, int src_prec, void* dst, int dst_prec, size_t n, cudaStream_t st);
+int launch_identity_gauge(void* G, int prec, const Geom& g, int nfields, cudaStream_t st);
+int launch_apply_gauge(void* U, const void* G, int prec, const Geom& g, int nfields, cudaStream_t st);
+int launch_reunitarise(void* M, int which, int prec, const Geom& g, int nfields, cudaStream_t st);
+int compute_plaquette(const void* U, int prec, const Geom& g, int nfields, double* out_host, cudaStream_t st);
+int compute_functional(const void* U, int prec, const Geom& g, int nfields, double* out_host, cudaStream_t st);
+int compute_center(const void* U, int prec, int8_t* Z, const Geom& g, int nfields, long long* counts_host,
+                   cudaStream_t st);
+// FP32 transform W (of this call) -> FP64: W64 = reunit(W); U64 <- W64 U64 W64(x+mu)^dag;
+// G64 <- reunit(W64 G64).
+int launch_handoff(const void* W32, double* U64, double* G64, const Geom& g, int nfields, cudaStream_t st);
+
+// ---- smearing (mcg_smear.cu) ------------------------------------------------
+int run_smear(const void* Uin, void* Uout, int prec, const Geom& g, int nfields, double rho, double eps, int n,
+              cudaStream_t st);
+
+}  // namespace mcg

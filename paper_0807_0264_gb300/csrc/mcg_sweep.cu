@@ -1,0 +1,718 @@
+// MCG relaxation on sm_103a: the checkerboard half-sweep kernel, the fused R
+// reduction, per-field convergence control and the graph-captured sweep loop.
+//
+// Site update (Sec. II.A, MCG functional R = sum |tr U|^2; the update rule
+// itself is the exact SU(2)-subgroup maximisation over subgroups (0,1),
+// (0,2), (1,2)): for subgroup (p,q) the 8 links at x give
+//   tr(G U_mu(x))        = c + w . a
+//   tr(U_mu(x-mu) G^dag) = c + w' . a   (a_1..a_3 enter with a minus sign)
+// for G the embedding of g = a0 + i a.sigma, so the local functional is
+// a^T A a + 2 b.a + const with A = sum Re(conj(w) w^T), b = sum Re(conj(c) w),
+// maximised on |a| = 1 (a trust-region subproblem: (mu - A) a = b with
+// mu >= lambda_max(A)).
+//
+// Precision: the FP32 kernel does everything in FP32 (R accumulated in FP64).
+// The FP64 kernel builds A, b and applies G in FP64; the 4x4 solve is seeded
+// by an FP32 Jacobi eigen-decomposition + secular Newton and then refined to
+// FP64 accuracy by Newton steps on the KKT system whose residual is evaluated
+// in FP64 (the FP32 eigen-decomposition serves as the approximate inverse).
+// Solves the refinement cannot settle (near-degenerate or hard cases) rerun
+// in full FP64.  FP64 arithmetic is scarce on GB300, so the expensive part of
+// the solve stays on the FP32 pipe.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "mcg_common.cuh"
+#include "mcg_internal.h"
+
+namespace mcg {
+
+// ---------------------------------------------------------------------------
+// 4x4 symmetric eigen-decomposition (cyclic Jacobi)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float frcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
+
+template <typename T, int P, int Q>
+__device__ __forceinline__ void jrot(T (&S)[4][4], T (&V)[4][4]) {
+    const T apq = S[P][Q];
+    const T th = (S[Q][Q] - S[P][P]) * T(0.5);
+    const T den = fabs(th) + sqrt(th * th + apq * apq);
+    T t = den > T(0) ? apq * frcp(den) : T(0);
+    if (th < T(0)) t = -t;
+    const T c = rsqrt(T(1) + t * t);
+    const T s = t * c;
+    S[P][P] -= t * apq;
+    S[Q][Q] += t * apq;
+    S[P][Q] = T(0);
+    S[Q][P] = T(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (k == P || k == Q) continue;
+        const T akp = S[k][P], akq = S[k][Q];
+        const T np = c * akp - s * akq, nq = s * akp + c * akq;
+        S[k][P] = np;
+        S[P][k] = np;
+        S[k][Q] = nq;
+        S[Q][k] = nq;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const T vkp = V[k][P], vkq = V[k][Q];
+        V[k][P] = c * vkp - s * vkq;
+        V[k][Q] = s * vkp + c * vkq;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void jacobi4(T (&S)[4][4], T (&V)[4][4], int max_sweeps, T rel_tol) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) V[i][j] = (i == j) ? T(1) : T(0);
+    T fro2 = T(0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) fro2 += S[i][j] * S[i][j];
+    for (int sw = 0; sw < max_sweeps; ++sw) {
+        const T off = S[0][1] * S[0][1] + S[0][2] * S[0][2] + S[0][3] * S[0][3] + S[1][2] * S[1][2] +
+                      S[1][3] * S[1][3] + S[2][3] * S[2][3];
+        if (off <= rel_tol * rel_tol * fro2) break;
+        jrot<T, 0, 1>(S, V);
+        jrot<T, 0, 2>(S, V);
+        jrot<T, 0, 3>(S, V);
+        jrot<T, 1, 2>(S, V);
+        jrot<T, 1, 3>(S, V);
+        jrot<T, 2, 3>(S, V);
+    }
+}
+
+// Trust-region maximiser from the eigen-decomposition (al, V columns).
+// Returns 0 easy case, 1 hard case.  mu_out is the multiplier.
+template <typename T>
+__device__ __forceinline__ int trs_from_eigen(const T (&S)[4][4], const T (&V)[4][4], const T (&b)[4], T (&a)[4],
+                                              T& mu_out) {
+    const T eps = sizeof(T) == 8 ? T(2.2e-16) : T(1.2e-7);
+    const T deg_tol = sizeof(T) == 8 ? T(1e-13) : T(1e-5);
+    const T hard_tol = sizeof(T) == 8 ? T(1e-14) : T(1e-6);
+    T al[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) al[i] = S[i][i];
+    const T bn = sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2] + b[3] * b[3]);
+    T scale = bn;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) scale = fmax(scale, fabs(al[i]));
+    if (scale == T(0)) {
+        a[0] = T(1);
+        a[1] = a[2] = a[3] = T(0);
+        mu_out = T(0);
+        return 1;
+    }
+    T amax = al[0];
+    int imax = 0;
+#pragma unroll
+    for (int i = 1; i < 4; ++i)
+        if (al[i] > amax) {
+            amax = al[i];
+            imax = i;
+        }
+    T beta[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) beta[i] = V[0][i] * b[0] + V[1][i] * b[1] + V[2][i] * b[2] + V[3][i] * b[3];
+    T btop2 = T(0);
+    bool top[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        top[i] = (amax - al[i]) <= deg_tol * scale;
+        if (top[i]) btop2 += beta[i] * beta[i];
+    }
+    const T btop = sqrt(btop2);
+    if (btop <= hard_tol * scale) {
+        T coef[4], pn2 = T(0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            coef[i] = top[i] ? T(0) : beta[i] / (amax - al[i]);
+            pn2 += coef[i] * coef[i];
+        }
+        if (pn2 < T(1)) {
+            T vm[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                vm[k] = V[k][0];
+#pragma unroll
+                for (int i = 1; i < 4; ++i)
+                    if (i == imax) vm[k] = V[k][i];
+            }
+            int kb = 0;
+            T vb = fabs(vm[0]);
+#pragma unroll
+            for (int k = 1; k < 4; ++k)
+                if (fabs(vm[k]) > vb) {
+                    vb = fabs(vm[k]);
+                    kb = k;
+                }
+            T sgn = T(1);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (k == kb) sgn = vm[k] >= T(0) ? T(1) : T(-1);
+            const T t = sqrt(T(1) - pn2) * sgn;
+            T n2 = T(0);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                a[k] = V[k][0] * coef[0] + V[k][1] * coef[1] + V[k][2] * coef[2] + V[k][3] * coef[3] + t * vm[k];
+                n2 += a[k] * a[k];
+            }
+            const T inv = rsqrt(n2);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) a[k] *= inv;
+            mu_out = amax;
+            return 1;
+        }
+    }
+    // easy case: root of ||a(mu)|| = 1 right of amax, bracket [amax+btop, amax+||b||]
+    T lo = amax + btop, hi = amax + bn, mu = lo;
+    const int maxit = sizeof(T) == 8 ? 100 : 40;
+    for (int it = 0; it < maxit; ++it) {
+        T s2 = T(0), s3 = T(0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const T r = frcp(mu - al[i]);
+            const T q = beta[i] * beta[i] * r * r;
+            s2 += q;
+            s3 += q * r;
+        }
+        const T n = sqrt(s2);
+        if (n >= T(1))
+            lo = fmax(lo, mu);
+        else
+            hi = fmin(hi, mu);
+        T next = mu + (n - T(1)) * s2 / s3;
+        if (!(next > lo && next < hi)) next = T(0.5) * (lo + hi);
+        if (fabs(next - mu) <= eps * fabs(mu)) {
+            mu = next;
+            break;
+        }
+        mu = next;
+        if (hi - lo <= T(4) * eps * fabs(mu)) break;
+    }
+    T n2 = T(0);
+    T coef[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) coef[i] = beta[i] / (mu - al[i]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        a[k] = V[k][0] * coef[0] + V[k][1] * coef[1] + V[k][2] * coef[2] + V[k][3] * coef[3];
+        n2 += a[k] * a[k];
+    }
+    const T inv = rsqrt(n2);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a[k] *= inv;
+    mu_out = mu;
+    return 0;
+}
+
+// FP32 solve of the subproblem given A (symmetric) and b.
+__device__ __forceinline__ int solve_f32(const float (&A)[4][4], const float (&b)[4], float (&a)[4], float& mu,
+                                         float (&S)[4][4], float (&V)[4][4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) S[i][j] = A[i][j];
+    jacobi4<float>(S, V, 8, 1e-7f);
+    return trs_from_eigen<float>(S, V, b, a, mu);
+}
+
+// Newton refinement of (a, mu) on the KKT system (mu - A) a = b, |a| = 1 with
+// FP64 residuals and the FP32 eigen-decomposition as approximate inverse of
+// (mu - A).  Returns true when the last correction is below FP64 resolution.
+__device__ __forceinline__ bool kkt_refine(const double (&A)[4][4], const double (&b)[4], const float (&S)[4][4],
+                                           const float (&V)[4][4], double (&a)[4], double& mu) {
+    for (int it = 0; it < 6; ++it) {
+        double r[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            double acc = fma(-mu, a[k], b[k]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc = fma(A[k][j], a[j], acc);
+            r[k] = acc;
+        }
+        const double s = 0.5 * (1.0 - (a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]));
+        const float muf = (float)mu;
+        float rt[4], at[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float d = __frcp_rn(muf - S[i][i]);
+            rt[i] = (V[0][i] * (float)r[0] + V[1][i] * (float)r[1] + V[2][i] * (float)r[2] + V[3][i] * (float)r[3]) * d;
+            at[i] = (V[0][i] * (float)a[0] + V[1][i] * (float)a[1] + V[2][i] * (float)a[2] + V[3][i] * (float)a[3]) * d;
+        }
+        double x[4], y[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            x[k] = (double)(V[k][0] * rt[0] + V[k][1] * rt[1] + V[k][2] * rt[2] + V[k][3] * rt[3]);
+            y[k] = (double)(V[k][0] * at[0] + V[k][1] * at[1] + V[k][2] * at[2] + V[k][3] * at[3]);
+        }
+        const double ax = a[0] * x[0] + a[1] * x[1] + a[2] * x[2] + a[3] * x[3];
+        const double ay = a[0] * y[0] + a[1] * y[1] + a[2] * y[2] + a[3] * y[3];
+        const double dmu = (ax - s) / ay;
+        double dmax = 0.0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const double da = fma(-dmu, y[k], x[k]);
+            a[k] += da;
+            dmax = fmax(dmax, fabs(da));
+        }
+        mu += dmu;
+        if (!(dmax == dmax)) return false;  // NaN
+        if (dmax <= 1e-15) return true;
+    }
+    return false;
+}
+
+template <typename T>
+struct Solver;
+
+template <>
+struct Solver<float> {
+    __device__ __forceinline__ static int solve(const float (&A)[4][4], const float (&b)[4], float (&a)[4]) {
+        float S[4][4], V[4][4], mu;
+        solve_f32(A, b, a, mu, S, V);
+        return 0;
+    }
+};
+
+template <>
+struct Solver<double> {
+    // returns 1 when the full FP64 fallback was used
+    __device__ __forceinline__ static int solve(const double (&A)[4][4], const double (&b)[4], double (&a)[4]) {
+        float Af[4][4], bf[4], af[4], S[4][4], V[4][4], muf;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            bf[i] = (float)b[i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) Af[i][j] = (float)A[i][j];
+        }
+        const int hard = solve_f32(Af, bf, af, muf, S, V);
+        bool ok = false;
+        if (!hard) {
+            // conditioning of (mu - A) in FP32 terms: refinement contracts by ~cond * 1e-7
+            float amax = S[0][0], amin = S[0][0];
+#pragma unroll
+            for (int i = 1; i < 4; ++i) {
+                amax = fmaxf(amax, S[i][i]);
+                amin = fminf(amin, S[i][i]);
+            }
+            const float gap = muf - amax;
+            if (gap > 2e-4f * (muf - amin + 1e-30f)) {
+                double mu = (double)muf;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) a[k] = (double)af[k];
+                ok = kkt_refine(A, b, S, V, a, mu);
+            }
+        }
+        if (!ok) {
+            double Sd[4][4], Vd[4][4], mud;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) Sd[i][j] = A[i][j];
+            jacobi4<double>(Sd, Vd, 30, 1e-15);
+            trs_from_eigen<double>(Sd, Vd, b, a, mud);
+            return 1;
+        }
+        const double inv = rsqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a[k] *= inv;
+        return 0;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// link storage for one site's 8 links: registers (FP32) or shared memory (FP64)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct RegLinks {
+    cplx<T> v[8][9];
+    __device__ __forceinline__ cplx<T>& operator()(int l, int e) { return v[l][e]; }
+};
+
+template <typename T, int NT>
+struct SmemLinks {
+    cplx<T>* base;
+    __device__ __forceinline__ cplx<T>& operator()(int l, int e) { return base[(l * 9 + e) * NT + threadIdx.x]; }
+};
+
+// One SU(2)-subgroup step on the 8 links (l < 4: forward U_l(x), l >= 4:
+// backward U_{l-4}(x - l)) and Omega(x).  Returns fallback count.
+template <typename T, int P, int Q, int R, typename L>
+__device__ __forceinline__ int subgroup_step(L& lk, cplx<T> (&Om)[9]) {
+    T A[4][4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        b[i] = T(0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) A[i][j] = T(0);
+    }
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+        const cplx<T> m11 = lk(l, 3 * P + P), m12 = lk(l, 3 * P + Q), m21 = lk(l, 3 * Q + P), m22 = lk(l, 3 * Q + Q);
+        const cplx<T> c = lk(l, 3 * R + R);
+        cplx<T> w[4];
+        w[0] = cadd(m11, m22);
+        w[1] = mk(-(m21.y + m12.y), m21.x + m12.x);  // i (m21 + m12)
+        w[2] = csub(m21, m12);
+        w[3] = mk(-(m11.y - m22.y), m11.x - m22.x);  // i (m11 - m22)
+        if (l >= 4) {
+#pragma unroll
+            for (int k = 1; k < 4; ++k) w[k] = mk(-w[k].x, -w[k].y);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            b[k] = fma(c.x, w[k].x, fma(c.y, w[k].y, b[k]));
+#pragma unroll
+            for (int j = k; j < 4; ++j) A[k][j] = fma(w[k].x, w[j].x, fma(w[k].y, w[j].y, A[k][j]));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int j = 0; j < k; ++j) A[k][j] = A[j][k];
+    T a[4];
+    const int fb = Solver<T>::solve(A, b, a);
+    const cplx<T> g11 = mk(a[0], a[3]), g12 = mk(a[2], a[1]), g21 = mk(-a[2], a[1]), g22 = mk(a[0], -a[3]);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {  // rows P, Q of G U
+            const cplx<T> xp = lk(l, 3 * P + k), xq = lk(l, 3 * Q + k);
+            lk(l, 3 * P + k) = cfma(g12, xq, cmul(g11, xp));
+            lk(l, 3 * Q + k) = cfma(g22, xq, cmul(g21, xp));
+        }
+    }
+#pragma unroll
+    for (int l = 4; l < 8; ++l) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {  // columns P, Q of U G^dag
+            const cplx<T> xp = lk(l, 3 * k + P), xq = lk(l, 3 * k + Q);
+            lk(l, 3 * k + P) = cfmac(xq, g12, cmulc(xp, g11));
+            lk(l, 3 * k + Q) = cfmac(xq, g22, cmulc(xp, g21));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const cplx<T> xp = Om[3 * P + k], xq = Om[3 * Q + k];
+        Om[3 * P + k] = cfma(g12, xq, cmul(g11, xp));
+        Om[3 * Q + k] = cfma(g22, xq, cmul(g21, xp));
+    }
+    return fb;
+}
+
+__device__ __forceinline__ int field_of_block(const FieldDesc* __restrict__ d, int nf, int b) {
+    int lo = 0, hi = nf - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (d[mid].blk0 <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+template <typename T, bool ACC, int NT>
+__global__ void __launch_bounds__(NT) k_halfsweep(SweepBatch bt, int parity) {
+    const int f = field_of_block(bt.desc, bt.nf, blockIdx.x);
+    if (bt.state[f].done) return;  // block-uniform
+    const FieldDesc fd = bt.desc[f];
+    const Geom g = fd.geo;
+    cplx<T>* __restrict__ U = reinterpret_cast<cplx<T>*>(fd.U);
+    cplx<T>* __restrict__ G = reinterpret_cast<cplx<T>*>(fd.G);
+    const int s = (blockIdx.x - fd.blk0) * NT + threadIdx.x;
+    const bool active = s < g.vh;
+
+    using Links = typename std::conditional<sizeof(T) == 8, SmemLinks<T, NT>, RegLinks<T>>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Links lk;
+    if constexpr (sizeof(T) == 8) lk.base = reinterpret_cast<cplx<T>*>(smem_raw);
+
+    double rsum = 0.0;
+    int fb = 0;
+    if (active) {
+        int c[4];
+        eo_coords(g, parity, s, c);
+        int sb[4];
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) sb[mu] = eo_neighbor(g, c, mu, -1);
+        cplx<T> Om[9];
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+            for (int e = 0; e < 9; ++e) lk(mu, e) = U[lidx(g, mu, parity, e, s)];
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+            for (int e = 0; e < 9; ++e) lk(4 + mu, e) = U[lidx(g, mu, parity ^ 1, e, sb[mu])];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) Om[e] = G[gidx(g, parity, e, s)];
+
+        fb += subgroup_step<T, 0, 1, 2>(lk, Om);
+        fb += subgroup_step<T, 0, 2, 1>(lk, Om);
+        fb += subgroup_step<T, 1, 2, 0>(lk, Om);
+
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+            for (int e = 0; e < 9; ++e) U[lidx(g, mu, parity, e, s)] = lk(mu, e);
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+            for (int e = 0; e < 9; ++e) U[lidx(g, mu, parity ^ 1, e, sb[mu])] = lk(4 + mu, e);
+#pragma unroll
+        for (int e = 0; e < 9; ++e) G[gidx(g, parity, e, s)] = Om[e];
+        if (ACC) {
+#pragma unroll
+            for (int l = 0; l < 8; ++l) {
+                const T tr = lk(l, 0).x + lk(l, 4).x + lk(l, 8).x;
+                const T ti = lk(l, 0).y + lk(l, 4).y + lk(l, 8).y;
+                rsum += (double)tr * (double)tr + (double)ti * (double)ti;
+            }
+        }
+    }
+    __shared__ double red[NT / 32];
+    if (ACC) {
+        const double tot = block_sum(rsum, red);
+        if (threadIdx.x == 0) bt.partial[blockIdx.x] = tot;
+    }
+    if (sizeof(T) == 8) {
+        // count FP64 fallbacks (diagnostic)
+        int w = __reduce_add_sync(0xffffffffu, fb);
+        if ((threadIdx.x & 31) == 0 && w) atomicAdd(&bt.state[f].fallbacks, w);
+    }
+}
+
+// R over all links of each field, into per-block partials (same block map as
+// the half-sweep).
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_functional(SweepBatch bt) {
+    const int f = field_of_block(bt.desc, bt.nf, blockIdx.x);
+    const FieldDesc fd = bt.desc[f];
+    const Geom g = fd.geo;
+    const cplx<T>* __restrict__ U = reinterpret_cast<const cplx<T>*>(fd.U);
+    const int s = (blockIdx.x - fd.blk0) * NT + threadIdx.x;
+    double r = 0.0;
+    if (s < g.vh) {
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int mu = 0; mu < 4; ++mu) {
+                const cplx<T> a = U[lidx(g, mu, p, 0, s)], b = U[lidx(g, mu, p, 4, s)], c = U[lidx(g, mu, p, 8, s)];
+                const double tr = (double)(a.x + b.x + c.x), ti = (double)(a.y + b.y + c.y);
+                r += tr * tr + ti * ti;
+            }
+    }
+    __shared__ double red[NT / 32];
+    const double tot = block_sum(r, red);
+    if (threadIdx.x == 0) bt.partial[blockIdx.x] = tot;
+}
+
+// mode 0: end of a sweep; 1: fresh start (sweep = 0); 2: continue (new phase)
+__global__ void __launch_bounds__(256) k_finalize(SweepBatch bt, int mode) {
+    const int f = blockIdx.x;
+    FieldState* st = &bt.state[f];
+    if (mode == 0 && st->done) {
+        if (threadIdx.x == 0) st->reunit_pending = 0;
+        return;
+    }
+    const FieldDesc fd = bt.desc[f];
+    double v = 0.0;
+    for (int k = threadIdx.x; k < fd.nblk; k += blockDim.x) v += bt.partial[fd.blk0 + k];
+    __shared__ double red[8];
+    const double R = block_sum(v, red);
+    if (threadIdx.x != 0) return;
+    if (mode != 0) {
+        if (mode == 1) {
+            st->sweep = 0;
+            st->fallbacks = 0;
+            if (bt.R_hist) bt.R_hist[(size_t)f * bt.hist_len] = R;
+        }
+        st->R_prev = R;
+        st->R_last = R;
+        st->reunit_pending = 0;
+        st->done = st->sweep >= st->max_sweeps ? 2 : 0;
+        return;
+    }
+    const int k = st->sweep + 1;
+    st->sweep = k;
+    if (bt.R_hist && k < bt.hist_len) bt.R_hist[(size_t)f * bt.hist_len + k] = R;
+    const double dV = (R - st->R_prev) * fd.norm;
+    st->R_prev = R;
+    st->R_last = R;
+    st->reunit_pending = (bt.reunit_every > 0 && k % bt.reunit_every == 0) ? 1 : 0;
+    if (dV < bt.tol)
+        st->done = 1;
+    else if (k >= st->max_sweeps)
+        st->done = 2;
+}
+
+// Re-unitarise the links and Omega of fields with reunit_pending set.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_reunit_pending(SweepBatch bt) {
+    const int f = field_of_block(bt.desc, bt.nf, blockIdx.x);
+    if (!bt.state[f].reunit_pending) return;
+    const FieldDesc fd = bt.desc[f];
+    const Geom g = fd.geo;
+    cplx<T>* __restrict__ U = reinterpret_cast<cplx<T>*>(fd.U);
+    cplx<T>* __restrict__ G = reinterpret_cast<cplx<T>*>(fd.G);
+    const int s = (blockIdx.x - fd.blk0) * NT + threadIdx.x;
+    if (s >= g.vh) return;
+    for (int p = 0; p < 2; ++p) {
+        cplx<T> m[9];
+        for (int mu = 0; mu < 4; ++mu) {
+            load_link(U, g, mu, p, s, m);
+            m3_reunitarise(m);
+            store_link(U, g, mu, p, s, m);
+        }
+#pragma unroll
+        for (int e = 0; e < 9; ++e) m[e] = G[gidx(g, p, e, s)];
+        m3_reunitarise(m);
+#pragma unroll
+        for (int e = 0; e < 9; ++e) G[gidx(g, p, e, s)] = m[e];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------
+template <typename T>
+static int enqueue_sweep(const SweepBatch& bt, size_t smem, cudaStream_t st) {
+    constexpr int NT = sweep_threads<T>();
+    k_halfsweep<T, false, NT><<<bt.total_blocks, NT, smem, st>>>(bt, 0);
+    k_halfsweep<T, true, NT><<<bt.total_blocks, NT, smem, st>>>(bt, 1);
+    k_finalize<<<bt.nf, 256, 0, st>>>(bt, 0);
+    if (bt.reunit_every > 0) k_reunit_pending<T, NT><<<bt.total_blocks, NT, 0, st>>>(bt);
+    return 0;
+}
+
+template <typename T>
+int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, FieldState* h_state, double* d_hist,
+                  int hist_len, double tol, int reunit_every, int abs_cap, int check_every, bool fresh,
+                  cudaStream_t stream) {
+    constexpr int NT = sweep_threads<T>();
+    const int nf = (int)fields_in.size();
+    std::vector<FieldDesc> fields = fields_in;
+    int total = 0;
+    for (auto& fd : fields) {
+        fd.nblk = (fd.geo.vh + NT - 1) / NT;
+        fd.blk0 = total;
+        total += fd.nblk;
+    }
+    int rc = 0;
+    FieldDesc* d_desc = (FieldDesc*)scratch_device("fix.desc", sizeof(FieldDesc) * nf, &rc);
+    if (rc) return rc;
+    double* d_partial = (double*)scratch_device("fix.partial", sizeof(double) * total, &rc);
+    if (rc) return rc;
+    FieldDesc* h_desc = (FieldDesc*)scratch_host("fix.desc", sizeof(FieldDesc) * nf, &rc);
+    if (rc) return rc;
+    // the previous call may still read the pinned staging buffer
+    MCG_CK(cudaStreamSynchronize(stream));
+    std::copy(fields.begin(), fields.end(), h_desc);
+    MCG_CK(cudaMemcpyAsync(d_desc, h_desc, sizeof(FieldDesc) * nf, cudaMemcpyHostToDevice, stream));
+    // per-field phase caps
+    MCG_CK(cudaMemcpyAsync(h_state, d_state, sizeof(FieldState) * nf, cudaMemcpyDeviceToHost, stream));
+    MCG_CK(cudaStreamSynchronize(stream));
+    int min_sweep = 1 << 30;
+    for (int f = 0; f < nf; ++f) {
+        if (fresh) {
+            h_state[f].sweep = 0;
+            h_state[f].fallbacks = 0;
+        }
+        h_state[f].max_sweeps = abs_cap;
+        h_state[f].done = 0;
+        min_sweep = std::min(min_sweep, h_state[f].sweep);
+    }
+    const int phase_len = abs_cap - min_sweep;
+    MCG_CK(cudaMemcpyAsync(d_state, h_state, sizeof(FieldState) * nf, cudaMemcpyHostToDevice, stream));
+
+    SweepBatch bt;
+    bt.desc = d_desc;
+    bt.nf = nf;
+    bt.total_blocks = total;
+    bt.state = d_state;
+    bt.partial = d_partial;
+    bt.R_hist = d_hist;
+    bt.hist_len = hist_len;
+    bt.tol = tol;
+    bt.reunit_every = reunit_every;
+
+    size_t smem = 0;
+    if (sizeof(T) == 8) {
+        smem = sizeof(cplx<T>) * 72 * NT;
+        static bool attr_set = false;
+        if (!attr_set) {
+            MCG_CK(cudaFuncSetAttribute(k_halfsweep<T, false, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+            MCG_CK(cudaFuncSetAttribute(k_halfsweep<T, true, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+            attr_set = true;
+        }
+    }
+
+    k_functional<T, NT><<<total, NT, 0, stream>>>(bt);
+    k_finalize<<<nf, 256, 0, stream>>>(bt, fresh ? 1 : 2);
+    MCG_CK(cudaGetLastError());
+    if (phase_len <= 0) {
+        MCG_CK(cudaMemcpyAsync(h_state, d_state, sizeof(FieldState) * nf, cudaMemcpyDeviceToHost, stream));
+        MCG_CK(cudaStreamSynchronize(stream));
+        return 0;
+    }
+
+    // graph of one chunk of sweeps, captured on the library's own stream
+    const int chunk = std::max(1, std::min(check_every, phase_len));
+    cudaStream_t cs = capture_stream(&rc);
+    if (rc) return rc;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    MCG_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    for (int i = 0; i < chunk; ++i) enqueue_sweep<T>(bt, smem, cs);
+    cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    if (ce != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return cuda_fail(ce, "cudaGraphInstantiate");
+    }
+    const int max_chunks = (phase_len + chunk - 1) / chunk + 1;
+    int status = 0;
+    for (int c = 0; c < max_chunks; ++c) {
+        ce = cudaGraphLaunch(exec, stream);
+        if (ce != cudaSuccess) {
+            status = cuda_fail(ce, "cudaGraphLaunch");
+            break;
+        }
+        ce = cudaMemcpyAsync(h_state, d_state, sizeof(FieldState) * nf, cudaMemcpyDeviceToHost, stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
+        if (ce != cudaSuccess) {
+            status = cuda_fail(ce, "sweep chunk");
+            break;
+        }
+        bool all = true;
+        for (int f = 0; f < nf; ++f) all = all && h_state[f].done != 0;
+        if (all) break;
+    }
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    return status;
+}
+
+template int run_fix_phase<float>(const std::vector<FieldDesc>&, FieldState*, FieldState*, double*, int, double,
+                                  int, int, int, bool, cudaStream_t);
+template int run_fix_phase<double>(const std::vector<FieldDesc>&, FieldState*, FieldState*, double*, int, double,
+                                   int, int, int, bool, cudaStream_t);
+
+}  // namespace mcg

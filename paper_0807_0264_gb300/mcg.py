@@ -1,0 +1,348 @@
+"""Thin Python binding of libmcg (include/mcg.h) over ctypes.
+
+Every function here marshals arguments and calls the C-ABI entry point of the
+same name; all computation runs in the CUDA kernels of libmcg.so.  PyTorch
+provides device memory (tensors) and the current CUDA stream.  There is no CPU
+fallback: if the library is missing, importing this module builds it with
+nvcc, and if that fails the import raises.
+
+Tensor conventions (device, even/odd SoA, see include/mcg.h):
+    links  U: float64 / float32 tensor (nfields, 4, 2, 9, Vh, 2)  [mu, parity, entry, site, re/im]
+    gauge  G: float64 / float32 tensor (nfields, 2, 9, Vh, 2)
+    center Z: int8 tensor (nfields, 4, 2, Vh)
+    canonical links:  complex128 tensor (nfields, V, 4, 3, 3)
+    canonical gauge:  complex128 tensor (nfields, V, 3, 3)
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+import torch
+
+from . import build as _build
+
+F64, F32 = 0, 1
+OK, NOT_CONVERGED = 0, 1
+_STATUS = {0: "MCG_OK", 1: "MCG_NOT_CONVERGED", 2: "MCG_BAD_DIMS", 3: "MCG_BAD_ARG", 4: "MCG_BAD_INPUT",
+           5: "MCG_CUDA_ERROR", 6: "MCG_WAIT_TIMEOUT"}
+
+
+class MCGError(RuntimeError):
+    def __init__(self, fn: str, code: int, msg: str):
+        super().__init__(f"{fn} -> {_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class mcg_lattice(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int * 4), ("nfields", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class mcg_params(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_sweeps", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("reunit_every", ctypes.c_int), ("fp32_sweeps", ctypes.c_int), ("fp32_tol", ctypes.c_double),
+                ("fp32_reunit_every", ctypes.c_int)]
+
+
+class mcg_precond_result(ctypes.Structure):
+    _fields_ = [("V_smeared", ctypes.c_double), ("V_fixed", ctypes.c_double), ("plaquette_in", ctypes.c_double),
+                ("plaquette_out", ctypes.c_double), ("vortices", ctypes.c_longlong),
+                ("vortex_density", ctypes.c_double), ("sweeps_smeared", ctypes.c_int),
+                ("sweeps_fixed", ctypes.c_int), ("sweeps_fp32", ctypes.c_int), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _load() -> ctypes.CDLL:
+    path = _build.LIB
+    if not os.path.exists(path):
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    L = ctypes.POINTER(mcg_lattice)
+    PR = ctypes.POINTER(mcg_params)
+    sig = {
+        "mcg_version": ([], I),
+        "mcg_last_error": ([], ctypes.c_char_p),
+        "mcg_release": ([], I),
+        "mcg_pack_links": ([P, P, L, P], I),
+        "mcg_unpack_links": ([P, P, L, P], I),
+        "mcg_pack_gauge": ([P, P, L, P], I),
+        "mcg_unpack_gauge": ([P, P, L, P], I),
+        "mcg_unpack_center": ([P, P, L, P], I),
+        "mcg_convert": ([P, I, P, I, S, P], I),
+        "mcg_set_identity_gauge": ([P, L, P], I),
+        "mcg_plaquette": ([P, P, L, P], I),
+        "mcg_functional": ([P, P, L, P], I),
+        "mcg_apply_gauge": ([P, P, L, P], I),
+        "mcg_reunitarise": ([P, I, L, P], I),
+        "mcg_smear": ([P, P, L, D, D, I, P], I),
+        "mcg_fix": ([P, P, L, PR, P, P, P, P], I),
+        "mcg_center_project": ([P, P, P, L, P], I),
+        "mcg_precondition_fix": ([P, P, P, L, PR, D, D, I, I, ctypes.POINTER(mcg_precond_result), P], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = _load()
+
+#: every entry point include/mcg.h declares (checked by the test suite)
+EXPORTS = ("mcg_version", "mcg_last_error", "mcg_release", "mcg_pack_links", "mcg_unpack_links", "mcg_pack_gauge",
+           "mcg_unpack_gauge", "mcg_unpack_center", "mcg_convert", "mcg_set_identity_gauge", "mcg_plaquette",
+           "mcg_functional", "mcg_apply_gauge", "mcg_reunitarise", "mcg_smear", "mcg_fix", "mcg_center_project",
+           "mcg_precondition_fix")
+
+
+def library() -> ctypes.CDLL:
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+@dataclasses.dataclass
+class Params:
+    """mcg_params: stop threshold on dV_U and the sweep schedule."""
+    tol: float = 1e-10
+    max_sweeps: int = 2000
+    check_every: int = 20
+    reunit_every: int = 50
+    fp32_sweeps: int = 0
+    fp32_tol: float = 1e-9
+    fp32_reunit_every: int = 10
+
+    def c(self) -> mcg_params:
+        return mcg_params(self.tol, self.max_sweeps, self.check_every, self.reunit_every, self.fp32_sweeps,
+                          self.fp32_tol, self.fp32_reunit_every)
+
+
+def lattice(dims, nfields: int = 1, precision: int = F64) -> mcg_lattice:
+    lat = mcg_lattice()
+    for k in range(4):
+        lat.dims[k] = int(dims[k])
+    lat.nfields = int(nfields)
+    lat.precision = int(precision)
+    return lat
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _check(fn: str, rc: int, allow=(OK,)) -> int:
+    if rc not in allow:
+        raise MCGError(fn, rc, _lib.mcg_last_error().decode())
+    return rc
+
+
+def _real_dtype(precision: int):
+    return torch.float64 if precision == F64 else torch.float32
+
+
+def vh_of(dims) -> int:
+    v = 1
+    for d in dims:
+        v *= int(d)
+    return v // 2
+
+
+def empty_links(dims, nfields=1, precision=F64, device="cuda"):
+    return torch.empty((nfields, 4, 2, 9, vh_of(dims), 2), dtype=_real_dtype(precision), device=device)
+
+
+def empty_gauge(dims, nfields=1, precision=F64, device="cuda"):
+    return torch.empty((nfields, 2, 9, vh_of(dims), 2), dtype=_real_dtype(precision), device=device)
+
+
+def precision_of(t: torch.Tensor) -> int:
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.float32:
+        return F32
+    raise TypeError(f"field tensor must be float64 or float32, got {t.dtype}")
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is not None and (not t.is_cuda or not t.is_contiguous()):
+            raise ValueError("libmcg arguments must be contiguous CUDA tensors")
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+def mcg_version() -> int:
+    return _lib.mcg_version()
+
+
+def mcg_release() -> None:
+    _check("mcg_release", _lib.mcg_release())
+
+
+def mcg_pack_links(canon: torch.Tensor, dims, precision=F64, stream=None) -> torch.Tensor:
+    """canonical complex128 (nf, V, 4, 3, 3) -> SoA links."""
+    _need_cuda(canon)
+    assert canon.dtype == torch.complex128
+    nf = canon.shape[0]
+    U = empty_links(dims, nf, precision, canon.device)
+    _check("mcg_pack_links", _lib.mcg_pack_links(_ptr(canon), _ptr(U), lattice(dims, nf, precision), _stream(stream)))
+    return U
+
+
+def mcg_unpack_links(U: torch.Tensor, dims, stream=None) -> torch.Tensor:
+    _need_cuda(U)
+    nf = U.shape[0]
+    canon = torch.empty((nf, 2 * vh_of(dims), 4, 3, 3), dtype=torch.complex128, device=U.device)
+    _check("mcg_unpack_links",
+           _lib.mcg_unpack_links(_ptr(U), _ptr(canon), lattice(dims, nf, precision_of(U)), _stream(stream)))
+    return canon
+
+
+def mcg_pack_gauge(canon: torch.Tensor, dims, precision=F64, stream=None) -> torch.Tensor:
+    _need_cuda(canon)
+    assert canon.dtype == torch.complex128
+    nf = canon.shape[0]
+    G = empty_gauge(dims, nf, precision, canon.device)
+    _check("mcg_pack_gauge", _lib.mcg_pack_gauge(_ptr(canon), _ptr(G), lattice(dims, nf, precision), _stream(stream)))
+    return G
+
+
+def mcg_unpack_gauge(G: torch.Tensor, dims, stream=None) -> torch.Tensor:
+    _need_cuda(G)
+    nf = G.shape[0]
+    canon = torch.empty((nf, 2 * vh_of(dims), 3, 3), dtype=torch.complex128, device=G.device)
+    _check("mcg_unpack_gauge",
+           _lib.mcg_unpack_gauge(_ptr(G), _ptr(canon), lattice(dims, nf, precision_of(G)), _stream(stream)))
+    return canon
+
+
+def mcg_unpack_center(Z: torch.Tensor, dims, stream=None) -> torch.Tensor:
+    _need_cuda(Z)
+    nf = Z.shape[0]
+    canon = torch.empty((nf, 2 * vh_of(dims), 4), dtype=torch.int8, device=Z.device)
+    _check("mcg_unpack_center", _lib.mcg_unpack_center(_ptr(Z), _ptr(canon), lattice(dims, nf, F64), _stream(stream)))
+    return canon
+
+
+def mcg_convert(src: torch.Tensor, dst_precision: int, stream=None) -> torch.Tensor:
+    _need_cuda(src)
+    dst = torch.empty(src.shape, dtype=_real_dtype(dst_precision), device=src.device)
+    _check("mcg_convert", _lib.mcg_convert(_ptr(src), precision_of(src), _ptr(dst), dst_precision,
+                                           src.numel() // 2, _stream(stream)))
+    return dst
+
+
+def mcg_set_identity_gauge(G: torch.Tensor, dims, stream=None) -> torch.Tensor:
+    _need_cuda(G)
+    _check("mcg_set_identity_gauge",
+           _lib.mcg_set_identity_gauge(_ptr(G), lattice(dims, G.shape[0], precision_of(G)), _stream(stream)))
+    return G
+
+
+def identity_gauge(dims, nfields=1, precision=F64, device="cuda") -> torch.Tensor:
+    return mcg_set_identity_gauge(empty_gauge(dims, nfields, precision, device), dims)
+
+
+def mcg_plaquette(U: torch.Tensor, dims, stream=None):
+    _need_cuda(U)
+    nf = U.shape[0]
+    out = (ctypes.c_double * nf)()
+    _check("mcg_plaquette", _lib.mcg_plaquette(_ptr(U), out, lattice(dims, nf, precision_of(U)), _stream(stream)))
+    return list(out)
+
+
+def mcg_functional(U: torch.Tensor, dims, stream=None):
+    _need_cuda(U)
+    nf = U.shape[0]
+    out = (ctypes.c_double * nf)()
+    _check("mcg_functional", _lib.mcg_functional(_ptr(U), out, lattice(dims, nf, precision_of(U)), _stream(stream)))
+    return list(out)
+
+
+def mcg_apply_gauge(U: torch.Tensor, G: torch.Tensor, dims, stream=None) -> torch.Tensor:
+    _need_cuda(U, G)
+    _check("mcg_apply_gauge",
+           _lib.mcg_apply_gauge(_ptr(U), _ptr(G), lattice(dims, U.shape[0], precision_of(U)), _stream(stream)))
+    return U
+
+
+def mcg_reunitarise(M: torch.Tensor, which: int, dims, stream=None) -> torch.Tensor:
+    _need_cuda(M)
+    _check("mcg_reunitarise",
+           _lib.mcg_reunitarise(_ptr(M), int(which), lattice(dims, M.shape[0], precision_of(M)), _stream(stream)))
+    return M
+
+
+def mcg_smear(U_in: torch.Tensor, dims, rho: float, eps: float, n: int, U_out: torch.Tensor | None = None,
+              stream=None) -> torch.Tensor:
+    _need_cuda(U_in)
+    if U_out is None:
+        U_out = torch.empty_like(U_in)
+    _check("mcg_smear", _lib.mcg_smear(_ptr(U_in), _ptr(U_out), lattice(dims, U_in.shape[0], precision_of(U_in)),
+                                       float(rho), float(eps), int(n), _stream(stream)))
+    return U_out
+
+
+def mcg_fix(U: torch.Tensor, G: torch.Tensor, dims, params: Params | None = None, history: bool = False,
+            stream=None) -> dict:
+    """MCG relaxation in place on U and G.  Returns dict(R, sweeps, converged, R_hist)."""
+    _need_cuda(U, G)
+    params = params or Params()
+    nf = U.shape[0]
+    R = (ctypes.c_double * nf)()
+    sw = (ctypes.c_int * nf)()
+    hist = (ctypes.c_double * (nf * (params.max_sweeps + 1)))() if history else None
+    cp = params.c()
+    rc = _check("mcg_fix", _lib.mcg_fix(_ptr(U), _ptr(G), lattice(dims, nf, precision_of(U)), ctypes.byref(cp), R, sw,
+                                        hist, _stream(stream)), allow=(OK, NOT_CONVERGED))
+    out = dict(R=list(R), sweeps=list(sw), converged=(rc == OK))
+    if history:
+        import numpy as np
+
+        h = np.ctypeslib.as_array(hist).reshape(nf, params.max_sweeps + 1).copy()
+        out["R_hist"] = [h[f, : sw[f] + 1] for f in range(nf)]
+    return out
+
+
+def mcg_center_project(U: torch.Tensor, dims, Z: torch.Tensor | None = None, stream=None):
+    """Returns (Z, counts) with counts a list per field of [total, 01, 02, 03, 12, 13, 23]."""
+    _need_cuda(U)
+    nf = U.shape[0]
+    if Z is None:
+        Z = torch.empty((nf, 4, 2, vh_of(dims)), dtype=torch.int8, device=U.device)
+    counts = (ctypes.c_longlong * (7 * nf))()
+    _check("mcg_center_project",
+           _lib.mcg_center_project(_ptr(U), _ptr(Z), counts, lattice(dims, nf, precision_of(U)), _stream(stream)))
+    return Z, [list(counts[7 * f: 7 * f + 7]) for f in range(nf)]
+
+
+def mcg_precondition_fix(U: torch.Tensor, G: torch.Tensor, dims, params: Params | None = None, rho: float = 0.1,
+                         eps: float = 1.0, nsmear: int = 0, smear_precision: int | None = None,
+                         Z: torch.Tensor | None = None, stream=None) -> list:
+    """Sec. II.B pipeline in place (U -> fixed field, G -> total transform)."""
+    _need_cuda(U, G, Z)
+    params = params or Params()
+    nf = U.shape[0]
+    prec = precision_of(U)
+    res = (mcg_precond_result * nf)()
+    cp = params.c()
+    _check("mcg_precondition_fix",
+           _lib.mcg_precondition_fix(_ptr(U), _ptr(G), _ptr(Z), lattice(dims, nf, prec), ctypes.byref(cp), float(rho),
+                                     float(eps), int(nsmear), prec if smear_precision is None else int(smear_precision),
+                                     res, _stream(stream)), allow=(OK, NOT_CONVERGED))
+    return [r.as_dict() for r in res]

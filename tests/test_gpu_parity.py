@@ -1,0 +1,306 @@
+"""GPU parity: libmcg (CUDA, sm_103a, called through the C ABI) against the
+FP64 CPU oracle on identical seeded inputs.
+
+Bars (from the method's arithmetic):
+  - FP64 sweep: per link <= 1e-11 abs after each sweep from identical input;
+    final R <= 1e-9 relative over a trajectory;
+  - Z3 projection and vortex counts: bit-exact on identical links;
+  - layout conversion, plaquette, R, gauge transforms: rounding level;
+  - FP32 paths: errors stated per test from FP32 rounding (~1e-7 per op).
+Sizes span several thread blocks with a ragged tail (64 threads per block
+for FP64, 128 for FP32) plus the 2^4 degenerate lattice.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0807_0264_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+DIMS_SMALL = [(2, 2, 2, 2), (4, 4, 4, 4), (6, 4, 4, 6), (4, 2, 6, 8)]
+NEVER = -1e300  # tol that never triggers: run exactly max_sweeps
+
+
+@pytest.fixture(scope="module")
+def mcg():
+    from paper_0807_0264_gb300 import mcg as m
+
+    return m
+
+
+def to_dev(U):
+    return torch.from_numpy(np.ascontiguousarray(U)).to("cuda").unsqueeze(0)
+
+
+def pack(mcg, U, dims, prec=0):
+    return mcg.mcg_pack_links(to_dev(U), dims, prec)
+
+
+def unpack(mcg, Ud, dims):
+    return mcg.mcg_unpack_links(Ud, dims)[0].cpu().numpy()
+
+
+def pack_g(mcg, G, dims, prec=0):
+    return mcg.mcg_pack_gauge(to_dev(G), dims, prec)
+
+
+def unpack_g(mcg, Gd, dims):
+    return mcg.mcg_unpack_gauge(Gd, dims)[0].cpu().numpy()
+
+
+@pytest.mark.parametrize("dims", DIMS_SMALL)
+def test_pack_roundtrip(mcg, dims):
+    U = synth.make_field(dims, 0.5, 1)
+    Ud = pack(mcg, U, dims)
+    np.testing.assert_array_equal(unpack(mcg, Ud, dims), U)
+    G = synth.random_gauge(dims, 2)
+    np.testing.assert_array_equal(unpack_g(mcg, pack_g(mcg, G, dims), dims), G)
+    U32 = pack(mcg, U, dims, 1)
+    assert np.abs(unpack(mcg, U32, dims) - U).max() < 1e-7
+
+
+@pytest.mark.parametrize("dims", DIMS_SMALL)
+def test_plaquette_and_functional(mcg, dims):
+    U = synth.make_field(dims, 0.5, 3)
+    Ud = pack(mcg, U, dims)
+    assert abs(mcg.mcg_plaquette(Ud, dims)[0] - oracle.plaquette(dims, U)) < 1e-13
+    R = oracle.functional_R(dims, U)
+    assert abs(mcg.mcg_functional(Ud, dims)[0] - R) < 1e-12 * R
+
+
+@pytest.mark.parametrize("dims", DIMS_SMALL)
+def test_apply_gauge_and_reunitarise(mcg, dims):
+    U = synth.make_field(dims, 0.5, 3)
+    G = synth.random_gauge(dims, 4)
+    Ud, Gd = pack(mcg, U, dims), pack_g(mcg, G, dims)
+    mcg.mcg_apply_gauge(Ud, Gd, dims)
+    assert np.abs(unpack(mcg, Ud, dims) - oracle.apply_gauge(dims, U, G)).max() < 1e-14
+    rng = np.random.default_rng(0)
+    noisy = U + 1e-7 * (rng.standard_normal(U.shape) + 1j * rng.standard_normal(U.shape))
+    Nd = pack(mcg, noisy, dims)
+    mcg.mcg_reunitarise(Nd, 0, dims)
+    assert np.abs(unpack(mcg, Nd, dims) - oracle.reunitarise(noisy)).max() < 1e-14
+
+
+@pytest.mark.parametrize("dims", DIMS_SMALL + [(8, 8, 8, 8)])
+@pytest.mark.parametrize("width", [0.4326, 1.2])
+def test_center_projection_bit_exact(mcg, dims, width):
+    U = synth.make_field(dims, width, 5)
+    Ud = pack(mcg, U, dims)
+    Z, counts = mcg.mcg_center_project(Ud, dims)
+    m_gpu = mcg.mcg_unpack_center(Z, dims)[0].cpu().numpy()
+    m_orc = oracle.center_project(dims, U)
+    np.testing.assert_array_equal(m_gpu, m_orc)
+    tot, per = oracle.vortex_count(dims, m_orc)
+    assert counts[0][0] == tot and counts[0][1:] == list(per)
+
+
+def test_center_projection_fp32_decides_in_fp64(mcg):
+    dims = (6, 4, 4, 6)
+    U = synth.make_field(dims, 1.0, 6)
+    Ud32 = pack(mcg, U, dims, 1)
+    U32 = unpack(mcg, Ud32, dims)  # exactly the FP32 values, widened
+    Z, counts = mcg.mcg_center_project(Ud32, dims)
+    np.testing.assert_array_equal(mcg.mcg_unpack_center(Z, dims)[0].cpu().numpy(), oracle.center_project(dims, U32))
+
+
+def test_center_golden_boundaries(mcg):
+    """Sector boundaries of the golden table, through the FP64 kernel."""
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "center_sectors.json")) as f:
+        cases = json.load(f)["cases"]
+    n = len(cases)
+    dims = (2, 2, 2, 2)
+    V = int(np.prod(dims))
+    assert 4 * V >= n
+    U = np.zeros((V * 4, 3, 3), np.complex128)
+    U[:n, 0, 0] = [c[0] + 1j * c[1] for c in cases]
+    U = U.reshape(V, 4, 3, 3)
+    Z, _ = mcg.mcg_center_project(pack(mcg, U, dims), dims)
+    m = mcg.mcg_unpack_center(Z, dims)[0].cpu().numpy().ravel()[:n]
+    np.testing.assert_array_equal(m, [c[2] for c in cases])
+
+
+def gpu_sweeps(mcg, U, G, dims, n, prec=0, reunit_every=50):
+    Ud, Gd = pack(mcg, U, dims, prec), pack_g(mcg, G, dims, prec)
+    p = mcg.Params(tol=NEVER, max_sweeps=n, check_every=max(1, n), reunit_every=reunit_every)
+    res = mcg.mcg_fix(Ud, Gd, dims, p, history=True)
+    return unpack(mcg, Ud, dims), unpack_g(mcg, Gd, dims), res
+
+
+@pytest.mark.parametrize("dims", DIMS_SMALL)
+def test_fp64_sweep_parity_per_sweep(mcg, dims):
+    """Each FP64 sweep from identical input agrees per link to 1e-11."""
+    U = synth.make_field(dims, 0.5, 7)
+    G = synth.identity_gauge(dims)
+    worst = 0.0
+    for k in range(6):
+        r = oracle.fix(dims, U, G, tol=NEVER, max_sweeps=1, reunit_every=0)
+        Ug, Gg, res = gpu_sweeps(mcg, U, G, dims, 1, reunit_every=0)
+        err = max(np.abs(Ug - r["U"]).max(), np.abs(Gg - r["G"]).max())
+        worst = max(worst, err)
+        assert err <= 1e-11, (k, err)
+        R = r["R_hist"][-1]
+        assert abs(res["R"][0] - R) <= 1e-12 * R
+        U, G = r["U"], r["G"]
+    print("worst per-sweep link deviation", worst)
+
+
+def test_fp64_trajectory_parity(mcg):
+    dims = (6, 4, 4, 6)
+    U = synth.make_field(dims, 0.5, 8)
+    G = synth.identity_gauge(dims)
+    n = 60
+    r = oracle.fix(dims, U, G, tol=NEVER, max_sweeps=n, reunit_every=50)
+    Ug, Gg, res = gpu_sweeps(mcg, U, G, dims, n, reunit_every=50)
+    hist = res["R_hist"][0]
+    np.testing.assert_allclose(hist, r["R_hist"], rtol=1e-9)
+    assert np.abs(Ug - r["U"]).max() < 1e-9
+
+
+def test_config1_fix_to_convergence(mcg):
+    """4^4, w = 0.5, seed 0: dV_U < 1e-10 or 2000 sweeps; same stop sweep,
+    R and vortex count as the oracle."""
+    dims = (4, 4, 4, 4)
+    U = synth.make_field(dims, 0.5, 0)
+    r = oracle.fix(dims, U, None, tol=1e-10, max_sweeps=2000, reunit_every=50)
+    Ud, Gd = pack(mcg, U, dims), mcg.identity_gauge(dims)
+    res = mcg.mcg_fix(Ud, Gd, dims, mcg.Params(tol=1e-10, max_sweeps=2000, check_every=7, reunit_every=50))
+    assert res["converged"] and r["converged"]
+    assert res["sweeps"][0] == r["sweeps"]
+    assert abs(res["R"][0] - r["R_hist"][-1]) < 1e-9 * r["R_hist"][-1]
+    Uf = unpack(mcg, Ud, dims)
+    assert np.abs(Uf - r["U"]).max() < 1e-9
+    _, counts = mcg.mcg_center_project(Ud, dims)
+    assert counts[0][0] == oracle.vortex_count(dims, oracle.center_project(dims, r["U"]))[0]
+
+
+def test_pure_gauge_reaches_one(mcg):
+    dims = (4, 4, 4, 4)
+    U = synth.make_field(dims, 0.0, 0)
+    Ud, Gd = pack(mcg, U, dims), mcg.identity_gauge(dims)
+    res = mcg.mcg_fix(Ud, Gd, dims, mcg.Params(tol=1e-10, max_sweeps=2000))
+    assert res["converged"]
+    assert res["R"][0] / (36 * 256) > 1 - 1e-10
+
+
+def test_gauge_orbit_and_transform_tracking(mcg):
+    dims = (6, 4, 4, 6)
+    U = synth.make_field(dims, 0.5, 9)
+    Ud, Gd = pack(mcg, U, dims), mcg.identity_gauge(dims)
+    mcg.mcg_fix(Ud, Gd, dims, mcg.Params(tol=1e-10, max_sweeps=500))
+    Uf, Gf = unpack(mcg, Ud, dims), unpack_g(mcg, Gd, dims)
+    assert np.abs(oracle.apply_gauge(dims, U, Gf) - Uf).max() < 1e-12
+    assert abs(oracle.plaquette(dims, Uf) - oracle.plaquette(dims, U)) < 1e-13
+
+
+@pytest.mark.parametrize("eps,rho,n", [(1.0, 0.1, 1), (1.0, 0.1, 4), (-0.25, 0.06, 1), (-0.25, 0.06, 3), (0.0, 0.1, 2)])
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 4, 6), (2, 2, 4, 4)])
+def test_smear_parity(mcg, dims, eps, rho, n):
+    U = synth.make_field(dims, 0.5, 10)
+    S = oracle.smear(dims, U, rho, eps, n)
+    Sd = mcg.mcg_smear(pack(mcg, U, dims), dims, rho, eps, n)
+    assert np.abs(unpack(mcg, Sd, dims) - S).max() < 1e-12
+    S32 = mcg.mcg_smear(pack(mcg, U, dims, 1), dims, rho, eps, n)
+    assert np.abs(unpack(mcg, S32, dims) - S).max() < 2e-5 * n
+
+
+def test_smear_small_Q_branch(mcg):
+    """Nearly smooth field: Q is tiny, exercising the series branch of exp(iQ)."""
+    dims = (4, 4, 4, 4)
+    U = synth.make_field(dims, 1e-3, 11)
+    S = oracle.smear(dims, U, 0.1, 1.0, 2)
+    Sd = mcg.mcg_smear(pack(mcg, U, dims), dims, 0.1, 1.0, 2)
+    assert np.abs(unpack(mcg, Sd, dims) - S).max() < 1e-14
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 4, 6)])
+def test_fp32_sweep_close_to_fp64(mcg, dims):
+    U = synth.make_field(dims, 0.5, 12)
+    G = synth.identity_gauge(dims)
+    r = oracle.fix(dims, U, G, tol=NEVER, max_sweeps=1, reunit_every=0)
+    Ug, Gg, res = gpu_sweeps(mcg, U, G, dims, 1, prec=1, reunit_every=0)
+    assert np.abs(Ug - r["U"]).max() < 5e-5
+    assert abs(res["R"][0] - r["R_hist"][-1]) < 1e-5 * r["R_hist"][-1]
+
+
+def test_fp32_R_monotone(mcg):
+    dims = (6, 4, 4, 6)
+    U = synth.make_field(dims, 0.5, 13)
+    _, _, res = gpu_sweeps(mcg, U, synth.identity_gauge(dims), dims, 40, prec=1, reunit_every=10)
+    h = res["R_hist"][0]
+    assert (np.diff(h) >= -1e-5 * h[1:]).all()
+
+
+def test_mixed_schedule_on_orbit_and_converged(mcg):
+    """FP32 sweeps then FP64 finish: the field stays on its gauge orbit (FP64
+    hand-off), converges to dV_U < 1e-10 and lands at the oracle's R."""
+    dims = (8, 8, 8, 8)
+    U = synth.make_field(dims, synth.W_PLAQ_06, 0)
+    r = oracle.fix(dims, U, None, tol=1e-10, max_sweeps=2000)
+    Ud, Gd = pack(mcg, U, dims), mcg.identity_gauge(dims)
+    res = mcg.mcg_fix(Ud, Gd, dims, mcg.Params(tol=1e-10, max_sweeps=2000, fp32_sweeps=2000, fp32_tol=1e-9))
+    assert res["converged"]
+    Uf, Gf = unpack(mcg, Ud, dims), unpack_g(mcg, Gd, dims)
+    assert np.abs(oracle.apply_gauge(dims, U, Gf) - Uf).max() < 1e-12
+    assert abs(oracle.plaquette(dims, Uf) - oracle.plaquette(dims, U)) < 1e-13
+    V_gpu = res["R"][0] / (36 * 4096)
+    V_orc = r["R_hist"][-1] / (36 * 4096)
+    print("mixed V", V_gpu, "oracle FP64 V", V_orc, "sweeps", res["sweeps"], r["sweeps"])
+    assert abs(V_gpu - V_orc) < 1e-6
+
+
+def test_batched_fields_match_single(mcg):
+    dims = (4, 4, 4, 4)
+    Us = [synth.make_field(dims, 0.5, s) for s in (20, 21, 22)]
+    canon = torch.from_numpy(np.stack(Us)).to("cuda")
+    Ud = mcg.mcg_pack_links(canon, dims)
+    Gd = mcg.identity_gauge(dims, 3)
+    res = mcg.mcg_fix(Ud, Gd, dims, mcg.Params(tol=1e-10, max_sweeps=500))
+    out = mcg.mcg_unpack_links(Ud, dims).cpu().numpy()
+    for f, U in enumerate(Us):
+        r = oracle.fix(dims, U, None, tol=1e-10, max_sweeps=500)
+        assert res["sweeps"][f] == r["sweeps"]
+        assert np.abs(out[f] - r["U"]).max() < 1e-9
+
+
+@pytest.mark.parametrize("nsmear,eps,rho", [(0, 1.0, 0.1), (4, 1.0, 0.1), (3, -0.25, 0.06)])
+def test_precondition_pipeline_parity(mcg, nsmear, eps, rho):
+    dims = (4, 4, 4, 4)
+    U = synth.make_field(dims, 0.5, 2)
+    o = oracle.precondition_and_fix(dims, U, rho=rho, eps=eps, nsmear=nsmear, tol=1e-10, max_sweeps=1000)
+    Ud, Gd = pack(mcg, U, dims), mcg.identity_gauge(dims)
+    Z = torch.empty((1, 4, 2, 128), dtype=torch.int8, device="cuda")
+    res = mcg.mcg_precondition_fix(Ud, Gd, dims, mcg.Params(tol=1e-10, max_sweeps=1000), rho=rho, eps=eps,
+                                   nsmear=nsmear, Z=Z)[0]
+    assert res["sweeps_fixed"] == o["fixed"]["sweeps"]
+    assert abs(res["V_fixed"] - o["fixed"]["R_hist"][-1] / (36 * 256)) < 1e-10
+    if nsmear:
+        assert res["sweeps_smeared"] == o["smeared"]["sweeps"]
+    assert res["vortices"] == o["vortices"]
+    assert abs(res["plaquette_out"] - res["plaquette_in"]) < 1e-13
+    Uf = unpack(mcg, Ud, dims)
+    assert np.abs(Uf - o["fixed"]["U"]).max() < 1e-9
+    assert np.abs(unpack_g(mcg, Gd, dims) - o["G_total"]).max() < 1e-9
+    np.testing.assert_array_equal(mcg.mcg_unpack_center(Z, dims)[0].cpu().numpy(), o["m"])
+
+
+def test_full_size_20x40_one_sweep_parity(mcg):
+    """20^3 x 40 (the bench workload's lattice): one FP64 sweep against the
+    oracle over every link, the FP32 sweep close, plaquette of the input."""
+    dims = (20, 20, 20, 40)
+    U = synth.make_field(dims, synth.W_PLAQ_06, 0)
+    G = synth.identity_gauge(dims)
+    r = oracle.fix(dims, U, G, tol=NEVER, max_sweeps=1, reunit_every=0)
+    Ug, Gg, res = gpu_sweeps(mcg, U, G, dims, 1, reunit_every=0)
+    assert np.abs(Ug - r["U"]).max() <= 1e-11
+    assert np.abs(Gg - r["G"]).max() <= 1e-11
+    assert abs(res["R"][0] - r["R_hist"][-1]) <= 1e-12 * r["R_hist"][-1]
+    Ud = pack(mcg, r["U"], dims)
+    _, counts = mcg.mcg_center_project(Ud, dims)
+    assert counts[0][0] == oracle.vortex_count(dims, oracle.center_project(dims, r["U"]))[0]
