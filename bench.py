@@ -1,0 +1,401 @@
+"""Benchmark: MCG site-updates/s and time to dV_U < 1e-10 on the 20^3 x 40
+preconditioning workload (Sec. II.B / Sec. III: stout smearing rho = 0.1 with
+n in {0, 4, 10, 20} sweeps, each level conducted independently from the same
+field), batched/mixed-precision form against the plain FP64 GPU sweep.
+
+One step = the whole hot path over one synthetic field: smear (one chain,
+snapshots at every level), MCG-fix the smeared fields as a batch, apply each
+transform to a copy of the original, MCG-fix the preconditioned fields as a
+batch, center-project and count P-vortices, plaquettes (mcg_precondition_levels).
+A site-update is one site of one parity with all three SU(2) subgroups, so a
+full sweep of one field is V = 320 000 site-updates.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MCG site-updates/s & time-to-ΔR<1e-10 at 20^3x40: batched/mixed vs plain FP64"
+UNIT = "site-updates/s"
+DIMS = (20, 20, 20, 40)
+LEVELS = (0, 4, 10, 20)
+RHO = 0.1
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-FP64 comparison run")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--dims", type=int, nargs=4, default=list(DIMS))
+    ap.add_argument("--levels", type=int, nargs="+", default=list(LEVELS))
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampler (nvidia-smi during the timed region)
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_sample(U, dims, seconds: float):
+    """Oracle MCG sweeps on the workload field (identity start), bounded to
+    about `seconds` of CPU work; returns (site-updates/s, sweeps, threads)."""
+    import oracle
+
+    cores = len(os.sched_getaffinity(0))
+    oracle.set_threads(cores)
+    V = 1
+    for d in dims:
+        V *= d
+    t0 = time.perf_counter()
+    r = oracle.fix(dims, U, None, tol=-1e300, max_sweeps=1, reunit_every=0)
+    t1 = time.perf_counter() - t0
+    n = max(1, min(200, int(seconds / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.fix(dims, r["U"], r["G"], tol=-1e300, max_sweeps=n, reunit_every=0)
+    dt = time.perf_counter() - t0
+    return n * V / dt, n, cores
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_0807_0264_gb300 import synth
+
+    dims = tuple(args.dims)
+    U = synth.make_field(dims, synth.W_PLAQ_06, 0)
+    import oracle
+
+    cores = len(os.sched_getaffinity(0))
+    oracle.set_threads(cores)
+    V = 1
+    for d in dims:
+        V *= d
+    per_step = max(1, int(os.environ.get("MCG_REF_SWEEPS_PER_STEP", "2")))
+    state = oracle.fix(dims, U, None, tol=-1e300, max_sweeps=1, reunit_every=0)
+    for _ in range(args.warmup):
+        state = oracle.fix(dims, state["U"], state["G"], tol=-1e300, max_sweeps=1, reunit_every=0)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        state = oracle.fix(dims, state["U"], state["G"], tol=-1e300, max_sweeps=per_step, reunit_every=0)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = per_step * V / (ms / 1e3)
+    sample = f"{per_step} oracle MCG sweeps per step on the {dims[0]}x{dims[1]}x{dims[2]}x{dims[3]} field"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": config_of(args, "oracle"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(args, form):
+    d = tuple(args.dims)
+    return {"workload": f"Sec. II.B preconditioned MCG, {d[0]}x{d[1]}x{d[2]}x{d[3]} SU(3), stout rho={RHO} "
+                        f"n in {list(args.levels)}, levels batched, dV_U<1e-10",
+            "lattice": list(d), "levels": list(args.levels), "rho": RHO, "tol": 1e-10, "form": form,
+            "field": "synthetic g(x) exp(i w theta.lambda/2) g(x+mu)^dag, w=0.4326 (plaquette 0.60), seed 0",
+            "l2": "inputs larger than L2 (184 MB FP64 field, 4 x 184 MB outputs)"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    from paper_0807_0264_gb300 import mcg, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dims = tuple(args.dims)
+    V = 1
+    for d in dims:
+        V *= d
+    levels = list(args.levels)
+    # each rank is an independent replica on its own synthetic field
+    U_host = synth.make_field(dims, synth.W_PLAQ_06, rank)
+    canon_pinned = torch.from_numpy(U_host).unsqueeze(0).pin_memory()
+    canon_dev = canon_pinned.to(dev)
+    U = mcg.mcg_pack_links(canon_dev, dims, mcg.F64)
+    nl = len(levels)
+    U_out = mcg.empty_links(dims, nl, mcg.F64, dev)
+    G_out = mcg.empty_gauge(dims, nl, mcg.F64, dev)
+    Z_out = torch.empty((nl, 4, 2, V // 2), dtype=torch.int8, device=dev)
+    mixed = mcg.Params(tol=1e-10, max_sweeps=8000, check_every=25, reunit_every=50, fp32_sweeps=8000,
+                       fp32_tol=float(os.environ.get("MCG_FP32_TOL", "1e-10")), fp32_window=25,
+                       fp32_overrelax=float(os.environ.get("MCG_OMEGA", "1.7")))
+    stream = torch.cuda.current_stream(dev)
+
+    def step(params, smear_prec):
+        return mcg.mcg_precondition_levels(U, dims, levels, params, rho=RHO, eps=1.0, smear_precision=smear_prec,
+                                           U_out=U_out, G_out=G_out, Z_out=Z_out)[3]
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def max_over_ranks(x: float) -> float:
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x: float) -> float:
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    for _ in range(args.warmup):
+        res = step(mixed, mcg.F32)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches0 = mcg.mcg_kernel_launches()
+    with Clocks(local) as clk:
+        barrier()
+        e0.record(stream)
+        site_updates = 0
+        for _ in range(args.steps):
+            res = step(mixed, mcg.F32)
+            site_updates += sum(r["sweeps_smeared"] + r["sweeps_fixed"] for r in res) * V
+        e1.record(stream)
+        barrier()
+    launches = mcg.mcg_kernel_launches() - launches0
+    ms_total = max_over_ranks(e0.elapsed_time(e1))
+    ms = ms_total / args.steps
+    total_updates = sum_over_ranks(site_updates)
+    value = total_updates / (ms_total / 1e3)
+    mixed_res = res
+    sw32 = sum(r["sweeps_fp32"] for r in res)
+    sw_all = sum(r["sweeps_smeared"] + r["sweeps_fixed"] for r in res)
+
+    # plain FP64 comparison (the paper's relaxation, FP64 throughout) on the
+    # unpreconditioned level: it is capped, because on this field it creeps
+    # (dV_U ~ 5e-10 per sweep for 1e4+ sweeps); the mixed form is timed on the
+    # same single fix for a like-for-like ratio
+    plain_info = None
+    if not args.no_plain:
+        cap = int(os.environ.get("MCG_PLAIN_CAP", "4000"))
+        one = mcg.Params(tol=1e-10, max_sweeps=cap, check_every=50, reunit_every=50)
+        Up = U.clone()
+        Gp = mcg.identity_gauge(dims, 1, mcg.F64, dev)
+        barrier()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        pr = mcg.mcg_fix(Up, Gp, dims, one, history=True)
+        p1.record(stream)
+        barrier()
+        pms = max_over_ranks(p0.elapsed_time(p1))
+        import numpy as np
+
+        h = pr["R_hist"][0] / (36.0 * V)
+        d = np.diff(h)
+        info = {"level": 0, "cap_sweeps": cap, "sweeps": pr["sweeps"][0], "converged": pr["converged"],
+                "ms": pms, "ms_per_sweep": pms / max(1, pr["sweeps"][0]), "V": float(h[-1]),
+                "dV_last": float(d[-1]) if len(d) else None}
+        if not pr["converged"] and len(d) > 1000 and d[-1] > 0:
+            # dV_U(k) ~ C exp(-k / tau) fitted over the last 1000 sweeps
+            k = np.arange(len(d) - 1000, len(d))
+            sl = np.polyfit(k, np.log(np.maximum(d[-1000:], 1e-300)), 1)[0]
+            if sl < 0:
+                tau = -1.0 / sl
+                extra = tau * np.log(d[-1] / 1e-10)
+                info["fit_tau_sweeps"] = float(tau)
+                info["extrapolated_sweeps_to_tol"] = float(len(d) + max(0.0, extra))
+                info["extrapolated_ms_to_converged"] = float(info["extrapolated_sweeps_to_tol"] * info["ms_per_sweep"])
+        Um = U.clone()
+        Gm = mcg.identity_gauge(dims, 1, mcg.F64, dev)
+        barrier()
+        p0.record(stream)
+        mr = mcg.mcg_fix(Um, Gm, dims, mixed)
+        p1.record(stream)
+        barrier()
+        mms = max_over_ranks(p0.elapsed_time(p1))
+        info["mixed_same_fix"] = {"ms": mms, "sweeps": mr["sweeps"][0], "converged": mr["converged"],
+                                  "V": mr["R"][0] / (36.0 * V)}
+        info["speedup_lower_bound"] = pms / mms if mr["converged"] else None
+        if "extrapolated_ms_to_converged" in info and mr["converged"]:
+            info["speedup_extrapolated"] = info["extrapolated_ms_to_converged"] / mms
+        if pr["converged"] and mr["converged"]:
+            info["speedup"] = pms / mms
+        plain_info = info
+        del Up, Gp, Um, Gm
+
+    # dominant kernel: per-launch durations of the FP32 and FP64 half-sweep,
+    # L2 flushed between launches, on a scratch copy of the field
+    Uc = U.clone()
+    Gc = mcg.identity_gauge(dims, 1, mcg.F64, dev)
+    U32 = mcg.mcg_convert(Uc, mcg.F32)
+    G32 = mcg.identity_gauge(dims, 1, mcg.F32, dev)
+    t32 = mcg.mcg_time_halfsweep(U32, G32, dims, parity=1, nreps=20, flush_l2=True)
+    t32_even = mcg.mcg_time_halfsweep(U32, G32, dims, parity=0, nreps=20, flush_l2=True)
+    t64 = mcg.mcg_time_halfsweep(Uc, Gc, dims, parity=1, nreps=5, flush_l2=True)
+    del Uc, Gc, U32, G32
+    sw64 = sw_all - sw32
+    share32 = sw32 * (t32 + t32_even)
+    share64 = sw64 * 2 * t64
+    vh = V // 2
+    bytes32 = vh * (8 * 72 * 2 + 72 * 2)  # 8 links read+write, Omega read+write, FP32
+    if share32 >= share64:
+        achieved = bytes32 / ((t32 + t32_even) / 2 / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": "k_halfsweep<float>", "achieved": achieved, "peak": 6780.0,
+                "unit": "GB/s", "frac": achieved / 6780.0, "traffic": None,
+                "algorithmic_bytes_per_launch": bytes32, "ms_per_launch": (t32 + t32_even) / 2,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    else:
+        bytes64 = 2 * bytes32
+        achieved = bytes64 / (t64 / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": "k_halfsweep<double>", "achieved": achieved, "peak": 6780.0,
+                "unit": "GB/s", "frac": achieved / 6780.0, "traffic": None,
+                "algorithmic_bytes_per_launch": bytes64, "ms_per_launch": t64,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    roof["kernel_ms"] = {"fp32_odd": t32, "fp32_even": t32_even, "fp64_odd": t64}
+    roof["step_share_estimate"] = {"fp32": share32 / max(share32 + share64, 1e-9),
+                                   "fp64": share64 / max(share32 + share64, 1e-9)}
+
+    # end to end through the public API: host canonical field in, results out
+    barrier()
+    z_host = torch.empty((nl, V, 4), dtype=torch.int8).pin_memory()
+    h0 = torch.cuda.Event(enable_timing=True)
+    h1 = torch.cuda.Event(enable_timing=True)
+    h0.record(stream)
+    e2e_updates = 0
+    for _ in range(args.steps):
+        canon_dev.copy_(canon_pinned, non_blocking=True)
+        Ue = mcg.mcg_pack_links(canon_dev, dims, mcg.F64)
+        r2 = mcg.mcg_precondition_levels(Ue, dims, levels, mixed, rho=RHO, eps=1.0, smear_precision=mcg.F32,
+                                         U_out=U_out, G_out=G_out, Z_out=Z_out)[3]
+        z_host.copy_(mcg.mcg_unpack_center(Z_out, dims), non_blocking=True)
+        e2e_updates += sum(r["sweeps_smeared"] + r["sweeps_fixed"] for r in r2) * V
+    h1.record(stream)
+    barrier()
+    e2e_ms = max_over_ranks(h0.elapsed_time(h1))
+    e2e_value = sum_over_ranks(e2e_updates) / (e2e_ms / 1e3)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, n, cores = oracle_sample(U_host, dims, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n} oracle FP64 MCG sweeps of the {dims[0]}x{dims[1]}x{dims[2]}x{dims[3]} workload field"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": config_of(args, f"batched levels, FP32 smearing, FP32 sweeps (over-relaxed, omega="
+                                          f"{mixed.fp32_overrelax}) then FP64 plain relaxation to dV_U<1e-10"),
+                "ttc": {"mixed_ms_to_converged": ms, "plain_fp64": plain_info,
+                        "sweeps": sw_all, "sweeps_fp32": sw32,
+                        "V_fixed": [r["V_fixed"] for r in mixed_res],
+                        "V_smeared": [r["V_smeared"] for r in mixed_res],
+                        "vortex_density": [r["vortex_density"] for r in mixed_res],
+                        "plaquette_in": mixed_res[0]["plaquette_in"],
+                        "plaquette_out": [r["plaquette_out"] for r in mixed_res],
+                        "converged": all(r["status"] == 0 for r in mixed_res)},
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": canon_pinned.numel() * 16,
+                        "d2h_bytes_per_step": z_host.numel(), "ms_per_step": e2e_ms / args.steps},
+                "clocks": clk.summary(), "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

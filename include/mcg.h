@@ -75,11 +75,19 @@ typedef struct {
     double tol;        /* stop threshold on the per-sweep change of V_U (1e-10) */
     int max_sweeps;    /* upper bound on full sweeps (even + odd half-sweep)    */
     int check_every;   /* sweeps between host-side convergence polls (>= 1)     */
-    int reunit_every;  /* re-unitarise links and Omega every n sweeps (0: off)  */
+    int reunit_every;  /* FP64 sweeps: re-unitarise links and Omega every n     */
+                       /* sweeps (0: off).  FP32 sweeps re-unitarise in FP32    */
+                       /* every sweep inside the sweep kernel.                  */
     int fp32_sweeps;   /* MCG_F64 fields only: run up to this many sweeps in a  */
                        /* FP32 phase before the FP64 sweeps (0: plain FP64)     */
-    double fp32_tol;   /* FP32 phase stops early when its dV_U < fp32_tol       */
-    int fp32_reunit_every; /* FP32 phase: re-unitarise every n sweeps          */
+    double fp32_tol;   /* FP32 phase stops once its dV_U per sweep, averaged    */
+    int fp32_window;   /* over the last fp32_window (1..31) sweeps, is below    */
+                       /* fp32_tol (FP32 rounding makes single-sweep dV noisy)  */
+    double fp32_overrelax; /* FP32 phase only: over-relaxation omega in (0,2); */
+                       /* 1 = the plain relaxation.  Each subgroup step then    */
+                       /* applies normalise((1-omega) + omega a) instead of a.  */
+                       /* Not part of the paper's method; FP64 sweeps always    */
+                       /* use the plain relaxation.                             */
 } mcg_params;
 
 /* Per-field result of mcg_precondition_fix (Sec. II.B pipeline). */
@@ -205,6 +213,42 @@ int mcg_center_project(const void* U, int8_t* Z, long long* counts, const mcg_la
 int mcg_precondition_fix(void* U, void* G, int8_t* Z, const mcg_lattice* lat, const mcg_params* params,
                          double rho, double eps, int nsmear, int smear_precision, mcg_precond_result* results,
                          cudaStream_t stream);
+
+/*
+ * The Sec. II.B experiment over several preconditioning levels of one field,
+ * batched: Sec. III scans the number of smearing sweeps (0, 4, ..., 20), each
+ * preconditioning conducted independently from the same original field.
+ * One smearing chain of U produces the smeared field at every requested level
+ * (nsmear: host array, nlevels entries, non-decreasing; 0 = no
+ * preconditioning); the smeared fields are MCG-fixed as one batch; each
+ * level's transform (re-unitarised) is applied to a copy of U; the
+ * preconditioned copies are MCG-fixed as one batch; then center projection,
+ * P-vortex counts and plaquettes per level.
+ * U: one input field (lat->nfields must be 1), not modified.
+ * U_out: nlevels fields (device) receiving the fixed fields; G_out: nlevels
+ * transforms (U_out[l] = U^G_out[l]); Z_out (device int8, nlevels fields, may
+ * be NULL): center sectors.  results: host, nlevels entries.
+ * Returns MCG_OK or MCG_NOT_CONVERGED.  Synchronises.
+ */
+int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_out, const mcg_lattice* lat,
+                            const mcg_params* params, double rho, double eps, const int* nsmear, int nlevels,
+                            int smear_precision, mcg_precond_result* results, cudaStream_t stream);
+
+/* ---- measurement ---------------------------------------------------------- */
+
+/* Mean duration of one launch of the half-sweep kernel (parity 0: even sites;
+ * parity 1: odd sites with the fused R reduction) on one field, over nreps
+ * launches each bracketed by CUDA events on `stream`; with flush_l2 != 0 a
+ * 256 MB buffer is overwritten between launches, outside the timed interval,
+ * so every launch reads its links from HBM.  The sweeps are applied to U and G.
+ * ms_out: host float.  Synchronises.  (Instrumentation; not part of the
+ * paper's method.) */
+int mcg_time_halfsweep(void* U, void* G, const mcg_lattice* lat, int parity, int nreps, int flush_l2, float* ms_out,
+                       cudaStream_t stream);
+
+/* Running total of CUDA kernels this library has enqueued in this process
+ * (kernels inside a CUDA graph count once per graph launch). */
+long long mcg_kernel_launches(void);
 
 #ifdef __cplusplus
 }

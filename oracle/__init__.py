@@ -55,9 +55,9 @@ def _load():
             lib.orc_compose_gauge.argtypes = [L, P, P, P]
             lib.orc_trs_solve.argtypes = [P, P, P]
             lib.orc_trs_solve.restype = I
-            lib.orc_halfsweep.argtypes = [P, P, P, I]
+            lib.orc_halfsweep.argtypes = [P, P, P, I, D]
             lib.orc_halfsweep.restype = L
-            lib.orc_fix.argtypes = [P, P, P, D, I, I, P, P, P]
+            lib.orc_fix.argtypes = [P, P, P, D, I, I, D, P, P, P]
             lib.orc_fix.restype = I
             lib.orc_expm.argtypes = [P, P]
             lib.orc_smear_step.argtypes = [P, P, P, D, D]
@@ -135,15 +135,15 @@ def trs_solve(A, b):
     return a, bool(hard)
 
 
-def halfsweep(dims, U, G, parity: int):
+def halfsweep(dims, U, G, parity: int, omega: float = 1.0):
     """One checkerboard half-sweep; returns (U', G', hard_case_count)."""
     U = _cfield(U).copy()
     G = _cfield(G).copy()
-    hard = _load().orc_halfsweep(_p(_dims(dims)), _p(U), _p(G), int(parity))
+    hard = _load().orc_halfsweep(_p(_dims(dims)), _p(U), _p(G), int(parity), float(omega))
     return U, G, int(hard)
 
 
-def fix(dims, U, G=None, tol: float = 1e-10, max_sweeps: int = 2000, reunit_every: int = 50):
+def fix(dims, U, G=None, tol: float = 1e-10, max_sweeps: int = 2000, reunit_every: int = 50, omega: float = 1.0):
     """MCG relaxation.  Returns dict(U, G, R_hist, sweeps, converged, hard)."""
     U = _cfield(U).copy()
     vol = U.shape[0]
@@ -155,7 +155,7 @@ def fix(dims, U, G=None, tol: float = 1e-10, max_sweeps: int = 2000, reunit_ever
     sweeps = ctypes.c_int(0)
     hard = ctypes.c_long(0)
     rc = _load().orc_fix(_p(_dims(dims)), _p(U), _p(G), float(tol), int(max_sweeps), int(reunit_every),
-                         _p(R_hist), ctypes.byref(sweeps), ctypes.byref(hard))
+                         float(omega), _p(R_hist), ctypes.byref(sweeps), ctypes.byref(hard))
     n = sweeps.value
     return dict(U=U, G=G, R_hist=R_hist[: n + 1], sweeps=n, converged=(rc == 0), hard=int(hard.value))
 

@@ -402,7 +402,7 @@ static void subgroup_coeffs(const cplx* M, int p, int q, int r, int backward, cp
  * subgroup element G maximising sum over the 8 links at x of |tr|^2, then
  * U_mu(x) <- G U_mu(x), U_mu(x-mu) <- U_mu(x-mu) G^dag, Omega(x) <- G Omega(x).
  * Returns the number of hard-case solves. */
-static int site_update(const geom* g, cplx* U, cplx* Om, long x) {
+static int site_update(const geom* g, cplx* U, cplx* Om, long x, double omega) {
     static const int PQ[3][3] = {{0, 1, 2}, {0, 2, 1}, {1, 2, 0}};
     int hard = 0;
     cplx* F[4];
@@ -424,6 +424,14 @@ static int site_update(const geom* g, cplx* U, cplx* Om, long x) {
         }
         double a[4];
         hard += orc_trs_solve(A, b, a);
+        if (omega != 1.0) {
+            /* over-relaxation: a -> normalise((1 - omega) e0 + omega a), the
+             * truncated form of g^omega (not part of the paper's method) */
+            a[0] = (1.0 - omega) + omega * a[0];
+            for (int k = 1; k < 4; ++k) a[k] *= omega;
+            double an = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
+            for (int k = 0; k < 4; ++k) a[k] /= an;
+        }
         cplx g11 = a[0] + I * a[3], g12 = a[2] + I * a[1];
         cplx g21 = -a[2] + I * a[1], g22 = a[0] - I * a[3];
         for (int mu = 0; mu < 4; ++mu) {
@@ -453,12 +461,12 @@ static int site_update(const geom* g, cplx* U, cplx* Om, long x) {
 /* Update every site of one parity (0: x+y+z+t even).  Same-parity sites share
  * no link, so the order within the parity does not matter.  Returns the number
  * of hard-case local solves. */
-long orc_halfsweep(const int* dims, cplx* U, cplx* Om, int parity) {
+long orc_halfsweep(const int* dims, cplx* U, cplx* Om, int parity, double omega) {
     geom g = make_geom(dims);
     long hard = 0;
 #pragma omp parallel for schedule(static) reduction(+ : hard)
     for (long x = 0; x < g.vol; ++x)
-        if (parity_of(&g, x) == parity) hard += site_update(&g, U, Om, x);
+        if (parity_of(&g, x) == parity) hard += site_update(&g, U, Om, x, omega);
     return hard;
 }
 
@@ -466,10 +474,12 @@ long orc_halfsweep(const int* dims, cplx* U, cplx* Om, int parity) {
  * MCG relaxation (Sec. II.A, II.B): full sweeps (even then odd half-sweep)
  * until V_U(k) - V_U(k-1) < tol or max_sweeps, where V_U = R / (9 * 4V).
  * Every reunit_every sweeps (if > 0) links and Omega are re-unitarised.
+ * omega = 1 is the plain relaxation; omega != 1 over-relaxes each subgroup
+ * step (an optional accelerator, not described in the paper).
  * R_hist[0..sweeps] receives R before the first sweep and after each sweep.
  * Returns 0 if converged, 1 if max_sweeps was reached.
  */
-int orc_fix(const int* dims, cplx* U, cplx* Om, double tol, int max_sweeps, int reunit_every,
+int orc_fix(const int* dims, cplx* U, cplx* Om, double tol, int max_sweeps, int reunit_every, double omega,
             double* R_hist, int* sweeps_out, long* hard_out) {
     geom g = make_geom(dims);
     double norm = 1.0 / (9.0 * 4.0 * (double)g.vol);
@@ -478,8 +488,8 @@ int orc_fix(const int* dims, cplx* U, cplx* Om, double tol, int max_sweeps, int 
     long hard = 0;
     int k;
     for (k = 1; k <= max_sweeps; ++k) {
-        hard += orc_halfsweep(dims, U, Om, 0);
-        hard += orc_halfsweep(dims, U, Om, 1);
+        hard += orc_halfsweep(dims, U, Om, 0, omega);
+        hard += orc_halfsweep(dims, U, Om, 1, omega);
         if (reunit_every > 0 && k % reunit_every == 0) {
             orc_reunitarise_field(g.vol * 4, U);
             orc_reunitarise_field(g.vol, Om);

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -40,6 +41,12 @@ int cuda_fail(cudaError_t e, const char* what) {
     set_error(buf);
     return MCG_CUDA_ERROR;
 }
+
+// ---------------------------------------------------------------------------
+// launch accounting
+// ---------------------------------------------------------------------------
+static std::atomic<long long> g_launches{0};
+void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------------------
 // scratch: grow-only named buffers per device
@@ -167,8 +174,11 @@ static int check_params(const mcg_params* p) {
     if (!p) return fail(MCG_BAD_ARG, "params is NULL");
     if (p->max_sweeps < 0) return fail(MCG_BAD_ARG, "max_sweeps must be >= 0");
     if (p->check_every < 1) return fail(MCG_BAD_ARG, "check_every must be >= 1");
-    if (p->reunit_every < 0 || p->fp32_sweeps < 0 || p->fp32_reunit_every < 0)
-        return fail(MCG_BAD_ARG, "negative schedule parameter");
+    if (p->reunit_every < 0 || p->fp32_sweeps < 0) return fail(MCG_BAD_ARG, "negative schedule parameter");
+    if (p->fp32_sweeps > 0 && !(p->fp32_overrelax > 0.0 && p->fp32_overrelax < 2.0))
+        return fail(MCG_BAD_ARG, "fp32_overrelax must be in (0, 2)");
+    if (p->fp32_sweeps > 0 && (p->fp32_window < 1 || p->fp32_window > 31))
+        return fail(MCG_BAD_ARG, "fp32_window must be in 1..31");
     if (!(p->tol == p->tol)) return fail(MCG_BAD_ARG, "tol is NaN");
     return 0;
 }
@@ -212,8 +222,8 @@ static int fix_impl(void* U, void* G, const mcg_lattice* lat, const Geom& g, con
             fds[f].norm = norm;
         }
         const int cap = std::min(prm->fp32_sweeps, prm->max_sweeps);
-        rc = run_fix_phase<float>(fds, d_state, h_state, d_hist, hist_len, prm->fp32_tol, prm->fp32_reunit_every, cap,
-                                  prm->check_every, true, st);
+        rc = run_fix_phase<float>(fds, d_state, h_state, d_hist, hist_len, prm->fp32_tol, prm->fp32_window,
+                                  prm->fp32_overrelax, 0, cap, prm->check_every, true, st);
         if (rc) return rc;
         for (int f = 0; f < nf; ++f) s32[f] = h_state[f].sweep;
         // hand-off: FP64 re-unitarised transform applied to the FP64 links
@@ -228,11 +238,11 @@ static int fix_impl(void* U, void* G, const mcg_lattice* lat, const Geom& g, con
         fds[f].norm = norm;
     }
     if (lat->precision == MCG_F64)
-        rc = run_fix_phase<double>(fds, d_state, h_state, d_hist, hist_len, prm->tol, prm->reunit_every,
+        rc = run_fix_phase<double>(fds, d_state, h_state, d_hist, hist_len, prm->tol, 1, 1.0, prm->reunit_every,
                                    prm->max_sweeps, prm->check_every, fresh, st);
     else
-        rc = run_fix_phase<float>(fds, d_state, h_state, d_hist, hist_len, prm->tol, prm->reunit_every,
-                                  prm->max_sweeps, prm->check_every, fresh, st);
+        rc = run_fix_phase<float>(fds, d_state, h_state, d_hist, hist_len, prm->tol, 1, 1.0, 0, prm->max_sweeps,
+                                  prm->check_every, fresh, st);
     if (rc) return rc;
     bool all = true;
     for (int f = 0; f < nf; ++f) {
@@ -464,6 +474,118 @@ int mcg_precondition_fix(void* U, void* G, int8_t* Z, const mcg_lattice* lat, co
         r.sweeps_smeared = sw_s[f];
         r.sweeps_fixed = sw_f[f];
         r.sweeps_fp32 = sw32_s[f] + sw32_f[f];
+        r.status = status;
+    }
+    return status;
+}
+
+long long mcg_kernel_launches(void) { return g_launches.load(); }
+
+int mcg_time_halfsweep(void* U, void* G, const mcg_lattice* lat, int parity, int nreps, int flush_l2, float* ms_out,
+                       cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if (!U || !G || !ms_out) return fail(MCG_BAD_ARG, "null pointer");
+    if (lat->nfields != 1) return fail(MCG_BAD_ARG, "mcg_time_halfsweep takes one field");
+    if (nreps < 1 || (parity != 0 && parity != 1)) return fail(MCG_BAD_ARG, "nreps >= 1, parity 0 or 1");
+    if (lat->precision == MCG_F64) return time_halfsweep<double>(U, G, g, parity, nreps, flush_l2, ms_out, stream);
+    return time_halfsweep<float>(U, G, g, parity, nreps, flush_l2, ms_out, stream);
+}
+
+int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_out, const mcg_lattice* lat,
+                            const mcg_params* params, double rho, double eps, const int* nsmear, int nlevels,
+                            int smear_precision, mcg_precond_result* results, cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if ((rc = check_params(params))) return rc;
+    if (lat->nfields != 1) return fail(MCG_BAD_ARG, "mcg_precondition_levels takes one input field");
+    if (!U || !U_out || !G_out || !nsmear || !results) return fail(MCG_BAD_ARG, "null pointer");
+    if (nlevels < 1) return fail(MCG_BAD_ARG, "nlevels must be >= 1");
+    if (smear_precision != MCG_F64 && smear_precision != MCG_F32) return fail(MCG_BAD_ARG, "bad smear precision");
+    for (int l = 0; l < nlevels; ++l)
+        if (nsmear[l] < 0 || (l > 0 && nsmear[l] < nsmear[l - 1]))
+            return fail(MCG_BAD_ARG, "nsmear must be non-negative and non-decreasing");
+    const int prec = lat->precision;
+    const size_t le = link_elems(g), ge = gauge_elems(g), eb = elem_bytes(prec), seb = elem_bytes(smear_precision);
+    if (overlap(U, eb * le, U_out, eb * le * nlevels)) return fail(MCG_BAD_ARG, "U and U_out overlap");
+    const double norm = 1.0 / (9.0 * 8.0 * g.vh);
+    double plaq_in = 0;
+    if ((rc = compute_plaquette(U, prec, g, 1, &plaq_in, stream))) return rc;
+    // smeared levels: one smearing chain, snapshots at each requested level
+    std::vector<int> smeared;
+    for (int l = 0; l < nlevels; ++l)
+        if (nsmear[l] > 0) smeared.push_back(l);
+    const int ns = (int)smeared.size();
+    std::vector<double> Rs(std::max(ns, 1), 0.0), Rf(nlevels);
+    std::vector<int> sw_s(std::max(ns, 1), 0), sw32_s(std::max(ns, 1), 0), sw_f(nlevels), sw32_f(nlevels);
+    int status = MCG_OK;
+    // every level starts from the input field and the identity transform
+    for (int l = 0; l < nlevels; ++l)
+        MCG_CK(cudaMemcpyAsync((char*)U_out + eb * le * l, U, eb * le, cudaMemcpyDeviceToDevice, stream));
+    if ((rc = launch_identity_gauge(G_out, prec, g, nlevels, stream))) return rc;
+    if (ns > 0) {
+        void* cur = scratch_device("lev.cur", seb * le, &rc);
+        if (rc) return rc;
+        void* tmp = scratch_device("lev.tmp", seb * le, &rc);
+        if (rc) return rc;
+        void* Sp = scratch_device("lev.Sp", eb * le * ns, &rc);
+        if (rc) return rc;
+        void* W = scratch_device("lev.W", eb * ge * ns, &rc);
+        if (rc) return rc;
+        if ((rc = launch_convert(U, prec, cur, smear_precision, le, stream))) return rc;
+        int done_steps = 0;
+        for (int k = 0; k < ns; ++k) {
+            const int steps = nsmear[smeared[k]] - done_steps;
+            if (steps > 0) {
+                if ((rc = run_smear(cur, tmp, smear_precision, g, 1, rho, eps, steps, stream))) return rc;
+                std::swap(cur, tmp);
+                done_steps += steps;
+            }
+            if ((rc = launch_convert(cur, smear_precision, (char*)Sp + eb * le * k, prec, le, stream))) return rc;
+        }
+        if (smear_precision != prec && (rc = launch_reunitarise(Sp, 0, prec, g, ns, stream))) return rc;
+        if ((rc = launch_identity_gauge(W, prec, g, ns, stream))) return rc;
+        mcg_lattice lb = *lat;
+        lb.nfields = ns;
+        rc = fix_impl(Sp, W, &lb, g, params, Rs.data(), sw_s.data(), sw32_s.data(), nullptr, stream);
+        if (rc != MCG_OK && rc != MCG_NOT_CONVERGED) return rc;
+        if (rc == MCG_NOT_CONVERGED) status = MCG_NOT_CONVERGED;
+        for (int k = 0; k < ns; ++k)
+            MCG_CK(cudaMemcpyAsync((char*)G_out + eb * ge * smeared[k], (char*)W + eb * ge * k, eb * ge,
+                                   cudaMemcpyDeviceToDevice, stream));
+        if ((rc = launch_reunitarise(G_out, 1, prec, g, nlevels, stream))) return rc;
+        if ((rc = launch_apply_gauge(U_out, G_out, prec, g, nlevels, stream))) return rc;
+    }
+    mcg_lattice lb = *lat;
+    lb.nfields = nlevels;
+    rc = fix_impl(U_out, G_out, &lb, g, params, Rf.data(), sw_f.data(), sw32_f.data(), nullptr, stream);
+    if (rc != MCG_OK && rc != MCG_NOT_CONVERGED) return rc;
+    if (rc == MCG_NOT_CONVERGED) status = MCG_NOT_CONVERGED;
+    int8_t* Zb = Z_out;
+    if (!Zb) {
+        Zb = (int8_t*)scratch_device("lev.Z", 8 * (size_t)g.vh * nlevels, &rc);
+        if (rc) return rc;
+    }
+    std::vector<long long> counts(7 * (size_t)nlevels);
+    std::vector<double> plaq_out(nlevels);
+    if ((rc = compute_center(U_out, prec, Zb, g, nlevels, counts.data(), stream))) return rc;
+    if ((rc = compute_plaquette(U_out, prec, g, nlevels, plaq_out.data(), stream))) return rc;
+    for (int l = 0; l < nlevels; ++l) {
+        mcg_precond_result& r = results[l];
+        int k = -1;
+        for (int j = 0; j < ns; ++j)
+            if (smeared[j] == l) k = j;
+        r.V_smeared = k >= 0 ? Rs[k] * norm : 0.0;
+        r.sweeps_smeared = k >= 0 ? sw_s[k] : 0;
+        r.V_fixed = Rf[l] * norm;
+        r.plaquette_in = plaq_in;
+        r.plaquette_out = plaq_out[l];
+        r.vortices = counts[7 * l];
+        r.vortex_density = (double)counts[7 * l] / (6.0 * 2.0 * g.vh);
+        r.sweeps_fixed = sw_f[l];
+        r.sweeps_fp32 = (k >= 0 ? sw32_s[k] : 0) + sw32_f[l];
         r.status = status;
     }
     return status;

@@ -404,6 +404,7 @@ int launch_convert(const void* src, int sp, void* dst, int dp, size_t n, cudaStr
     else
         k_convert<float, float><<<nb, FT, 0, st>>>((const cplx<float>*)src, (cplx<float>*)dst, n);
     MCG_CK(cudaGetLastError());
+    note_launches(1);
     return 0;
 }
 
@@ -430,6 +431,7 @@ int launch_pack(const double* canon, void* soa, int prec, const Geom& g, int nfi
             k_pack_gauge<float><<<nb, FT, 0, st>>>((const double2*)canon, (cplx<float>*)soa, g, nfields, unpack);
     }
     MCG_CK(cudaGetLastError());
+    note_launches(1);
     return 0;
 }
 
@@ -437,6 +439,7 @@ int launch_unpack_center(const int8_t* Z, int8_t* canon, const Geom& g, int nfie
     const long long n = 2LL * g.vh * nfields;
     k_unpack_center<<<blocks_for(n, FT), FT, 0, st>>>(Z, canon, g, nfields);
     MCG_CK(cudaGetLastError());
+    note_launches(1);
     return 0;
 }
 
@@ -447,6 +450,7 @@ int launch_identity_gauge(void* G, int prec, const Geom& g, int nfields, cudaStr
     else
         k_identity_gauge<float><<<blocks_for(n, FT), FT, 0, st>>>((cplx<float>*)G, g, nfields);
     MCG_CK(cudaGetLastError());
+    note_launches(1);
     return 0;
 }
 
@@ -457,6 +461,7 @@ int launch_apply_gauge(void* U, const void* G, int prec, const Geom& g, int nfie
     else
         k_apply_gauge<float><<<blocks_for(n, FT), FT, 0, st>>>((cplx<float>*)U, (const cplx<float>*)G, g, nfields);
     MCG_CK(cudaGetLastError());
+    note_launches(1);
     return 0;
 }
 
@@ -468,6 +473,7 @@ int launch_reunitarise(void* M, int which, int prec, const Geom& g, int nfields,
     else
         k_reunit_all<float><<<blocks_for(n, FT), FT, 0, st>>>((cplx<float>*)M, per, g, nfields);
     MCG_CK(cudaGetLastError());
+    note_launches(1);
     return 0;
 }
 
@@ -493,6 +499,7 @@ static int reduce_per_field(int which, const void* U, int prec, const Geom& g, i
     }
     k_sum_partials<<<nfields, 256, 0, st>>>(partial, bpf, d_out);
     MCG_CK(cudaGetLastError());
+    note_launches(2);
     MCG_CK(cudaMemcpyAsync(out_host, d_out, sizeof(double) * nfields, cudaMemcpyDeviceToHost, st));
     MCG_CK(cudaStreamSynchronize(st));
     if (which == 0)
@@ -522,6 +529,7 @@ int compute_center(const void* U, int prec, int8_t* Z, const Geom& g, int nfield
     MCG_CK(cudaMemsetAsync(d_counts, 0, sizeof(unsigned long long) * 7 * nfields, st));
     k_vortex_count<<<blocks_for(n, FT), FT, 0, st>>>(Z, g, nfields, d_counts);
     MCG_CK(cudaGetLastError());
+    note_launches(2);
     if (counts_host) {
         MCG_CK(cudaMemcpyAsync(counts_host, d_counts, sizeof(long long) * 7 * nfields, cudaMemcpyDeviceToHost, st));
         MCG_CK(cudaStreamSynchronize(st));
@@ -543,6 +551,7 @@ int launch_handoff(const void* W32, double* U64, double* G64, const Geom& g, int
     k_handoff_gauge<<<blocks_for(n, FT), FT, 0, st>>>((const cplx<float>*)W32, W64, (cplx<double>*)G64, g, nfields);
     k_apply_gauge<double><<<blocks_for(n, FT), FT, 0, st>>>((cplx<double>*)U64, W64, g, nfields);
     MCG_CK(cudaGetLastError());
+    note_launches(2);
     return 0;
 }
 

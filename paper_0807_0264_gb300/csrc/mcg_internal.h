@@ -22,6 +22,11 @@ int cuda_fail(cudaError_t e, const char* what);
         if (e_ != cudaSuccess) return ::mcg::cuda_fail(e_, #call); \
     } while (0)
 
+// ---- launch accounting ------------------------------------------------------
+// Every kernel the library enqueues is counted (graph launches count their
+// kernel nodes); mcg_kernel_launches() reports the running total.
+void note_launches(long long n);
+
 // ---- scratch ----------------------------------------------------------------
 // Named, grow-only device and pinned-host buffers cached per device; freed by
 // mcg_release().
@@ -40,15 +45,18 @@ struct FieldDesc {
     double norm;  // 1 / (9 * 4V)
 };
 
+constexpr int kRing = 32;  // R history kept per field for windowed stop tests
+
 struct FieldState {
     double R_prev;  // R after the previous sweep (or at phase start)
     double R_last;  // R after the last sweep
     int sweep;      // sweeps completed (across phases)
     int done;       // 0 running, 1 converged, 2 sweep cap of the phase reached
     int reunit_pending;
-    int max_sweeps;  // absolute sweep cap of the current phase
-    int fallbacks;   // local solves that needed the FP64 fallback path
-    int pad;
+    int max_sweeps;   // absolute sweep cap of the current phase
+    int fallbacks;    // local solves that needed the FP64 fallback path
+    int phase_start;  // sweep count when the current phase began
+    double ring[kRing];  // R after sweep k stored at k % kRing
 };
 
 struct SweepBatch {
@@ -60,7 +68,9 @@ struct SweepBatch {
     double* R_hist;   // nf x hist_len (may be null)
     int hist_len;
     double tol;
+    int window;  // stop when the dV_U averaged over `window` sweeps < tol
     int reunit_every;
+    double omega;  // over-relaxation parameter (1: plain relaxation)
 };
 
 // Run MCG relaxation on a batch (all fields same precision T) until every
@@ -69,8 +79,16 @@ struct SweepBatch {
 // continue the sweep count in `state` (a new phase).  Returns 0 or an error.
 template <typename T>
 int run_fix_phase(const std::vector<FieldDesc>& fields, FieldState* d_state, FieldState* h_state, double* d_hist,
-                  int hist_len, double tol, int reunit_every, int abs_cap, int check_every, bool fresh,
-                  cudaStream_t stream);
+                  int hist_len, double tol, int window, double omega, int reunit_every, int abs_cap,
+                  int check_every, bool fresh, cudaStream_t stream);
+
+// Time `nreps` launches of one half-sweep kernel (parity 1 includes the fused
+// R reduction) on a single field, each bracketed by CUDA events on `stream`;
+// with flush_l2 a 256 MB buffer is overwritten between launches (outside the
+// timed interval).  Returns the mean per-launch milliseconds in *ms.
+template <typename T>
+int time_halfsweep(void* U, void* G, const Geom& g, int parity, int nreps, int flush_l2, float* ms,
+                   cudaStream_t stream);
 
 template <typename T>
 constexpr int sweep_threads() {

@@ -298,6 +298,7 @@ int run_smear(const void* Uin, void* Uout, int prec, const Geom& g, int nfields,
                                                               (float)rho, (float)cp, (float)cr);
         }
         MCG_CK(cudaGetLastError());
+        note_launches(1);
         src = dst;
     }
     return 0;

@@ -33,14 +33,20 @@ namespace mcg {
 // ---------------------------------------------------------------------------
 // 4x4 symmetric eigen-decomposition (cyclic Jacobi)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float frcp(float x) { return __frcp_rn(x); }
+// FP32 solves use the SFU approximations (rsqrt, reciprocal: ~1-2 ulp); the
+// FP64 fallback path uses IEEE operations.
+__device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float fsqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+__device__ __forceinline__ double fsqrt(double x) { return sqrt(x); }
 
 template <typename T, int P, int Q>
 __device__ __forceinline__ void jrot(T (&S)[4][4], T (&V)[4][4]) {
     const T apq = S[P][Q];
     const T th = (S[Q][Q] - S[P][P]) * T(0.5);
-    const T den = fabs(th) + sqrt(th * th + apq * apq);
+    const T den = fabs(th) + fsqrt(th * th + apq * apq);
     T t = den > T(0) ? apq * frcp(den) : T(0);
     if (th < T(0)) t = -t;
     const T c = rsqrt(T(1) + t * t);
@@ -78,6 +84,7 @@ __device__ __forceinline__ void jacobi4(T (&S)[4][4], T (&V)[4][4], int max_swee
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) fro2 += S[i][j] * S[i][j];
+#pragma unroll 1
     for (int sw = 0; sw < max_sweeps; ++sw) {
         const T off = S[0][1] * S[0][1] + S[0][2] * S[0][2] + S[0][3] * S[0][3] + S[1][2] * S[1][2] +
                       S[1][3] * S[1][3] + S[2][3] * S[2][3];
@@ -102,7 +109,7 @@ __device__ __forceinline__ int trs_from_eigen(const T (&S)[4][4], const T (&V)[4
     T al[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) al[i] = S[i][i];
-    const T bn = sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2] + b[3] * b[3]);
+    const T bn = fsqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2] + b[3] * b[3]);
     T scale = bn;
 #pragma unroll
     for (int i = 0; i < 4; ++i) scale = fmax(scale, fabs(al[i]));
@@ -130,12 +137,12 @@ __device__ __forceinline__ int trs_from_eigen(const T (&S)[4][4], const T (&V)[4
         top[i] = (amax - al[i]) <= deg_tol * scale;
         if (top[i]) btop2 += beta[i] * beta[i];
     }
-    const T btop = sqrt(btop2);
+    const T btop = fsqrt(btop2);
     if (btop <= hard_tol * scale) {
         T coef[4], pn2 = T(0);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            coef[i] = top[i] ? T(0) : beta[i] / (amax - al[i]);
+            coef[i] = top[i] ? T(0) : fdiv(beta[i], amax - al[i]);
             pn2 += coef[i] * coef[i];
         }
         if (pn2 < T(1)) {
@@ -159,7 +166,7 @@ __device__ __forceinline__ int trs_from_eigen(const T (&S)[4][4], const T (&V)[4
 #pragma unroll
             for (int k = 0; k < 4; ++k)
                 if (k == kb) sgn = vm[k] >= T(0) ? T(1) : T(-1);
-            const T t = sqrt(T(1) - pn2) * sgn;
+            const T t = fsqrt(T(1) - pn2) * sgn;
             T n2 = T(0);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -176,6 +183,7 @@ __device__ __forceinline__ int trs_from_eigen(const T (&S)[4][4], const T (&V)[4
     // easy case: root of ||a(mu)|| = 1 right of amax, bracket [amax+btop, amax+||b||]
     T lo = amax + btop, hi = amax + bn, mu = lo;
     const int maxit = sizeof(T) == 8 ? 100 : 40;
+#pragma unroll 1
     for (int it = 0; it < maxit; ++it) {
         T s2 = T(0), s3 = T(0);
 #pragma unroll
@@ -185,14 +193,14 @@ __device__ __forceinline__ int trs_from_eigen(const T (&S)[4][4], const T (&V)[4
             s2 += q;
             s3 += q * r;
         }
-        const T n = sqrt(s2);
+        const T n = fsqrt(s2);
         if (n >= T(1))
             lo = fmax(lo, mu);
         else
             hi = fmin(hi, mu);
-        T next = mu + (n - T(1)) * s2 / s3;
+        T next = mu + fdiv((n - T(1)) * s2, s3);
         if (!(next > lo && next < hi)) next = T(0.5) * (lo + hi);
-        if (fabs(next - mu) <= eps * fabs(mu)) {
+        if (fabs(next - mu) <= T(4) * eps * fabs(mu)) {
             mu = next;
             break;
         }
@@ -202,7 +210,7 @@ __device__ __forceinline__ int trs_from_eigen(const T (&S)[4][4], const T (&V)[4
     T n2 = T(0);
     T coef[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) coef[i] = beta[i] / (mu - al[i]);
+    for (int i = 0; i < 4; ++i) coef[i] = fdiv(beta[i], mu - al[i]);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         a[k] = V[k][0] * coef[0] + V[k][1] * coef[1] + V[k][2] * coef[2] + V[k][3] * coef[3];
@@ -215,6 +223,108 @@ __device__ __forceinline__ int trs_from_eigen(const T (&S)[4][4], const T (&V)[4
     return 0;
 }
 
+// ---------------------------------------------------------------------------
+// Newton on the KKT system from a warm start, certified by LDL^T
+// ---------------------------------------------------------------------------
+// LDL^T of the symmetric 4x4 matrix M (no pivoting).  Returns the smallest
+// pivot relative to the largest in absolute value (negative if M is not
+// positive definite); Dinv receives the inverse pivots.
+template <typename T>
+__device__ __forceinline__ T ldlt4(const T (&M)[4][4], T (&L)[4][4], T (&Dinv)[4]) {
+    T D[4];
+    D[0] = M[0][0];
+    Dinv[0] = frcp(D[0]);
+    L[1][0] = M[1][0] * Dinv[0];
+    L[2][0] = M[2][0] * Dinv[0];
+    L[3][0] = M[3][0] * Dinv[0];
+    D[1] = M[1][1] - L[1][0] * L[1][0] * D[0];
+    Dinv[1] = frcp(D[1]);
+    L[2][1] = (M[2][1] - L[2][0] * L[1][0] * D[0]) * Dinv[1];
+    L[3][1] = (M[3][1] - L[3][0] * L[1][0] * D[0]) * Dinv[1];
+    D[2] = M[2][2] - L[2][0] * L[2][0] * D[0] - L[2][1] * L[2][1] * D[1];
+    Dinv[2] = frcp(D[2]);
+    L[3][2] = (M[3][2] - L[3][0] * L[2][0] * D[0] - L[3][1] * L[2][1] * D[1]) * Dinv[2];
+    D[3] = M[3][3] - L[3][0] * L[3][0] * D[0] - L[3][1] * L[3][1] * D[1] - L[3][2] * L[3][2] * D[2];
+    Dinv[3] = frcp(D[3]);
+    T dmin = fmin(fmin(D[0], D[1]), fmin(D[2], D[3]));
+    T dmax = fmax(fmax(fabs(D[0]), fabs(D[1])), fmax(fabs(D[2]), fabs(D[3])));
+    return dmax > T(0) ? fdiv(dmin, dmax) : T(-1);
+}
+
+template <typename T, typename U>
+__device__ __forceinline__ void ldlt4_solve(const T (&L)[4][4], const T (&Dinv)[4], const U (&r)[4], T (&x)[4]) {
+    T z0 = (T)r[0];
+    T z1 = (T)r[1] - L[1][0] * z0;
+    T z2 = (T)r[2] - L[2][0] * z0 - L[2][1] * z1;
+    T z3 = (T)r[3] - L[3][0] * z0 - L[3][1] * z1 - L[3][2] * z2;
+    z0 *= Dinv[0];
+    z1 *= Dinv[1];
+    z2 *= Dinv[2];
+    z3 *= Dinv[3];
+    x[3] = z3;
+    x[2] = z2 - L[3][2] * x[3];
+    x[1] = z1 - L[2][1] * x[2] - L[3][1] * x[3];
+    x[0] = z0 - L[1][0] * x[1] - L[2][0] * x[2] - L[3][0] * x[3];
+}
+
+// Newton iterations on (mu - A) a = b, |a| = 1 starting from a = (1,0,0,0)
+// (the current links, i.e. no change) with mu its Lagrange estimate.  On
+// success (converged, and mu - A positive definite: the global maximum of the
+// trust-region subproblem) returns true with a normalised, mu, and the LDL^T
+// factors of (mu - A) for later use.
+template <typename T>
+__device__ __forceinline__ bool kkt_newton(const T (&A)[4][4], const T (&b)[4], T (&a)[4], T& mu, T (&L)[4][4],
+                                           T (&Dinv)[4], T& pd) {
+    const T conv = sizeof(T) == 8 ? T(1e-13) : T(2e-6);
+    a[0] = T(1);
+    a[1] = a[2] = a[3] = T(0);
+    mu = A[0][0] + b[0];
+    bool ok = false;
+#pragma unroll 1
+    for (int it = 0; it < 8; ++it) {
+        T M[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) M[i][j] = (i == j ? mu : T(0)) - A[i][j];
+        pd = ldlt4(M, L, Dinv);
+        if (!(fabs(pd) > T(1e-12))) return false;  // singular or NaN
+        T r[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) r[k] = b[k] - (M[k][0] * a[0] + M[k][1] * a[1] + M[k][2] * a[2] + M[k][3] * a[3]);
+        const T sres = T(0.5) * (T(1) - (a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]));
+        T x[4], y[4];
+        ldlt4_solve(L, Dinv, r, x);
+        ldlt4_solve(L, Dinv, a, y);
+        const T ay = a[0] * y[0] + a[1] * y[1] + a[2] * y[2] + a[3] * y[3];
+        const T dmu = fdiv(a[0] * x[0] + a[1] * x[1] + a[2] * x[2] + a[3] * x[3] - sres, ay);
+        T dmax = T(0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const T da = x[k] - dmu * y[k];
+            a[k] += da;
+            dmax = fmax(dmax, fabs(da));
+        }
+        mu += dmu;
+        if (dmax <= conv) {
+            ok = true;
+            break;
+        }
+    }
+    if (!ok) return false;
+    const T inv = rsqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a[k] *= inv;
+    // certificate: mu - A positive definite at the converged multiplier
+    T M[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) M[i][j] = (i == j ? mu : T(0)) - A[i][j];
+    pd = ldlt4(M, L, Dinv);
+    return pd > (sizeof(T) == 8 ? T(1e-12) : T(1e-5));
+}
+
 // FP32 solve of the subproblem given A (symmetric) and b.
 __device__ __forceinline__ int solve_f32(const float (&A)[4][4], const float (&b)[4], float (&a)[4], float& mu,
                                          float (&S)[4][4], float (&V)[4][4]) {
@@ -222,42 +332,52 @@ __device__ __forceinline__ int solve_f32(const float (&A)[4][4], const float (&b
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) S[i][j] = A[i][j];
-    jacobi4<float>(S, V, 8, 1e-7f);
+    jacobi4<float>(S, V, 8, 5e-7f);
     return trs_from_eigen<float>(S, V, b, a, mu);
 }
 
-// Newton refinement of (a, mu) on the KKT system (mu - A) a = b, |a| = 1 with
-// FP64 residuals and the FP32 eigen-decomposition as approximate inverse of
-// (mu - A).  Returns true when the last correction is below FP64 resolution.
+// Newton refinement of (a, mu) on the KKT system (mu - A) a = b, |a| = 1.
+// Residuals are evaluated in FP64; the correction uses the FP32
+// eigen-decomposition (S diagonal, V) at the FP32 multiplier as a fixed
+// approximate inverse of (mu - A), so each step contracts the error by about
+// cond(mu - A) * 1e-7.  Stops once the correction is below 1e-12 (the next one
+// would be below FP64 resolution).  Returns false if that does not happen in
+// 6 steps.
 __device__ __forceinline__ bool kkt_refine(const double (&A)[4][4], const double (&b)[4], const float (&S)[4][4],
-                                           const float (&V)[4][4], double (&a)[4], double& mu) {
+                                           const float (&V)[4][4], const float (&af)[4], float muf, double (&a)[4],
+                                           double& mu) {
+    float d[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) d[i] = __fdividef(1.0f, muf - S[i][i]);
+    float at[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) at[i] = (V[0][i] * af[0] + V[1][i] * af[1] + V[2][i] * af[2] + V[3][i] * af[3]) * d[i];
+    double y[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        y[k] = (double)(V[k][0] * at[0] + V[k][1] * at[1] + V[k][2] * at[2] + V[k][3] * at[3]);
+        a[k] = (double)af[k];
+    }
+    mu = (double)muf;
+    const double inv_ay = 1.0 / (a[0] * y[0] + a[1] * y[1] + a[2] * y[2] + a[3] * y[3]);
+#pragma unroll 1
     for (int it = 0; it < 6; ++it) {
-        double r[4];
+        float rf[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             double acc = fma(-mu, a[k], b[k]);
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc = fma(A[k][j], a[j], acc);
-            r[k] = acc;
+            rf[k] = (float)acc;
         }
         const double s = 0.5 * (1.0 - (a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]));
-        const float muf = (float)mu;
-        float rt[4], at[4];
+        float rt[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float d = __frcp_rn(muf - S[i][i]);
-            rt[i] = (V[0][i] * (float)r[0] + V[1][i] * (float)r[1] + V[2][i] * (float)r[2] + V[3][i] * (float)r[3]) * d;
-            at[i] = (V[0][i] * (float)a[0] + V[1][i] * (float)a[1] + V[2][i] * (float)a[2] + V[3][i] * (float)a[3]) * d;
-        }
-        double x[4], y[4];
+        for (int i = 0; i < 4; ++i) rt[i] = (V[0][i] * rf[0] + V[1][i] * rf[1] + V[2][i] * rf[2] + V[3][i] * rf[3]) * d[i];
+        double x[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            x[k] = (double)(V[k][0] * rt[0] + V[k][1] * rt[1] + V[k][2] * rt[2] + V[k][3] * rt[3]);
-            y[k] = (double)(V[k][0] * at[0] + V[k][1] * at[1] + V[k][2] * at[2] + V[k][3] * at[3]);
-        }
-        const double ax = a[0] * x[0] + a[1] * x[1] + a[2] * x[2] + a[3] * x[3];
-        const double ay = a[0] * y[0] + a[1] * y[1] + a[2] * y[2] + a[3] * y[3];
-        const double dmu = (ax - s) / ay;
+        for (int k = 0; k < 4; ++k) x[k] = (double)(V[k][0] * rt[0] + V[k][1] * rt[1] + V[k][2] * rt[2] + V[k][3] * rt[3]);
+        const double dmu = (a[0] * x[0] + a[1] * x[1] + a[2] * x[2] + a[3] * x[3] - s) * inv_ay;
         double dmax = 0.0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -267,9 +387,25 @@ __device__ __forceinline__ bool kkt_refine(const double (&A)[4][4], const double
         }
         mu += dmu;
         if (!(dmax == dmax)) return false;  // NaN
-        if (dmax <= 1e-15) return true;
+        if (dmax <= 1e-12) return true;
     }
     return false;
+}
+
+// Full FP64 solve (Jacobi + secular), kept out of line: it runs only for the
+// rare local problems the refinement cannot settle.
+__device__ __noinline__ void solve_f64_full(const double* Ain, const double* b_in, double* a_out) {
+    double Sd[4][4], Vd[4][4], bd[4], ad[4], mud;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        bd[i] = b_in[i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) Sd[i][j] = Ain[4 * i + j];
+    }
+    jacobi4<double>(Sd, Vd, 30, 1e-15);
+    trs_from_eigen<double>(Sd, Vd, bd, ad, mud);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a_out[k] = ad[k];
 }
 
 template <typename T>
@@ -277,50 +413,104 @@ struct Solver;
 
 template <>
 struct Solver<float> {
+    // returns 1 when the Jacobi path was needed (Newton failed or uncertified)
     __device__ __forceinline__ static int solve(const float (&A)[4][4], const float (&b)[4], float (&a)[4]) {
-        float S[4][4], V[4][4], mu;
+        float L[4][4], Dinv[4], mu, pd;
+        if (kkt_newton<float>(A, b, a, mu, L, Dinv, pd)) return 0;
+        float S[4][4], V[4][4];
         solve_f32(A, b, a, mu, S, V);
-        return 0;
+        return 1;
     }
 };
+
+// FP64 refinement with the FP32 LDL^T factors of (mu32 - A) as the fixed
+// approximate inverse (same iteration as kkt_refine).
+__device__ __forceinline__ bool kkt_refine_ldlt(const double (&A)[4][4], const double (&b)[4], const float (&L)[4][4],
+                                                const float (&Dinv)[4], const float (&af)[4], float muf, double (&a)[4]) {
+    float yf[4];
+    ldlt4_solve(L, Dinv, af, yf);
+    double y[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        y[k] = (double)yf[k];
+        a[k] = (double)af[k];
+    }
+    double mu = (double)muf;
+    const double inv_ay = 1.0 / (a[0] * y[0] + a[1] * y[1] + a[2] * y[2] + a[3] * y[3]);
+#pragma unroll 1
+    for (int it = 0; it < 6; ++it) {
+        float rf[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            double acc = fma(-mu, a[k], b[k]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc = fma(A[k][j], a[j], acc);
+            rf[k] = (float)acc;
+        }
+        const double s = 0.5 * (1.0 - (a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]));
+        float xf[4];
+        ldlt4_solve(L, Dinv, rf, xf);
+        double x[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) x[k] = (double)xf[k];
+        const double dmu = (a[0] * x[0] + a[1] * x[1] + a[2] * x[2] + a[3] * x[3] - s) * inv_ay;
+        double dmax = 0.0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const double da = fma(-dmu, y[k], x[k]);
+            a[k] += da;
+            dmax = fmax(dmax, fabs(da));
+        }
+        mu += dmu;
+        if (!(dmax == dmax)) return false;
+        if (dmax <= 1e-12) return true;
+    }
+    return false;
+}
 
 template <>
 struct Solver<double> {
     // returns 1 when the full FP64 fallback was used
     __device__ __forceinline__ static int solve(const double (&A)[4][4], const double (&b)[4], double (&a)[4]) {
-        float Af[4][4], bf[4], af[4], S[4][4], V[4][4], muf;
+        float Af[4][4], bf[4], af[4], muf;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             bf[i] = (float)b[i];
 #pragma unroll
             for (int j = 0; j < 4; ++j) Af[i][j] = (float)A[i][j];
         }
-        const int hard = solve_f32(Af, bf, af, muf, S, V);
         bool ok = false;
-        if (!hard) {
-            // conditioning of (mu - A) in FP32 terms: refinement contracts by ~cond * 1e-7
-            float amax = S[0][0], amin = S[0][0];
+        {
+            float L[4][4], Dinv[4], pd;
+            // warm-started FP32 Newton; the refinement contracts by ~cond * 1e-7,
+            // with cond ~ 1 / pd bounded by the pivot test
+            if (kkt_newton<float>(Af, bf, af, muf, L, Dinv, pd) && pd > 2e-4f)
+                ok = kkt_refine_ldlt(A, b, L, Dinv, af, muf, a);
+        }
+        if (!ok) {
+            float S[4][4], V[4][4];
+            const int hard = solve_f32(Af, bf, af, muf, S, V);
+            if (!hard) {
+                float amax = S[0][0], amin = S[0][0];
 #pragma unroll
-            for (int i = 1; i < 4; ++i) {
-                amax = fmaxf(amax, S[i][i]);
-                amin = fminf(amin, S[i][i]);
-            }
-            const float gap = muf - amax;
-            if (gap > 2e-4f * (muf - amin + 1e-30f)) {
-                double mu = (double)muf;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) a[k] = (double)af[k];
-                ok = kkt_refine(A, b, S, V, a, mu);
+                for (int i = 1; i < 4; ++i) {
+                    amax = fmaxf(amax, S[i][i]);
+                    amin = fminf(amin, S[i][i]);
+                }
+                const float gap = muf - amax;
+                if (gap > 2e-4f * (muf - amin + 1e-30f)) {
+                    double mu;
+                    ok = kkt_refine(A, b, S, V, af, muf, a, mu);
+                }
             }
         }
         if (!ok) {
-            double Sd[4][4], Vd[4][4], mud;
+            double Aflat[16];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) Sd[i][j] = A[i][j];
-            jacobi4<double>(Sd, Vd, 30, 1e-15);
-            trs_from_eigen<double>(Sd, Vd, b, a, mud);
+                for (int j = 0; j < 4; ++j) Aflat[4 * i + j] = A[i][j];
+            solve_f64_full(Aflat, b, a);
             return 1;
         }
         const double inv = rsqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
@@ -331,14 +521,9 @@ struct Solver<double> {
 };
 
 // ---------------------------------------------------------------------------
-// link storage for one site's 8 links: registers (FP32) or shared memory (FP64)
+// link storage for one site's 8 links: shared memory, entry-major so that the
+// threads of a warp touch consecutive addresses (conflict-free)
 // ---------------------------------------------------------------------------
-template <typename T>
-struct RegLinks {
-    cplx<T> v[8][9];
-    __device__ __forceinline__ cplx<T>& operator()(int l, int e) { return v[l][e]; }
-};
-
 template <typename T, int NT>
 struct SmemLinks {
     cplx<T>* base;
@@ -348,7 +533,7 @@ struct SmemLinks {
 // One SU(2)-subgroup step on the 8 links (l < 4: forward U_l(x), l >= 4:
 // backward U_{l-4}(x - l)) and Omega(x).  Returns fallback count.
 template <typename T, int P, int Q, int R, typename L>
-__device__ __forceinline__ int subgroup_step(L& lk, cplx<T> (&Om)[9]) {
+__device__ __forceinline__ int subgroup_step(L& lk, cplx<T> (&Om)[9], const T omega) {
     T A[4][4], b[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -381,7 +566,18 @@ __device__ __forceinline__ int subgroup_step(L& lk, cplx<T> (&Om)[9]) {
 #pragma unroll
         for (int j = 0; j < k; ++j) A[k][j] = A[j][k];
     T a[4];
+    asm volatile("" ::: "memory");
     const int fb = Solver<T>::solve(A, b, a);
+    if (omega != T(1)) {
+        // over-relaxation: a -> normalise((1 - omega) e0 + omega a)
+        a[0] = (T(1) - omega) + omega * a[0];
+        a[1] *= omega;
+        a[2] *= omega;
+        a[3] *= omega;
+        const T inv = rsqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a[k] *= inv;
+    }
     const cplx<T> g11 = mk(a[0], a[3]), g12 = mk(a[2], a[1]), g21 = mk(-a[2], a[1]), g22 = mk(a[0], -a[3]);
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
@@ -425,8 +621,10 @@ __device__ __forceinline__ int field_of_block(const FieldDesc* __restrict__ d, i
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
+// Occupancy: FP32 runs 2 blocks of 128 threads per SM (spill-free at <= 255
+// registers); FP64, bound by the FP64 pipe, runs 3 blocks of 64.
 template <typename T, bool ACC, int NT>
-__global__ void __launch_bounds__(NT) k_halfsweep(SweepBatch bt, int parity) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 3 : 2) k_halfsweep(SweepBatch bt, int parity) {
     const int f = field_of_block(bt.desc, bt.nf, blockIdx.x);
     if (bt.state[f].done) return;  // block-uniform
     const FieldDesc fd = bt.desc[f];
@@ -436,10 +634,9 @@ __global__ void __launch_bounds__(NT) k_halfsweep(SweepBatch bt, int parity) {
     const int s = (blockIdx.x - fd.blk0) * NT + threadIdx.x;
     const bool active = s < g.vh;
 
-    using Links = typename std::conditional<sizeof(T) == 8, SmemLinks<T, NT>, RegLinks<T>>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Links lk;
-    if constexpr (sizeof(T) == 8) lk.base = reinterpret_cast<cplx<T>*>(smem_raw);
+    SmemLinks<T, NT> lk;
+    lk.base = reinterpret_cast<cplx<T>*>(smem_raw);
 
     double rsum = 0.0;
     int fb = 0;
@@ -449,21 +646,49 @@ __global__ void __launch_bounds__(NT) k_halfsweep(SweepBatch bt, int parity) {
         int sb[4];
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) sb[mu] = eo_neighbor(g, c, mu, -1);
+        // stage the 8 links in shared memory without passing through registers
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+            for (int e = 0; e < 9; ++e) cp_async<sizeof(cplx<T>)>(&lk(mu, e), &U[lidx(g, mu, parity, e, s)]);
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+            for (int e = 0; e < 9; ++e)
+                cp_async<sizeof(cplx<T>)>(&lk(4 + mu, e), &U[lidx(g, mu, parity ^ 1, e, sb[mu])]);
         cplx<T> Om[9];
 #pragma unroll
-        for (int mu = 0; mu < 4; ++mu)
-#pragma unroll
-            for (int e = 0; e < 9; ++e) lk(mu, e) = U[lidx(g, mu, parity, e, s)];
-#pragma unroll
-        for (int mu = 0; mu < 4; ++mu)
-#pragma unroll
-            for (int e = 0; e < 9; ++e) lk(4 + mu, e) = U[lidx(g, mu, parity ^ 1, e, sb[mu])];
-#pragma unroll
         for (int e = 0; e < 9; ++e) Om[e] = G[gidx(g, parity, e, s)];
+        cp_async_wait_all();
 
-        fb += subgroup_step<T, 0, 1, 2>(lk, Om);
-        fb += subgroup_step<T, 0, 2, 1>(lk, Om);
-        fb += subgroup_step<T, 1, 2, 0>(lk, Om);
+        // compiler barriers: between the phases of the update the links live
+        // in shared memory instead of being carried in registers
+        const T omega = (T)bt.omega;
+        fb += subgroup_step<T, 0, 1, 2>(lk, Om, omega);
+        asm volatile("" ::: "memory");
+        fb += subgroup_step<T, 0, 2, 1>(lk, Om, omega);
+        asm volatile("" ::: "memory");
+        fb += subgroup_step<T, 1, 2, 0>(lk, Om, omega);
+        asm volatile("" ::: "memory");
+        if (sizeof(T) == 4) {
+            // FP32 sweeps re-unitarise in FP32 every sweep (Omega every
+            // half-sweep, the 8 links in the odd one, which touches every link
+            // once): FP32 rounding would otherwise inflate |tr U|^2 by ~1e-6
+            // per sweep and swamp the convergence signal.
+            m3_reunitarise_same(Om);
+            if (ACC) {
+#pragma unroll 1
+                for (int l = 0; l < 8; ++l) {
+                    cplx<T> m[9];
+#pragma unroll
+                    for (int e = 0; e < 9; ++e) m[e] = lk(l, e);
+                    m3_reunitarise_same(m);
+#pragma unroll
+                    for (int e = 0; e < 9; ++e) lk(l, e) = m[e];
+                }
+            }
+            asm volatile("" ::: "memory");
+        }
 
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu)
@@ -489,9 +714,9 @@ __global__ void __launch_bounds__(NT) k_halfsweep(SweepBatch bt, int parity) {
         const double tot = block_sum(rsum, red);
         if (threadIdx.x == 0) bt.partial[blockIdx.x] = tot;
     }
-    if (sizeof(T) == 8) {
-        // count FP64 fallbacks (diagnostic)
-        int w = __reduce_add_sync(0xffffffffu, fb);
+    {
+        // count local solves that left the fast path (diagnostic)
+        const int w = __reduce_add_sync(0xffffffffu, fb);
         if ((threadIdx.x & 31) == 0 && w) atomicAdd(&bt.state[f].fallbacks, w);
     }
 }
@@ -544,13 +769,24 @@ __global__ void __launch_bounds__(256) k_finalize(SweepBatch bt, int mode) {
         st->R_prev = R;
         st->R_last = R;
         st->reunit_pending = 0;
+        st->phase_start = st->sweep;
+        st->ring[st->sweep % kRing] = R;
         st->done = st->sweep >= st->max_sweeps ? 2 : 0;
         return;
     }
     const int k = st->sweep + 1;
     st->sweep = k;
     if (bt.R_hist && k < bt.hist_len) bt.R_hist[(size_t)f * bt.hist_len + k] = R;
-    const double dV = (R - st->R_prev) * fd.norm;
+    // dV per sweep, averaged over the last `window` sweeps of this phase
+    double dV;
+    if (bt.window <= 1) {
+        dV = (R - st->R_prev) * fd.norm;
+    } else if (k - st->phase_start >= bt.window) {
+        dV = (R - st->ring[(k - bt.window) % kRing]) * fd.norm / bt.window;
+    } else {
+        dV = 1e300;
+    }
+    st->ring[k % kRing] = R;
     st->R_prev = R;
     st->R_last = R;
     st->reunit_pending = (bt.reunit_every > 0 && k % bt.reunit_every == 0) ? 1 : 0;
@@ -601,8 +837,8 @@ static int enqueue_sweep(const SweepBatch& bt, size_t smem, cudaStream_t st) {
 
 template <typename T>
 int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, FieldState* h_state, double* d_hist,
-                  int hist_len, double tol, int reunit_every, int abs_cap, int check_every, bool fresh,
-                  cudaStream_t stream) {
+                  int hist_len, double tol, int window, double omega, int reunit_every, int abs_cap,
+                  int check_every, bool fresh, cudaStream_t stream) {
     constexpr int NT = sweep_threads<T>();
     const int nf = (int)fields_in.size();
     std::vector<FieldDesc> fields = fields_in;
@@ -648,11 +884,12 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
     bt.R_hist = d_hist;
     bt.hist_len = hist_len;
     bt.tol = tol;
+    bt.window = std::max(1, std::min(window, kRing - 1));
     bt.reunit_every = reunit_every;
+    bt.omega = omega;
 
-    size_t smem = 0;
-    if (sizeof(T) == 8) {
-        smem = sizeof(cplx<T>) * 72 * NT;
+    const size_t smem = sizeof(cplx<T>) * 72 * NT;
+    {
         static bool attr_set = false;
         if (!attr_set) {
             MCG_CK(cudaFuncSetAttribute(k_halfsweep<T, false, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -666,6 +903,7 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
     k_functional<T, NT><<<total, NT, 0, stream>>>(bt);
     k_finalize<<<nf, 256, 0, stream>>>(bt, fresh ? 1 : 2);
     MCG_CK(cudaGetLastError());
+    note_launches(2);
     if (phase_len <= 0) {
         MCG_CK(cudaMemcpyAsync(h_state, d_state, sizeof(FieldState) * nf, cudaMemcpyDeviceToHost, stream));
         MCG_CK(cudaStreamSynchronize(stream));
@@ -687,6 +925,7 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
         cudaGraphDestroy(graph);
         return cuda_fail(ce, "cudaGraphInstantiate");
     }
+    const int nodes_per_chunk = chunk * (reunit_every > 0 ? 4 : 3);
     const int max_chunks = (phase_len + chunk - 1) / chunk + 1;
     int status = 0;
     for (int c = 0; c < max_chunks; ++c) {
@@ -695,6 +934,7 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
             status = cuda_fail(ce, "cudaGraphLaunch");
             break;
         }
+        note_launches(nodes_per_chunk);
         ce = cudaMemcpyAsync(h_state, d_state, sizeof(FieldState) * nf, cudaMemcpyDeviceToHost, stream);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
         if (ce != cudaSuccess) {
@@ -710,9 +950,87 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
     return status;
 }
 
+template <typename T>
+int time_halfsweep(void* U, void* G, const Geom& g, int parity, int nreps, int flush_l2, float* ms,
+                   cudaStream_t stream) {
+    constexpr int NT = sweep_threads<T>();
+    int rc = 0;
+    FieldDesc fd;
+    fd.U = U;
+    fd.G = G;
+    fd.geo = g;
+    fd.blk0 = 0;
+    fd.nblk = (g.vh + NT - 1) / NT;
+    fd.norm = 1.0 / (9.0 * 8.0 * g.vh);
+    FieldDesc* d_desc = (FieldDesc*)scratch_device("time.desc", sizeof(FieldDesc), &rc);
+    if (rc) return rc;
+    FieldState* d_state = (FieldState*)scratch_device("time.state", sizeof(FieldState), &rc);
+    if (rc) return rc;
+    double* d_partial = (double*)scratch_device("time.partial", sizeof(double) * fd.nblk, &rc);
+    if (rc) return rc;
+    void* flush = nullptr;
+    const size_t flush_bytes = (size_t)256 << 20;
+    if (flush_l2) {
+        flush = scratch_device("time.flush", flush_bytes, &rc);
+        if (rc) return rc;
+    }
+    MCG_CK(cudaMemcpyAsync(d_desc, &fd, sizeof fd, cudaMemcpyHostToDevice, stream));
+    MCG_CK(cudaMemsetAsync(d_state, 0, sizeof(FieldState), stream));
+    SweepBatch bt;
+    bt.desc = d_desc;
+    bt.nf = 1;
+    bt.total_blocks = fd.nblk;
+    bt.state = d_state;
+    bt.partial = d_partial;
+    bt.R_hist = nullptr;
+    bt.hist_len = 0;
+    bt.tol = 0;
+    bt.window = 1;
+    bt.reunit_every = 0;
+    bt.omega = 1.0;
+    const size_t smem = sizeof(cplx<T>) * 72 * NT;
+    {
+        MCG_CK(cudaFuncSetAttribute(k_halfsweep<T, false, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MCG_CK(cudaFuncSetAttribute(k_halfsweep<T, true, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    cudaEvent_t e0, e1;
+    MCG_CK(cudaEventCreate(&e0));
+    MCG_CK(cudaEventCreate(&e1));
+    double total = 0.0;
+    for (int r = 0; r < nreps; ++r) {
+        if (flush) {
+            cudaMemsetAsync(flush, r & 0xff, flush_bytes, stream);
+        }
+        cudaEventRecord(e0, stream);
+        if (parity)
+            k_halfsweep<T, true, NT><<<fd.nblk, NT, smem, stream>>>(bt, 1);
+        else
+            k_halfsweep<T, false, NT><<<fd.nblk, NT, smem, stream>>>(bt, 0);
+        cudaEventRecord(e1, stream);
+        cudaError_t ce = cudaEventSynchronize(e1);
+        if (ce != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(ce, "time_halfsweep");
+        }
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        total += t;
+    }
+    note_launches(nreps);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    MCG_CK(cudaGetLastError());
+    *ms = (float)(total / std::max(1, nreps));
+    return 0;
+}
+
+template int time_halfsweep<float>(void*, void*, const Geom&, int, int, int, float*, cudaStream_t);
+template int time_halfsweep<double>(void*, void*, const Geom&, int, int, int, float*, cudaStream_t);
+
 template int run_fix_phase<float>(const std::vector<FieldDesc>&, FieldState*, FieldState*, double*, int, double,
-                                  int, int, int, bool, cudaStream_t);
+                                  int, double, int, int, int, bool, cudaStream_t);
 template int run_fix_phase<double>(const std::vector<FieldDesc>&, FieldState*, FieldState*, double*, int, double,
-                                   int, int, int, bool, cudaStream_t);
+                                   int, double, int, int, int, bool, cudaStream_t);
 
 }  // namespace mcg

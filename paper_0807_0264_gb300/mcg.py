@@ -42,7 +42,7 @@ class mcg_lattice(ctypes.Structure):
 class mcg_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_sweeps", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("reunit_every", ctypes.c_int), ("fp32_sweeps", ctypes.c_int), ("fp32_tol", ctypes.c_double),
-                ("fp32_reunit_every", ctypes.c_int)]
+                ("fp32_window", ctypes.c_int), ("fp32_overrelax", ctypes.c_double)]
 
 
 class mcg_precond_result(ctypes.Structure):
@@ -82,6 +82,10 @@ def _load() -> ctypes.CDLL:
         "mcg_fix": ([P, P, L, PR, P, P, P, P], I),
         "mcg_center_project": ([P, P, P, L, P], I),
         "mcg_precondition_fix": ([P, P, P, L, PR, D, D, I, I, ctypes.POINTER(mcg_precond_result), P], I),
+        "mcg_precondition_levels": ([P, P, P, P, L, PR, D, D, ctypes.POINTER(ctypes.c_int), I, I,
+                                     ctypes.POINTER(mcg_precond_result), P], I),
+        "mcg_time_halfsweep": ([P, P, L, I, I, I, ctypes.POINTER(ctypes.c_float), P], I),
+        "mcg_kernel_launches": ([], ctypes.c_longlong),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -96,7 +100,7 @@ _lib = _load()
 EXPORTS = ("mcg_version", "mcg_last_error", "mcg_release", "mcg_pack_links", "mcg_unpack_links", "mcg_pack_gauge",
            "mcg_unpack_gauge", "mcg_unpack_center", "mcg_convert", "mcg_set_identity_gauge", "mcg_plaquette",
            "mcg_functional", "mcg_apply_gauge", "mcg_reunitarise", "mcg_smear", "mcg_fix", "mcg_center_project",
-           "mcg_precondition_fix")
+           "mcg_precondition_fix", "mcg_precondition_levels", "mcg_time_halfsweep", "mcg_kernel_launches")
 
 
 def library() -> ctypes.CDLL:
@@ -118,12 +122,13 @@ class Params:
     check_every: int = 20
     reunit_every: int = 50
     fp32_sweeps: int = 0
-    fp32_tol: float = 1e-9
-    fp32_reunit_every: int = 10
+    fp32_tol: float = 1e-10
+    fp32_window: int = 25
+    fp32_overrelax: float = 1.0
 
     def c(self) -> mcg_params:
         return mcg_params(self.tol, self.max_sweeps, self.check_every, self.reunit_every, self.fp32_sweeps,
-                          self.fp32_tol, self.fp32_reunit_every)
+                          self.fp32_tol, self.fp32_window, self.fp32_overrelax)
 
 
 def lattice(dims, nfields: int = 1, precision: int = F64) -> mcg_lattice:
@@ -346,3 +351,46 @@ def mcg_precondition_fix(U: torch.Tensor, G: torch.Tensor, dims, params: Params 
                                      float(eps), int(nsmear), prec if smear_precision is None else int(smear_precision),
                                      res, _stream(stream)), allow=(OK, NOT_CONVERGED))
     return [r.as_dict() for r in res]
+
+
+def mcg_precondition_levels(U: torch.Tensor, dims, nsmear, params: Params | None = None, rho: float = 0.1,
+                            eps: float = 1.0, smear_precision: int | None = None, U_out: torch.Tensor | None = None,
+                            G_out: torch.Tensor | None = None, Z_out: torch.Tensor | None = None,
+                            stream=None):
+    """Batched Sec. II.B scan over smearing levels of one field.
+    Returns (U_out, G_out, Z_out, results)."""
+    _need_cuda(U)
+    params = params or Params()
+    prec = precision_of(U)
+    nl = len(nsmear)
+    if U_out is None:
+        U_out = empty_links(dims, nl, prec, U.device)
+    if G_out is None:
+        G_out = empty_gauge(dims, nl, prec, U.device)
+    if Z_out is None:
+        Z_out = torch.empty((nl, 4, 2, vh_of(dims)), dtype=torch.int8, device=U.device)
+    _need_cuda(U_out, G_out, Z_out)
+    ns = (ctypes.c_int * nl)(*[int(n) for n in nsmear])
+    res = (mcg_precond_result * nl)()
+    cp = params.c()
+    _check("mcg_precondition_levels",
+           _lib.mcg_precondition_levels(_ptr(U), _ptr(U_out), _ptr(G_out), _ptr(Z_out), lattice(dims, 1, prec),
+                                        ctypes.byref(cp), float(rho), float(eps), ns, nl,
+                                        prec if smear_precision is None else int(smear_precision), res,
+                                        _stream(stream)), allow=(OK, NOT_CONVERGED))
+    return U_out, G_out, Z_out, [r.as_dict() for r in res]
+
+
+def mcg_time_halfsweep(U: torch.Tensor, G: torch.Tensor, dims, parity: int = 1, nreps: int = 10,
+                       flush_l2: bool = True, stream=None) -> float:
+    """Mean per-launch milliseconds of the half-sweep kernel (CUDA events)."""
+    _need_cuda(U, G)
+    ms = ctypes.c_float(0)
+    _check("mcg_time_halfsweep", _lib.mcg_time_halfsweep(_ptr(U), _ptr(G), lattice(dims, 1, precision_of(U)),
+                                                         int(parity), int(nreps), int(bool(flush_l2)),
+                                                         ctypes.byref(ms), _stream(stream)))
+    return ms.value
+
+
+def mcg_kernel_launches() -> int:
+    return int(_lib.mcg_kernel_launches())
