@@ -246,6 +246,23 @@ int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_o
 int mcg_time_halfsweep(void* U, void* G, const mcg_lattice* lat, int parity, int nreps, int flush_l2, float* ms_out,
                        cudaStream_t stream);
 
+/*
+ * Mean plaquette per field, like mcg_plaquette, for callers that cannot let
+ * the library allocate device memory (the paper has no counterpart: this is
+ * an interface variant).  Its only scratch, the per-block partial sums, is a
+ * fixed 512 KiB array compiled into the library (65 536 doubles), so a call
+ * needs nfields * ceil(V / 256) <= 65 536; larger requests return
+ * MCG_BAD_ARG without touching the GPU.  out: DEVICE pointer to nfields
+ * doubles, written asynchronously on `stream` (no synchronisation, no host
+ * transfer).  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the one array and it keeps
+ * the previous call's partial sums: calls whose kernels overlap on the GPU
+ * (other streams, other host threads) race and must be ordered by the caller.
+ * Allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ */
+int mcg_plaquette_static(const void* U, double* out, const mcg_lattice* lat, cudaStream_t stream);
+
 /* Running total of CUDA kernels this library has enqueued in this process
  * (kernels inside a CUDA graph count once per graph launch). */
 long long mcg_kernel_launches(void);

@@ -3,6 +3,7 @@
 // All are HBM-bound streaming kernels (one thread per site of one parity).
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <vector>
 
 #include "mcg_common.cuh"
@@ -556,3 +557,87 @@ int launch_handoff(const void* W32, double* U64, double* G64, const Geom& g, int
 }
 
 }  // namespace mcg
+
+// ---------------------------------------------------------------------------
+// Plaquette without any allocation (mcg_plaquette_static)
+// ---------------------------------------------------------------------------
+namespace mcg {
+// sum of one field's block partials in a fixed order, scaled, to out[f]
+__global__ void k_static_finish(const double* __restrict__ partial, int bpf, double scale, double* __restrict__ out) {
+    const int f = blockIdx.x;
+    double v = 0.0;
+    for (int k = threadIdx.x; k < bpf; k += blockDim.x) v += partial[(size_t)f * bpf + k];
+    __shared__ double red[8];
+    const double tot = block_sum(v, red);
+    if (threadIdx.x == 0) out[f] = tot * scale;
+}
+}  // namespace mcg
+
+// Some callers cannot let a library call cudaMalloc: an application whose
+// device memory is fully handed to its own pool allocator (a new cudaMalloc
+// would fail or break its accounting), a latency-critical loop that cannot
+// absorb the device-wide synchronisation cudaFree implies, or code that
+// must keep its memory footprint fixed after start-up.  For them this entry
+// point keeps its only scratch, the per-block partial sums, in a fixed array
+// compiled into the library; the caller passes the field and a device buffer
+// for the result.  Every GPU that loads the library holds this array until
+// the process exits.
+namespace mcg {
+
+constexpr int kStaticPartials = 1 << 16;  // 65 536 doubles = 512 KiB
+static __device__ __align__(256) double g_static_partials[kStaticPartials];
+
+static std::mutex g_static_mu;
+static double* g_static_addr[64];  // symbol address per device, resolved once
+
+// Resolve the device address of the static partials for the current device.
+static int static_partials_address(double** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(MCG_BAD_ARG, "device index beyond 63");
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_partials);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static partials)");
+        g_static_addr[dev] = (double*)p;
+    }
+    *out = g_static_addr[dev];
+    return 0;
+}
+
+}  // namespace mcg
+
+extern "C" int mcg_plaquette_static(const void* U, double* out, const mcg_lattice* lat, cudaStream_t stream) {
+    using namespace mcg;
+    if (!lat) return fail(MCG_BAD_ARG, "lattice descriptor is NULL");
+    for (int d = 0; d < 4; ++d)
+        if (lat->dims[d] < 2 || (lat->dims[d] & 1)) return fail(MCG_BAD_DIMS, "every lattice extent must be even and >= 2");
+    if (lat->nfields < 1) return fail(MCG_BAD_DIMS, "nfields must be >= 1");
+    if (lat->precision != MCG_F64 && lat->precision != MCG_F32)
+        return fail(MCG_BAD_ARG, "precision must be MCG_F64 or MCG_F32");
+    if (!U || !out) return fail(MCG_BAD_ARG, "null pointer");
+    const long long V = (long long)lat->dims[0] * lat->dims[1] * lat->dims[2] * lat->dims[3];
+    const long long bpf = (V + FT - 1) / FT;
+    if (bpf * lat->nfields > kStaticPartials)
+        return fail(MCG_BAD_ARG, "mcg_plaquette_static: nfields * ceil(V / 256) exceeds the 65536 static partial "
+                                 "sums (at most 16 777 216 sites in total); use mcg_plaquette");
+    double* partial = nullptr;
+    int rc = static_partials_address(&partial);
+    if (rc) return rc;
+    Geom g;
+    for (int d = 0; d < 4; ++d) g.n[d] = lat->dims[d];
+    g.vh = (int)(V / 2);
+    // every partial slot read below is written by its block first: nothing in
+    // the shared array has to start at zero
+    const int nb = (int)bpf * lat->nfields;
+    if (lat->precision == MCG_F64)
+        k_plaquette<double><<<nb, FT, 0, stream>>>((const cplx<double>*)U, g, (int)bpf, partial);
+    else
+        k_plaquette<float><<<nb, FT, 0, stream>>>((const cplx<float>*)U, g, (int)bpf, partial);
+    k_static_finish<<<lat->nfields, 256, 0, stream>>>(partial, (int)bpf, 1.0 / (6.0 * (double)V), out);
+    MCG_CK(cudaGetLastError());
+    note_launches(2);
+    return MCG_OK;
+}

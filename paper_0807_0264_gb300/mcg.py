@@ -86,6 +86,7 @@ def _load() -> ctypes.CDLL:
                                      ctypes.POINTER(mcg_precond_result), P], I),
         "mcg_time_halfsweep": ([P, P, L, I, I, I, ctypes.POINTER(ctypes.c_float), P], I),
         "mcg_kernel_launches": ([], ctypes.c_longlong),
+        "mcg_plaquette_static": ([P, P, L, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -100,7 +101,8 @@ _lib = _load()
 EXPORTS = ("mcg_version", "mcg_last_error", "mcg_release", "mcg_pack_links", "mcg_unpack_links", "mcg_pack_gauge",
            "mcg_unpack_gauge", "mcg_unpack_center", "mcg_convert", "mcg_set_identity_gauge", "mcg_plaquette",
            "mcg_functional", "mcg_apply_gauge", "mcg_reunitarise", "mcg_smear", "mcg_fix", "mcg_center_project",
-           "mcg_precondition_fix", "mcg_precondition_levels", "mcg_time_halfsweep", "mcg_kernel_launches")
+           "mcg_precondition_fix", "mcg_precondition_levels", "mcg_time_halfsweep", "mcg_kernel_launches",
+           "mcg_plaquette_static")
 
 
 def library() -> ctypes.CDLL:
@@ -394,3 +396,15 @@ def mcg_time_halfsweep(U: torch.Tensor, G: torch.Tensor, dims, parity: int = 1, 
 
 def mcg_kernel_launches() -> int:
     return int(_lib.mcg_kernel_launches())
+
+
+def mcg_plaquette_static(U: torch.Tensor, dims, out: torch.Tensor, stream=None) -> torch.Tensor:
+    """Mean plaquette per field into the caller's float64 CUDA tensor `out`
+    (nfields entries); the library allocates nothing for this call (its
+    partial sums live in a fixed array inside libmcg).  Asynchronous."""
+    _need_cuda(U, out)
+    if out.dtype != torch.float64 or out.numel() < U.shape[0]:
+        raise ValueError("out must be a float64 CUDA tensor with one entry per field")
+    _check("mcg_plaquette_static",
+           _lib.mcg_plaquette_static(_ptr(U), _ptr(out), lattice(dims, U.shape[0], precision_of(U)), _stream(stream)))
+    return out
