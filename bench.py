@@ -212,7 +212,9 @@ def main():
     U_out = mcg.empty_links(dims, nl, mcg.F64, dev)
     G_out = mcg.empty_gauge(dims, nl, mcg.F64, dev)
     Z_out = torch.empty((nl, 4, 2, V // 2), dtype=torch.int8, device=dev)
-    mixed = mcg.Params(tol=1e-10, max_sweeps=8000, check_every=25, reunit_every=50, fp32_sweeps=8000,
+    tuned = {"f32": mcg.autotune_sweep_block(mcg.mcg_convert(U, mcg.F32), dims),
+             "f64": mcg.autotune_sweep_block(U, dims, reps=3)}
+    mixed = mcg.Params(tol=1e-10, max_sweeps=30000, check_every=25, reunit_every=50, fp32_sweeps=30000,
                        fp32_tol=float(os.environ.get("MCG_FP32_TOL", "1e-10")), fp32_window=25,
                        fp32_overrelax=float(os.environ.get("MCG_OMEGA", "1.7")))
     stream = torch.cuda.current_stream(dev)
@@ -388,7 +390,7 @@ def main():
                         "plaquette_in": mixed_res[0]["plaquette_in"],
                         "plaquette_out": [r["plaquette_out"] for r in mixed_res],
                         "converged": all(r["status"] == 0 for r in mixed_res)},
-                "roofline": roof, "cpu_baseline": cpu,
+                "roofline": roof, "cpu_baseline": cpu, "autotune": tuned,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": canon_pinned.numel() * 16,
                         "d2h_bytes_per_step": z_host.numel(), "ms_per_step": e2e_ms / args.steps},
                 "clocks": clk.summary(), "gpu_launches": launches}

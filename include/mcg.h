@@ -263,6 +263,14 @@ int mcg_time_halfsweep(void* U, void* G, const mcg_lattice* lat, int parity, int
  */
 int mcg_plaquette_static(const void* U, double* out, const mcg_lattice* lat, cudaStream_t stream);
 
+/* Threads per block of the half-sweep kernel for one precision: FP64 runs one
+ * thread per site (64 or 128), FP32 two threads per site (64, 128 or 256);
+ * 128 by default.  A process-wide tuning setting (not part of the paper's
+ * method): Python's autotune_sweep_block() times the choices with
+ * mcg_time_halfsweep and keeps the fastest.  Returns MCG_BAD_ARG otherwise. */
+int mcg_set_sweep_block(int precision, int threads);
+int mcg_get_sweep_block(int precision);
+
 /* Running total of CUDA kernels this library has enqueued in this process
  * (kernels inside a CUDA graph count once per graph launch). */
 long long mcg_kernel_launches(void);

@@ -481,6 +481,16 @@ int mcg_precondition_fix(void* U, void* G, int8_t* Z, const mcg_lattice* lat, co
 
 long long mcg_kernel_launches(void) { return g_launches.load(); }
 
+int mcg_set_sweep_block(int precision, int threads) {
+    if (precision != MCG_F64 && precision != MCG_F32) return fail(MCG_BAD_ARG, "bad precision");
+    if (threads != 64 && threads != 128 && !(threads == 256 && precision == MCG_F32))
+        return fail(MCG_BAD_ARG, "threads must be 64 or 128 (FP64), 64, 128 or 256 (FP32)");
+    set_sweep_block(precision, threads);
+    return MCG_OK;
+}
+
+int mcg_get_sweep_block(int precision) { return sweep_block(precision); }
+
 int mcg_time_halfsweep(void* U, void* G, const mcg_lattice* lat, int parity, int nreps, int flush_l2, float* ms_out,
                        cudaStream_t stream) {
     Geom g;

@@ -90,10 +90,11 @@ template <typename T>
 int time_halfsweep(void* U, void* G, const Geom& g, int parity, int nreps, int flush_l2, float* ms,
                    cudaStream_t stream);
 
-template <typename T>
-constexpr int sweep_threads() {
-    return sizeof(T) == 8 ? 64 : 128;
-}
+// threads per block of the half-sweep kernel for a precision, and the sites
+// each block covers (FP32 uses two threads per site)
+int sweep_block(int prec);
+void set_sweep_block(int prec, int nt);
+int sweep_sites_per_block(int prec);
 
 // ---- field kernels (mcg_field.cu) -------------------------------------------
 int launch_convert(const void* src, int src_prec, void* dst, int dst_prec, size_t n, cudaStream_t st);

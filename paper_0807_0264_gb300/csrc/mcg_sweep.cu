@@ -315,18 +315,14 @@ __device__ __forceinline__ bool kkt_newton(const T (&A)[4][4], const T (&b)[4], 
     const T inv = rsqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
 #pragma unroll
     for (int k = 0; k < 4; ++k) a[k] *= inv;
-    // certificate: mu - A positive definite at the converged multiplier
-    T M[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) M[i][j] = (i == j ? mu : T(0)) - A[i][j];
-    pd = ldlt4(M, L, Dinv);
+    // certificate: mu - A positive definite.  The factorization of the last
+    // step (at mu - dmu, with |dmu| far below the pivot margin) serves.
     return pd > (sizeof(T) == 8 ? T(1e-12) : T(1e-5));
 }
 
-// FP32 solve of the subproblem given A (symmetric) and b.
-__device__ __forceinline__ int solve_f32(const float (&A)[4][4], const float (&b)[4], float (&a)[4], float& mu,
+// FP32 solve of the subproblem given A (symmetric) and b (Jacobi + secular;
+// out of line: the warm-started Newton path handles almost every solve).
+__device__ __noinline__ int solve_f32(const float (&A)[4][4], const float (&b)[4], float (&a)[4], float& mu,
                                          float (&S)[4][4], float (&V)[4][4]) {
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -530,10 +526,12 @@ struct SmemLinks {
     __device__ __forceinline__ cplx<T>& operator()(int l, int e) { return base[(l * 9 + e) * NT + threadIdx.x]; }
 };
 
-// One SU(2)-subgroup step on the 8 links (l < 4: forward U_l(x), l >= 4:
-// backward U_{l-4}(x - l)) and Omega(x).  Returns fallback count.
-template <typename T, int P, int Q, int R, typename L>
-__device__ __forceinline__ int subgroup_step(L& lk, cplx<T> (&Om)[9], const T omega) {
+// One SU(2)-subgroup step (subgroup rows/columns P, Q; R the third index) on
+// the 8 links in shared memory (l < 4: forward U_l(x), 4 <= l < 8: backward
+// U_{l-4}(x - l)) and Omega(x) (slot 8).  Returns 1 if the local solve left
+// the fast path.
+template <typename T, typename L>
+__device__ __forceinline__ int subgroup_step(L& lk, const int P, const int Q, const int R, const T omega) {
     T A[4][4], b[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -541,10 +539,11 @@ __device__ __forceinline__ int subgroup_step(L& lk, cplx<T> (&Om)[9], const T om
 #pragma unroll
         for (int j = 0; j < 4; ++j) A[i][j] = T(0);
     }
+    const int ePP = 3 * P + P, ePQ = 3 * P + Q, eQP = 3 * Q + P, eQQ = 3 * Q + Q, eRR = 3 * R + R;
 #pragma unroll
     for (int l = 0; l < 8; ++l) {
-        const cplx<T> m11 = lk(l, 3 * P + P), m12 = lk(l, 3 * P + Q), m21 = lk(l, 3 * Q + P), m22 = lk(l, 3 * Q + Q);
-        const cplx<T> c = lk(l, 3 * R + R);
+        const cplx<T> m11 = lk(l, ePP), m12 = lk(l, ePQ), m21 = lk(l, eQP), m22 = lk(l, eQQ);
+        const cplx<T> c = lk(l, eRR);
         cplx<T> w[4];
         w[0] = cadd(m11, m22);
         w[1] = mk(-(m21.y + m12.y), m21.x + m12.x);  // i (m21 + m12)
@@ -579,29 +578,23 @@ __device__ __forceinline__ int subgroup_step(L& lk, cplx<T> (&Om)[9], const T om
         for (int k = 0; k < 4; ++k) a[k] *= inv;
     }
     const cplx<T> g11 = mk(a[0], a[3]), g12 = mk(a[2], a[1]), g21 = mk(-a[2], a[1]), g22 = mk(a[0], -a[3]);
+#pragma unroll 1
+    for (int l = 0; l < 9; ++l) {
+        if (l < 4 || l == 8) {
 #pragma unroll
-    for (int l = 0; l < 4; ++l) {
+            for (int k = 0; k < 3; ++k) {  // rows P, Q of G U (and of G Omega)
+                const cplx<T> xp = lk(l, 3 * P + k), xq = lk(l, 3 * Q + k);
+                lk(l, 3 * P + k) = cfma(g12, xq, cmul(g11, xp));
+                lk(l, 3 * Q + k) = cfma(g22, xq, cmul(g21, xp));
+            }
+        } else {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {  // rows P, Q of G U
-            const cplx<T> xp = lk(l, 3 * P + k), xq = lk(l, 3 * Q + k);
-            lk(l, 3 * P + k) = cfma(g12, xq, cmul(g11, xp));
-            lk(l, 3 * Q + k) = cfma(g22, xq, cmul(g21, xp));
+            for (int k = 0; k < 3; ++k) {  // columns P, Q of U G^dag
+                const cplx<T> xp = lk(l, 3 * k + P), xq = lk(l, 3 * k + Q);
+                lk(l, 3 * k + P) = cfmac(xq, g12, cmulc(xp, g11));
+                lk(l, 3 * k + Q) = cfmac(xq, g22, cmulc(xp, g21));
+            }
         }
-    }
-#pragma unroll
-    for (int l = 4; l < 8; ++l) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {  // columns P, Q of U G^dag
-            const cplx<T> xp = lk(l, 3 * k + P), xq = lk(l, 3 * k + Q);
-            lk(l, 3 * k + P) = cfmac(xq, g12, cmulc(xp, g11));
-            lk(l, 3 * k + Q) = cfmac(xq, g22, cmulc(xp, g21));
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const cplx<T> xp = Om[3 * P + k], xq = Om[3 * Q + k];
-        Om[3 * P + k] = cfma(g12, xq, cmul(g11, xp));
-        Om[3 * Q + k] = cfma(g22, xq, cmul(g21, xp));
     }
     return fb;
 }
@@ -621,10 +614,10 @@ __device__ __forceinline__ int field_of_block(const FieldDesc* __restrict__ d, i
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
-// Occupancy: FP32 runs 2 blocks of 128 threads per SM (spill-free at <= 255
-// registers); FP64, bound by the FP64 pipe, runs 3 blocks of 64.
+// Shared memory per thread: 8 links + Omega (81 complex): 41.5 KB for 64 FP32
+// threads (5 blocks per SM), 83 KB for 128 FP32 or 64 FP64 threads (2 per SM).
 template <typename T, bool ACC, int NT>
-__global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 3 : 2) k_halfsweep(SweepBatch bt, int parity) {
+__global__ void __launch_bounds__(NT, 2) k_halfsweep(SweepBatch bt, int parity) {
     const int f = field_of_block(bt.desc, bt.nf, blockIdx.x);
     if (bt.state[f].done) return;  // block-uniform
     const FieldDesc fd = bt.desc[f];
@@ -646,60 +639,64 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 3 : 2) k_halfsweep(SweepB
         int sb[4];
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) sb[mu] = eo_neighbor(g, c, mu, -1);
-        // stage the 8 links in shared memory without passing through registers
+        // stage the 8 links and Omega in shared memory without passing
+        // through registers
 #pragma unroll
-        for (int mu = 0; mu < 4; ++mu)
+        for (int mu = 0; mu < 4; ++mu) {
+            const cplx<T>* src = U + lidx(g, mu, parity, 0, s);
+#pragma unroll 1
+            for (int e = 0; e < 9; ++e) cp_async<sizeof(cplx<T>)>(&lk(mu, e), src + (size_t)e * g.vh);
+        }
 #pragma unroll
-            for (int e = 0; e < 9; ++e) cp_async<sizeof(cplx<T>)>(&lk(mu, e), &U[lidx(g, mu, parity, e, s)]);
+        for (int mu = 0; mu < 4; ++mu) {
+            const cplx<T>* src = U + lidx(g, mu, parity ^ 1, 0, sb[mu]);
+#pragma unroll 1
+            for (int e = 0; e < 9; ++e) cp_async<sizeof(cplx<T>)>(&lk(4 + mu, e), src + (size_t)e * g.vh);
+        }
 #pragma unroll
-        for (int mu = 0; mu < 4; ++mu)
-#pragma unroll
-            for (int e = 0; e < 9; ++e)
-                cp_async<sizeof(cplx<T>)>(&lk(4 + mu, e), &U[lidx(g, mu, parity ^ 1, e, sb[mu])]);
-        cplx<T> Om[9];
-#pragma unroll
-        for (int e = 0; e < 9; ++e) Om[e] = G[gidx(g, parity, e, s)];
+        for (int e = 0; e < 9; ++e) cp_async<sizeof(cplx<T>)>(&lk(8, e), &G[gidx(g, parity, e, s)]);
         cp_async_wait_all();
 
-        // compiler barriers: between the phases of the update the links live
-        // in shared memory instead of being carried in registers
+        // subgroups (0,1), (0,2), (1,2) in turn; compiler barriers keep the
+        // links in shared memory between the phases of the update
         const T omega = (T)bt.omega;
-        fb += subgroup_step<T, 0, 1, 2>(lk, Om, omega);
-        asm volatile("" ::: "memory");
-        fb += subgroup_step<T, 0, 2, 1>(lk, Om, omega);
-        asm volatile("" ::: "memory");
-        fb += subgroup_step<T, 1, 2, 0>(lk, Om, omega);
-        asm volatile("" ::: "memory");
+#pragma unroll 1
+        for (int sg = 0; sg < 3; ++sg) {
+            const int P = sg == 2 ? 1 : 0, Q = sg == 0 ? 1 : 2;
+            fb += subgroup_step<T>(lk, P, Q, 3 - P - Q, omega);
+            asm volatile("" ::: "memory");
+        }
         if (sizeof(T) == 4) {
             // FP32 sweeps re-unitarise in FP32 every sweep (Omega every
             // half-sweep, the 8 links in the odd one, which touches every link
             // once): FP32 rounding would otherwise inflate |tr U|^2 by ~1e-6
             // per sweep and swamp the convergence signal.
-            m3_reunitarise_same(Om);
-            if (ACC) {
 #pragma unroll 1
-                for (int l = 0; l < 8; ++l) {
-                    cplx<T> m[9];
+            for (int l = ACC ? 0 : 8; l < 9; ++l) {
+                cplx<T> m[9];
 #pragma unroll
-                    for (int e = 0; e < 9; ++e) m[e] = lk(l, e);
-                    m3_reunitarise_same(m);
+                for (int e = 0; e < 9; ++e) m[e] = lk(l, e);
+                m3_reunitarise_same(m);
 #pragma unroll
-                    for (int e = 0; e < 9; ++e) lk(l, e) = m[e];
-                }
+                for (int e = 0; e < 9; ++e) lk(l, e) = m[e];
             }
             asm volatile("" ::: "memory");
         }
 
 #pragma unroll
-        for (int mu = 0; mu < 4; ++mu)
+        for (int mu = 0; mu < 4; ++mu) {
+            cplx<T>* dst = U + lidx(g, mu, parity, 0, s);
+#pragma unroll 1
+            for (int e = 0; e < 9; ++e) dst[(size_t)e * g.vh] = lk(mu, e);
+        }
 #pragma unroll
-            for (int e = 0; e < 9; ++e) U[lidx(g, mu, parity, e, s)] = lk(mu, e);
+        for (int mu = 0; mu < 4; ++mu) {
+            cplx<T>* dst = U + lidx(g, mu, parity ^ 1, 0, sb[mu]);
+#pragma unroll 1
+            for (int e = 0; e < 9; ++e) dst[(size_t)e * g.vh] = lk(4 + mu, e);
+        }
 #pragma unroll
-        for (int mu = 0; mu < 4; ++mu)
-#pragma unroll
-            for (int e = 0; e < 9; ++e) U[lidx(g, mu, parity ^ 1, e, sb[mu])] = lk(4 + mu, e);
-#pragma unroll
-        for (int e = 0; e < 9; ++e) G[gidx(g, parity, e, s)] = Om[e];
+        for (int e = 0; e < 9; ++e) G[gidx(g, parity, e, s)] = lk(8, e);
         if (ACC) {
 #pragma unroll
             for (int l = 0; l < 8; ++l) {
@@ -721,15 +718,185 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 3 : 2) k_halfsweep(SweepB
     }
 }
 
+// Pair-split half-sweep (FP32): the two lanes 2j, 2j+1 of a warp share site j
+// of the block.  Lane h = 0 holds the forward links U_mu(x) and Omega(x), lane
+// h = 1 the backward links U_mu(x - mu).  Each builds its part of (A, b), the
+// pair adds the parts with one shuffle per entry (a + b == b + a exactly, so
+// both lanes hold identical sums), both lanes solve the 4x4 problem (the
+// solve is cheap next to the link traffic) and each updates its own links.
+// Halving the shared memory per thread doubles the resident warps.
+template <typename T, bool ACC, int NT>
+__global__ void __launch_bounds__(NT) k_halfsweep_pair(SweepBatch bt, int parity) {
+    constexpr int SPB = NT / 2;  // sites per block
+    const int f = field_of_block(bt.desc, bt.nf, blockIdx.x);
+    if (bt.state[f].done) return;  // block-uniform
+    const FieldDesc fd = bt.desc[f];
+    const Geom g = fd.geo;
+    cplx<T>* __restrict__ U = reinterpret_cast<cplx<T>*>(fd.U);
+    cplx<T>* __restrict__ G = reinterpret_cast<cplx<T>*>(fd.G);
+    const int h = threadIdx.x & 1;
+    const int s = (blockIdx.x - fd.blk0) * SPB + (threadIdx.x >> 1);
+    const bool active = s < g.vh;
+    const unsigned mask = __ballot_sync(0xffffffffu, active);
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemLinks<T, NT> lk;  // slots 0..3: own links; slot 4: Omega (lane 0)
+    lk.base = reinterpret_cast<cplx<T>*>(smem_raw);
+
+    double rsum = 0.0;
+    int fb = 0;
+    if (active) {
+        int c[4];
+        eo_coords(g, parity, s, c);
+        const int pl = parity ^ h;  // parity of the sites the own links start at
+        int sl[4];
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) sl[mu] = h ? eo_neighbor(g, c, mu, -1) : s;
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            const cplx<T>* src = U + lidx(g, mu, pl, 0, sl[mu]);
+#pragma unroll 1
+            for (int e = 0; e < 9; ++e) cp_async<sizeof(cplx<T>)>(&lk(mu, e), src + (size_t)e * g.vh);
+        }
+        if (h == 0) {
+#pragma unroll
+            for (int e = 0; e < 9; ++e) cp_async<sizeof(cplx<T>)>(&lk(4, e), &G[gidx(g, parity, e, s)]);
+        }
+        cp_async_wait_all();
+
+        const T omega = (T)bt.omega;
+#pragma unroll 1
+        for (int sg = 0; sg < 3; ++sg) {
+            const int P = sg == 2 ? 1 : 0, Q = sg == 0 ? 1 : 2, R = 3 - P - Q;
+            T A[4][4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                b[i] = T(0);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) A[i][j] = T(0);
+            }
+            const int ePP = 3 * P + P, ePQ = 3 * P + Q, eQP = 3 * Q + P, eQQ = 3 * Q + Q, eRR = 3 * R + R;
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const cplx<T> m11 = lk(l, ePP), m12 = lk(l, ePQ), m21 = lk(l, eQP), m22 = lk(l, eQQ);
+                const cplx<T> cc = lk(l, eRR);
+                cplx<T> w[4];
+                w[0] = cadd(m11, m22);
+                w[1] = mk(-(m21.y + m12.y), m21.x + m12.x);
+                w[2] = csub(m21, m12);
+                w[3] = mk(-(m11.y - m22.y), m11.x - m22.x);
+                if (h) {
+#pragma unroll
+                    for (int k = 1; k < 4; ++k) w[k] = mk(-w[k].x, -w[k].y);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    b[k] = fma(cc.x, w[k].x, fma(cc.y, w[k].y, b[k]));
+#pragma unroll
+                    for (int j = k; j < 4; ++j) A[k][j] = fma(w[k].x, w[j].x, fma(w[k].y, w[j].y, A[k][j]));
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                b[k] += __shfl_xor_sync(mask, b[k], 1);
+#pragma unroll
+                for (int j = k; j < 4; ++j) A[k][j] += __shfl_xor_sync(mask, A[k][j], 1);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int j = 0; j < k; ++j) A[k][j] = A[j][k];
+            T a[4];
+            asm volatile("" ::: "memory");
+            fb += Solver<T>::solve(A, b, a);
+            if (omega != T(1)) {
+                a[0] = (T(1) - omega) + omega * a[0];
+                a[1] *= omega;
+                a[2] *= omega;
+                a[3] *= omega;
+                const T inv = rsqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) a[k] *= inv;
+            }
+            const cplx<T> g11 = mk(a[0], a[3]), g12 = mk(a[2], a[1]), g21 = mk(-a[2], a[1]), g22 = mk(a[0], -a[3]);
+            if (h == 0) {
+#pragma unroll 1
+                for (int l = 0; l < 5; ++l) {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {  // rows P, Q of G U and of G Omega
+                        const cplx<T> xp = lk(l, 3 * P + k), xq = lk(l, 3 * Q + k);
+                        lk(l, 3 * P + k) = cfma(g12, xq, cmul(g11, xp));
+                        lk(l, 3 * Q + k) = cfma(g22, xq, cmul(g21, xp));
+                    }
+                }
+            } else {
+#pragma unroll 1
+                for (int l = 0; l < 4; ++l) {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {  // columns P, Q of U G^dag
+                        const cplx<T> xp = lk(l, 3 * k + P), xq = lk(l, 3 * k + Q);
+                        lk(l, 3 * k + P) = cfmac(xq, g12, cmulc(xp, g11));
+                        lk(l, 3 * k + Q) = cfmac(xq, g22, cmulc(xp, g21));
+                    }
+                }
+            }
+            asm volatile("" ::: "memory");
+        }
+        // FP32 re-unitarisation: Omega every half-sweep, the links in the odd one
+        {
+            const int l0 = ACC ? 0 : 4;
+            const int l1 = h == 0 ? 5 : 4;
+#pragma unroll 1
+            for (int l = l0; l < l1; ++l) {
+                cplx<T> m[9];
+#pragma unroll
+                for (int e = 0; e < 9; ++e) m[e] = lk(l, e);
+                m3_reunitarise_same(m);
+#pragma unroll
+                for (int e = 0; e < 9; ++e) lk(l, e) = m[e];
+            }
+            asm volatile("" ::: "memory");
+        }
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            cplx<T>* dst = U + lidx(g, mu, pl, 0, sl[mu]);
+#pragma unroll 1
+            for (int e = 0; e < 9; ++e) dst[(size_t)e * g.vh] = lk(mu, e);
+        }
+        if (h == 0) {
+#pragma unroll
+            for (int e = 0; e < 9; ++e) G[gidx(g, parity, e, s)] = lk(4, e);
+        }
+        if (ACC) {
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const T tr = lk(l, 0).x + lk(l, 4).x + lk(l, 8).x;
+                const T ti = lk(l, 0).y + lk(l, 4).y + lk(l, 8).y;
+                rsum += (double)tr * (double)tr + (double)ti * (double)ti;
+            }
+        }
+    }
+    __shared__ double red[NT / 32];
+    if (ACC) {
+        const double tot = block_sum(rsum, red);
+        if (threadIdx.x == 0) bt.partial[blockIdx.x] = tot;
+    }
+    {
+        // lane 0 of each pair reports the pair's fallbacks
+        const int w = __reduce_add_sync(0xffffffffu, h == 0 ? fb : 0);
+        if ((threadIdx.x & 31) == 0 && w) atomicAdd(&bt.state[f].fallbacks, w);
+    }
+}
+
 // R over all links of each field, into per-block partials (same block map as
 // the half-sweep).
-template <typename T, int NT>
-__global__ void __launch_bounds__(NT) k_functional(SweepBatch bt) {
+template <typename T>
+__global__ void __launch_bounds__(128) k_functional(SweepBatch bt) {
     const int f = field_of_block(bt.desc, bt.nf, blockIdx.x);
     const FieldDesc fd = bt.desc[f];
     const Geom g = fd.geo;
     const cplx<T>* __restrict__ U = reinterpret_cast<const cplx<T>*>(fd.U);
-    const int s = (blockIdx.x - fd.blk0) * NT + threadIdx.x;
+    const int s = (blockIdx.x - fd.blk0) * blockDim.x + threadIdx.x;
     double r = 0.0;
     if (s < g.vh) {
 #pragma unroll
@@ -741,7 +908,7 @@ __global__ void __launch_bounds__(NT) k_functional(SweepBatch bt) {
                 r += tr * tr + ti * ti;
             }
     }
-    __shared__ double red[NT / 32];
+    __shared__ double red[4];
     const double tot = block_sum(r, red);
     if (threadIdx.x == 0) bt.partial[blockIdx.x] = tot;
 }
@@ -797,15 +964,15 @@ __global__ void __launch_bounds__(256) k_finalize(SweepBatch bt, int mode) {
 }
 
 // Re-unitarise the links and Omega of fields with reunit_pending set.
-template <typename T, int NT>
-__global__ void __launch_bounds__(NT) k_reunit_pending(SweepBatch bt) {
+template <typename T>
+__global__ void __launch_bounds__(128) k_reunit_pending(SweepBatch bt) {
     const int f = field_of_block(bt.desc, bt.nf, blockIdx.x);
     if (!bt.state[f].reunit_pending) return;
     const FieldDesc fd = bt.desc[f];
     const Geom g = fd.geo;
     cplx<T>* __restrict__ U = reinterpret_cast<cplx<T>*>(fd.U);
     cplx<T>* __restrict__ G = reinterpret_cast<cplx<T>*>(fd.G);
-    const int s = (blockIdx.x - fd.blk0) * NT + threadIdx.x;
+    const int s = (blockIdx.x - fd.blk0) * blockDim.x + threadIdx.x;
     if (s >= g.vh) return;
     for (int p = 0; p < 2; ++p) {
         cplx<T> m[9];
@@ -825,13 +992,102 @@ __global__ void __launch_bounds__(NT) k_reunit_pending(SweepBatch bt) {
 // ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
+// Threads per block of the half-sweep kernel, per precision; set by
+// mcg_set_sweep_block (the block-size autotuner).  FP64 runs one thread per
+// site (64 or 128 threads); FP32 runs the pair-split kernel, two threads per
+// site (64, 128 or 256 threads).
+static int g_sweep_nt[2] = {128, 128};
+
+int sweep_block(int prec) { return g_sweep_nt[prec == MCG_F64 ? 0 : 1]; }
+void set_sweep_block(int prec, int nt) { g_sweep_nt[prec == MCG_F64 ? 0 : 1] = nt; }
+int sweep_sites_per_block(int prec) { return prec == MCG_F64 ? sweep_block(prec) : sweep_block(prec) / 2; }
+
 template <typename T>
-static int enqueue_sweep(const SweepBatch& bt, size_t smem, cudaStream_t st) {
-    constexpr int NT = sweep_threads<T>();
-    k_halfsweep<T, false, NT><<<bt.total_blocks, NT, smem, st>>>(bt, 0);
-    k_halfsweep<T, true, NT><<<bt.total_blocks, NT, smem, st>>>(bt, 1);
+static size_t halfsweep_smem(int nt) {
+    return sizeof(T) == 8 ? sizeof(cplx<T>) * 81 * nt : sizeof(cplx<T>) * 45 * nt;
+}
+
+template <typename K>
+static int raise_smem(K kernel, size_t smem) {
+    MCG_CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return 0;
+}
+
+template <typename T>
+static int prepare_halfsweep(int nt) {
+    static bool done[3] = {false, false, false};
+    const int slot = nt == 64 ? 0 : (nt == 128 ? 1 : 2);
+    if (done[slot]) return 0;
+    const size_t smem = halfsweep_smem<T>(nt);
+    int rc = 0;
+    if constexpr (sizeof(T) == 8) {
+        if (nt == 128) {
+            if ((rc = raise_smem(k_halfsweep<T, false, 128>, smem)) || (rc = raise_smem(k_halfsweep<T, true, 128>, smem)))
+                return rc;
+        } else {
+            if ((rc = raise_smem(k_halfsweep<T, false, 64>, smem)) || (rc = raise_smem(k_halfsweep<T, true, 64>, smem)))
+                return rc;
+        }
+    } else {
+        if (nt == 256) {
+            if ((rc = raise_smem(k_halfsweep_pair<T, false, 256>, smem)) ||
+                (rc = raise_smem(k_halfsweep_pair<T, true, 256>, smem)))
+                return rc;
+        } else if (nt == 128) {
+            if ((rc = raise_smem(k_halfsweep_pair<T, false, 128>, smem)) ||
+                (rc = raise_smem(k_halfsweep_pair<T, true, 128>, smem)))
+                return rc;
+        } else {
+            if ((rc = raise_smem(k_halfsweep_pair<T, false, 64>, smem)) ||
+                (rc = raise_smem(k_halfsweep_pair<T, true, 64>, smem)))
+                return rc;
+        }
+    }
+    done[slot] = true;
+    return 0;
+}
+
+template <typename T>
+static void launch_halfsweep(int nt, bool acc, const SweepBatch& bt, int parity, int nblocks, cudaStream_t st) {
+    const size_t smem = halfsweep_smem<T>(nt);
+    if constexpr (sizeof(T) == 8) {
+        if (nt == 128) {
+            if (acc)
+                k_halfsweep<T, true, 128><<<nblocks, 128, smem, st>>>(bt, parity);
+            else
+                k_halfsweep<T, false, 128><<<nblocks, 128, smem, st>>>(bt, parity);
+        } else {
+            if (acc)
+                k_halfsweep<T, true, 64><<<nblocks, 64, smem, st>>>(bt, parity);
+            else
+                k_halfsweep<T, false, 64><<<nblocks, 64, smem, st>>>(bt, parity);
+        }
+    } else {
+        if (nt == 256) {
+            if (acc)
+                k_halfsweep_pair<T, true, 256><<<nblocks, 256, smem, st>>>(bt, parity);
+            else
+                k_halfsweep_pair<T, false, 256><<<nblocks, 256, smem, st>>>(bt, parity);
+        } else if (nt == 128) {
+            if (acc)
+                k_halfsweep_pair<T, true, 128><<<nblocks, 128, smem, st>>>(bt, parity);
+            else
+                k_halfsweep_pair<T, false, 128><<<nblocks, 128, smem, st>>>(bt, parity);
+        } else {
+            if (acc)
+                k_halfsweep_pair<T, true, 64><<<nblocks, 64, smem, st>>>(bt, parity);
+            else
+                k_halfsweep_pair<T, false, 64><<<nblocks, 64, smem, st>>>(bt, parity);
+        }
+    }
+}
+
+template <typename T>
+static int enqueue_sweep(const SweepBatch& bt, int nt, int spb, cudaStream_t st) {
+    launch_halfsweep<T>(nt, false, bt, 0, bt.total_blocks, st);
+    launch_halfsweep<T>(nt, true, bt, 1, bt.total_blocks, st);
     k_finalize<<<bt.nf, 256, 0, st>>>(bt, 0);
-    if (bt.reunit_every > 0) k_reunit_pending<T, NT><<<bt.total_blocks, NT, 0, st>>>(bt);
+    if (bt.reunit_every > 0) k_reunit_pending<T><<<bt.total_blocks, spb, 0, st>>>(bt);
     return 0;
 }
 
@@ -839,12 +1095,14 @@ template <typename T>
 int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, FieldState* h_state, double* d_hist,
                   int hist_len, double tol, int window, double omega, int reunit_every, int abs_cap,
                   int check_every, bool fresh, cudaStream_t stream) {
-    constexpr int NT = sweep_threads<T>();
+    const int prec = sizeof(T) == 8 ? MCG_F64 : MCG_F32;
+    const int NT = sweep_block(prec);
+    const int SPB = sweep_sites_per_block(prec);
     const int nf = (int)fields_in.size();
     std::vector<FieldDesc> fields = fields_in;
     int total = 0;
     for (auto& fd : fields) {
-        fd.nblk = (fd.geo.vh + NT - 1) / NT;
+        fd.nblk = (fd.geo.vh + SPB - 1) / SPB;
         fd.blk0 = total;
         total += fd.nblk;
     }
@@ -888,19 +1146,9 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
     bt.reunit_every = reunit_every;
     bt.omega = omega;
 
-    const size_t smem = sizeof(cplx<T>) * 72 * NT;
-    {
-        static bool attr_set = false;
-        if (!attr_set) {
-            MCG_CK(cudaFuncSetAttribute(k_halfsweep<T, false, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
-            MCG_CK(cudaFuncSetAttribute(k_halfsweep<T, true, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
-            attr_set = true;
-        }
-    }
+    if ((rc = prepare_halfsweep<T>(NT))) return rc;
 
-    k_functional<T, NT><<<total, NT, 0, stream>>>(bt);
+    k_functional<T><<<total, SPB, 0, stream>>>(bt);
     k_finalize<<<nf, 256, 0, stream>>>(bt, fresh ? 1 : 2);
     MCG_CK(cudaGetLastError());
     note_launches(2);
@@ -917,7 +1165,7 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     MCG_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
-    for (int i = 0; i < chunk; ++i) enqueue_sweep<T>(bt, smem, cs);
+    for (int i = 0; i < chunk; ++i) enqueue_sweep<T>(bt, NT, SPB, cs);
     cudaError_t ce = cudaStreamEndCapture(cs, &graph);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
     ce = cudaGraphInstantiate(&exec, graph, 0);
@@ -953,14 +1201,16 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
 template <typename T>
 int time_halfsweep(void* U, void* G, const Geom& g, int parity, int nreps, int flush_l2, float* ms,
                    cudaStream_t stream) {
-    constexpr int NT = sweep_threads<T>();
+    const int prec = sizeof(T) == 8 ? MCG_F64 : MCG_F32;
+    const int NT = sweep_block(prec);
+    const int SPB = sweep_sites_per_block(prec);
     int rc = 0;
     FieldDesc fd;
     fd.U = U;
     fd.G = G;
     fd.geo = g;
     fd.blk0 = 0;
-    fd.nblk = (g.vh + NT - 1) / NT;
+    fd.nblk = (g.vh + SPB - 1) / SPB;
     fd.norm = 1.0 / (9.0 * 8.0 * g.vh);
     FieldDesc* d_desc = (FieldDesc*)scratch_device("time.desc", sizeof(FieldDesc), &rc);
     if (rc) return rc;
@@ -988,11 +1238,7 @@ int time_halfsweep(void* U, void* G, const Geom& g, int parity, int nreps, int f
     bt.window = 1;
     bt.reunit_every = 0;
     bt.omega = 1.0;
-    const size_t smem = sizeof(cplx<T>) * 72 * NT;
-    {
-        MCG_CK(cudaFuncSetAttribute(k_halfsweep<T, false, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        MCG_CK(cudaFuncSetAttribute(k_halfsweep<T, true, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    }
+    if ((rc = prepare_halfsweep<T>(NT))) return rc;
     cudaEvent_t e0, e1;
     MCG_CK(cudaEventCreate(&e0));
     MCG_CK(cudaEventCreate(&e1));
@@ -1002,10 +1248,7 @@ int time_halfsweep(void* U, void* G, const Geom& g, int parity, int nreps, int f
             cudaMemsetAsync(flush, r & 0xff, flush_bytes, stream);
         }
         cudaEventRecord(e0, stream);
-        if (parity)
-            k_halfsweep<T, true, NT><<<fd.nblk, NT, smem, stream>>>(bt, 1);
-        else
-            k_halfsweep<T, false, NT><<<fd.nblk, NT, smem, stream>>>(bt, 0);
+        launch_halfsweep<T>(NT, parity != 0, bt, parity, fd.nblk, stream);
         cudaEventRecord(e1, stream);
         cudaError_t ce = cudaEventSynchronize(e1);
         if (ce != cudaSuccess) {

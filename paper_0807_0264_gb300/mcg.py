@@ -87,6 +87,8 @@ def _load() -> ctypes.CDLL:
         "mcg_time_halfsweep": ([P, P, L, I, I, I, ctypes.POINTER(ctypes.c_float), P], I),
         "mcg_kernel_launches": ([], ctypes.c_longlong),
         "mcg_plaquette_static": ([P, P, L, P], I),
+        "mcg_set_sweep_block": ([I, I], I),
+        "mcg_get_sweep_block": ([I], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -102,7 +104,7 @@ EXPORTS = ("mcg_version", "mcg_last_error", "mcg_release", "mcg_pack_links", "mc
            "mcg_unpack_gauge", "mcg_unpack_center", "mcg_convert", "mcg_set_identity_gauge", "mcg_plaquette",
            "mcg_functional", "mcg_apply_gauge", "mcg_reunitarise", "mcg_smear", "mcg_fix", "mcg_center_project",
            "mcg_precondition_fix", "mcg_precondition_levels", "mcg_time_halfsweep", "mcg_kernel_launches",
-           "mcg_plaquette_static")
+           "mcg_plaquette_static", "mcg_set_sweep_block", "mcg_get_sweep_block")
 
 
 def library() -> ctypes.CDLL:
@@ -408,3 +410,30 @@ def mcg_plaquette_static(U: torch.Tensor, dims, out: torch.Tensor, stream=None) 
     _check("mcg_plaquette_static",
            _lib.mcg_plaquette_static(_ptr(U), _ptr(out), lattice(dims, U.shape[0], precision_of(U)), _stream(stream)))
     return out
+
+
+def mcg_set_sweep_block(precision: int, threads: int) -> None:
+    _check("mcg_set_sweep_block", _lib.mcg_set_sweep_block(int(precision), int(threads)))
+
+
+def mcg_get_sweep_block(precision: int) -> int:
+    return int(_lib.mcg_get_sweep_block(int(precision)))
+
+
+def autotune_sweep_block(U: torch.Tensor, dims, reps: int = 10) -> dict:
+    """Pick the half-sweep block size for U's precision (64/128 threads for
+    FP64, 64/128/256 for the pair-split FP32 kernel) by timing each on a
+    scratch copy of U (L2 flushed between launches); keeps the fastest for the
+    process and returns the timings in ms per launch."""
+    prec = precision_of(U)
+    Uc = U[:1].clone()
+    G = identity_gauge(dims, 1, prec, U.device)
+    times = {}
+    for nt in ((64, 128, 256) if prec == F32 else (64, 128)):
+        mcg_set_sweep_block(prec, nt)
+        mcg_time_halfsweep(Uc, G, dims, 1, 2, True)  # warm-up
+        times[nt] = 0.5 * (mcg_time_halfsweep(Uc, G, dims, 1, reps, True) +
+                           mcg_time_halfsweep(Uc, G, dims, 0, reps, True))
+    best = min(times, key=times.get)
+    mcg_set_sweep_block(prec, best)
+    return {"chosen": best, "ms_per_launch": times}
