@@ -27,6 +27,13 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# DRAM traffic of the dominant kernel per launch, from one ncu capture
+# (profiles/k_halfsweep_pair_f32_24x24x24x24.md, 24^4 scaled to the 160 000
+# sites of a 20^3 x 40 launch); reported only while the kernel source is the
+# one that was profiled
+TRAFFIC_FP32 = {"bytes_per_launch": 158.3e6, "source_sha256_prefix": "71cd4ac4b67e3600",
+                "profile": "profiles/k_halfsweep_pair_f32_24x24x24x24.md"}
+
 METRIC = "MCG site-updates/s & time-to-ΔR<1e-10 at 20^3x40: batched/mixed vs plain FP64"
 UNIT = "site-updates/s"
 DIMS = (20, 20, 20, 40)
@@ -45,6 +52,9 @@ def parse():
     ap.add_argument("--dims", type=int, nargs=4, default=list(DIMS))
     ap.add_argument("--levels", type=int, nargs="+", default=list(LEVELS))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--profile-slice", action="store_true",
+                    help="one bench step with sweeps capped (FP32 100 + FP64 1 per fix, levels 0 and 4, block sizes "
+                         "128): the same kernels and launch shapes in ~1000 launches, for an ncu launch list")
     return ap.parse_args()
 
 
@@ -212,6 +222,20 @@ def main():
     U_out = mcg.empty_links(dims, nl, mcg.F64, dev)
     G_out = mcg.empty_gauge(dims, nl, mcg.F64, dev)
     Z_out = torch.empty((nl, 4, 2, V // 2), dtype=torch.int8, device=dev)
+    if args.profile_slice:
+        # FP32 : FP64 sweeps 100 : 1 per fix, close to the full step's ratio
+        sl = mcg.Params(tol=-1e300, max_sweeps=101, check_every=25, reunit_every=50, fp32_sweeps=100,
+                        fp32_tol=-1e300, fp32_window=25, fp32_overrelax=1.7)
+        mcg.mcg_set_sweep_block(mcg.F32, 128)
+        mcg.mcg_set_sweep_block(mcg.F64, 128)
+        torch.cuda.synchronize(dev)
+        n0 = mcg.mcg_kernel_launches()
+        res = mcg.mcg_precondition_levels(U, dims, [0, 4], sl, rho=RHO, eps=1.0, smear_precision=mcg.F32)[3]
+        torch.cuda.synchronize(dev)
+        print(json.dumps({"profile_slice": True, "launches": mcg.mcg_kernel_launches() - n0,
+                          "sweeps": [r["sweeps_smeared"] + r["sweeps_fixed"] for r in res]}), flush=True)
+        return
+
     tuned = {"f32": mcg.autotune_sweep_block(mcg.mcg_convert(U, mcg.F32), dims),
              "f64": mcg.autotune_sweep_block(U, dims, reps=3)}
     mixed = mcg.Params(tol=1e-10, max_sweeps=30000, check_every=25, reunit_every=50, fp32_sweeps=30000,
@@ -334,10 +358,16 @@ def main():
     share64 = sw64 * 2 * t64
     vh = V // 2
     bytes32 = vh * (8 * 72 * 2 + 72 * 2)  # 8 links read+write, Omega read+write, FP32
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_0807_0264_gb300", "csrc", "mcg_sweep.cu")
+    same_src = hashlib.sha256(open(src, "rb").read()).hexdigest().startswith(TRAFFIC_FP32["source_sha256_prefix"])
     if share32 >= share64:
         achieved = bytes32 / ((t32 + t32_even) / 2 / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": "k_halfsweep<float>", "achieved": achieved, "peak": 6780.0,
-                "unit": "GB/s", "frac": achieved / 6780.0, "traffic": None,
+        roof = {"bound": "hbm", "kernel": "k_halfsweep_pair<float>", "achieved": achieved, "peak": 6780.0,
+                "unit": "GB/s", "frac": achieved / 6780.0,
+                "traffic": TRAFFIC_FP32["bytes_per_launch"] if same_src else None,
+                "traffic_source": TRAFFIC_FP32["profile"] if same_src else "kernel changed since the capture",
                 "algorithmic_bytes_per_launch": bytes32, "ms_per_launch": (t32 + t32_even) / 2,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     else:

@@ -868,12 +868,16 @@ __global__ void __launch_bounds__(NT) k_halfsweep_pair(SweepBatch bt, int parity
             for (int e = 0; e < 9; ++e) G[gidx(g, parity, e, s)] = lk(4, e);
         }
         if (ACC) {
+            // the lane's 4 links summed in FP32 (|tr|^2 <= 9 each), widened once;
+            // FP64 work stays off this kernel's critical path
+            T r4 = T(0);
 #pragma unroll
             for (int l = 0; l < 4; ++l) {
                 const T tr = lk(l, 0).x + lk(l, 4).x + lk(l, 8).x;
                 const T ti = lk(l, 0).y + lk(l, 4).y + lk(l, 8).y;
-                rsum += (double)tr * (double)tr + (double)ti * (double)ti;
+                r4 = fma(tr, tr, fma(ti, ti, r4));
             }
+            rsum = (double)r4;
         }
     }
     __shared__ double red[NT / 32];
