@@ -90,6 +90,14 @@ typedef struct {
                        /* use the plain relaxation.                             */
 } mcg_params;
 
+/* One field of a heterogeneous batch: device pointers to its links and its
+ * gauge transform (layout above) and its dims. */
+typedef struct {
+    void* U;
+    void* G;
+    int dims[4];
+} mcg_field;
+
 /* Per-field result of mcg_precondition_fix (Sec. II.B pipeline). */
 typedef struct {
     double V_smeared;      /* V_U reached on the smeared field (0 if nsmear=0) */
@@ -233,6 +241,32 @@ int mcg_precondition_fix(void* U, void* G, int8_t* Z, const mcg_lattice* lat, co
 int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_out, const mcg_lattice* lat,
                             const mcg_params* params, double rho, double eps, const int* nsmear, int nlevels,
                             int smear_precision, mcg_precond_result* results, cudaStream_t stream);
+
+/*
+ * MCG relaxation (as mcg_fix) of a batch of fields of any sizes, all of one
+ * precision: one launch per half-sweep covers every field; a field stops
+ * (its blocks exit at entry) once it has converged.  fields: host array of
+ * nfields entries.  R_out / sweeps_out: host, nfields entries (may be NULL).
+ * Returns MCG_OK when every field converged, else MCG_NOT_CONVERGED.
+ */
+int mcg_fix_batch(const mcg_field* fields, int nfields, int precision, const mcg_params* params, double* R_out,
+                  int* sweeps_out, cudaStream_t stream);
+
+/*
+ * Gribov-copy search (Sec. I: MCG fixing is plagued by Gribov copies, and
+ * higher maxima of the functional change the vortex content): for every copy,
+ * U (device) holds its configuration's links and G (device) a random initial
+ * transform Omega0; the call applies Omega0 (U <- U^Omega0), fixes all copies
+ * of all configurations as one batch (G then holds each copy's total
+ * transform, U = U_config^G), and picks per configuration the copy with the
+ * largest V_U (ties keep the lower copy index).  config_of_copy: host,
+ * ncopies entries in [0, nconfigs).  R_out / sweeps_out: host, per copy (may
+ * be NULL); best_copy / best_V: host, per configuration (may be NULL).
+ * Returns MCG_OK or MCG_NOT_CONVERGED.  Synchronises.
+ */
+int mcg_gribov_search(const mcg_field* copies, int ncopies, const int* config_of_copy, int nconfigs, int precision,
+                      const mcg_params* params, double* R_out, int* sweeps_out, int* best_copy, double* best_V,
+                      cudaStream_t stream);
 
 /* ---- measurement ---------------------------------------------------------- */
 

@@ -186,9 +186,18 @@ static int check_params(const mcg_params* p) {
 // ---------------------------------------------------------------------------
 // MCG fix orchestration
 // ---------------------------------------------------------------------------
-static int fix_impl(void* U, void* G, const mcg_lattice* lat, const Geom& g, const mcg_params* prm, double* R_out,
-                    int* sweeps_out, int* sweeps32_out, double* R_hist, cudaStream_t st) {
-    const int nf = lat->nfields;
+// One field of a (possibly heterogeneous) batch.
+struct FieldSpec {
+    void* U;
+    void* G;
+    Geom g;
+};
+
+// MCG relaxation of a batch of fields (all of one precision, any sizes), one
+// launch per half-sweep for the whole batch.
+static int fix_fields(const std::vector<FieldSpec>& fs, int prec, const mcg_params* prm, double* R_out,
+                      int* sweeps_out, int* sweeps32_out, double* R_hist, cudaStream_t st) {
+    const int nf = (int)fs.size();
     int rc = 0;
     FieldState* d_state = (FieldState*)scratch_device("fix.state", sizeof(FieldState) * nf, &rc);
     if (rc) return rc;
@@ -201,25 +210,32 @@ static int fix_impl(void* U, void* G, const mcg_lattice* lat, const Geom& g, con
         if (rc) return rc;
         MCG_CK(cudaMemsetAsync(d_hist, 0, sizeof(double) * hist_len * (size_t)nf, st));
     }
-    const double norm = 1.0 / (9.0 * 8.0 * g.vh);
-    const size_t le = link_elems(g), ge = gauge_elems(g);
     std::vector<int> s32(nf, 0);
     bool fresh = true;
 
-    if (lat->precision == MCG_F64 && prm->fp32_sweeps > 0) {
-        // FP32 phase on a copy of the links and the transform of this call
-        void* U32 = scratch_device("fix.U32", 8 * le * nf, &rc);
+    if (prec == MCG_F64 && prm->fp32_sweeps > 0) {
+        // FP32 phase on copies of the links and on the transform of this call
+        size_t le_tot = 0, ge_tot = 0;
+        for (const auto& f : fs) {
+            le_tot += link_elems(f.g);
+            ge_tot += gauge_elems(f.g);
+        }
+        char* U32 = (char*)scratch_device("fix.U32", 8 * le_tot, &rc);
         if (rc) return rc;
-        void* W32 = scratch_device("fix.W32", 8 * ge * nf, &rc);
+        char* W32 = (char*)scratch_device("fix.W32", 8 * ge_tot, &rc);
         if (rc) return rc;
-        if ((rc = launch_convert(U, MCG_F64, U32, MCG_F32, le * nf, st))) return rc;
-        if ((rc = launch_identity_gauge(W32, MCG_F32, g, nf, st))) return rc;
         std::vector<FieldDesc> fds(nf);
+        size_t lo = 0, go = 0;
         for (int f = 0; f < nf; ++f) {
-            fds[f].U = (char*)U32 + 8 * le * f;
-            fds[f].G = (char*)W32 + 8 * ge * f;
+            const Geom& g = fs[f].g;
+            fds[f].U = U32 + 8 * lo;
+            fds[f].G = W32 + 8 * go;
             fds[f].geo = g;
-            fds[f].norm = norm;
+            fds[f].norm = 1.0 / (9.0 * 8.0 * g.vh);
+            if ((rc = launch_convert(fs[f].U, MCG_F64, fds[f].U, MCG_F32, link_elems(g), st))) return rc;
+            if ((rc = launch_identity_gauge(fds[f].G, MCG_F32, g, 1, st))) return rc;
+            lo += link_elems(g);
+            go += gauge_elems(g);
         }
         const int cap = std::min(prm->fp32_sweeps, prm->max_sweeps);
         rc = run_fix_phase<float>(fds, d_state, h_state, d_hist, hist_len, prm->fp32_tol, prm->fp32_window,
@@ -227,17 +243,18 @@ static int fix_impl(void* U, void* G, const mcg_lattice* lat, const Geom& g, con
         if (rc) return rc;
         for (int f = 0; f < nf; ++f) s32[f] = h_state[f].sweep;
         // hand-off: FP64 re-unitarised transform applied to the FP64 links
-        if ((rc = launch_handoff(W32, (double*)U, (double*)G, g, nf, st))) return rc;
+        for (int f = 0; f < nf; ++f)
+            if ((rc = launch_handoff(fds[f].G, (double*)fs[f].U, (double*)fs[f].G, fs[f].g, 1, st))) return rc;
         fresh = false;
     }
     std::vector<FieldDesc> fds(nf);
     for (int f = 0; f < nf; ++f) {
-        fds[f].U = (char*)U + elem_bytes(lat->precision) * le * f;
-        fds[f].G = (char*)G + elem_bytes(lat->precision) * ge * f;
-        fds[f].geo = g;
-        fds[f].norm = norm;
+        fds[f].U = fs[f].U;
+        fds[f].G = fs[f].G;
+        fds[f].geo = fs[f].g;
+        fds[f].norm = 1.0 / (9.0 * 8.0 * fs[f].g.vh);
     }
-    if (lat->precision == MCG_F64)
+    if (prec == MCG_F64)
         rc = run_fix_phase<double>(fds, d_state, h_state, d_hist, hist_len, prm->tol, 1, 1.0, prm->reunit_every,
                                    prm->max_sweeps, prm->check_every, fresh, st);
     else
@@ -256,6 +273,36 @@ static int fix_impl(void* U, void* G, const mcg_lattice* lat, const Geom& g, con
         MCG_CK(cudaStreamSynchronize(st));
     }
     return all ? MCG_OK : MCG_NOT_CONVERGED;
+}
+
+// uniform batch: nfields fields of lat's dims stored back to back
+static int fix_impl(void* U, void* G, const mcg_lattice* lat, const Geom& g, const mcg_params* prm, double* R_out,
+                    int* sweeps_out, int* sweeps32_out, double* R_hist, cudaStream_t st) {
+    const size_t eb = elem_bytes(lat->precision);
+    std::vector<FieldSpec> fs(lat->nfields);
+    for (int f = 0; f < lat->nfields; ++f) {
+        fs[f].U = (char*)U + eb * link_elems(g) * f;
+        fs[f].G = (char*)G + eb * gauge_elems(g) * f;
+        fs[f].g = g;
+    }
+    return fix_fields(fs, lat->precision, prm, R_out, sweeps_out, sweeps32_out, R_hist, st);
+}
+
+// validate one entry of an mcg_field array
+static int field_spec(const mcg_field& in, int prec, FieldSpec* out) {
+    mcg_lattice lat;
+    for (int d = 0; d < 4; ++d) lat.dims[d] = in.dims[d];
+    lat.nfields = 1;
+    lat.precision = prec;
+    int rc = check_lat(&lat, &out->g);
+    if (rc) return rc;
+    if (!in.U || !in.G) return fail(MCG_BAD_ARG, "null field pointer");
+    const size_t eb = elem_bytes(prec);
+    if (overlap(in.U, eb * link_elems(out->g), in.G, eb * gauge_elems(out->g)))
+        return fail(MCG_BAD_ARG, "U and G of a field overlap");
+    out->U = in.U;
+    out->G = in.G;
+    return 0;
 }
 
 }  // namespace mcg
@@ -599,6 +646,57 @@ int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_o
         r.status = status;
     }
     return status;
+}
+
+int mcg_fix_batch(const mcg_field* fields, int nfields, int precision, const mcg_params* params, double* R_out,
+                  int* sweeps_out, cudaStream_t stream) {
+    if (!fields || nfields < 1) return fail(MCG_BAD_ARG, "fields is NULL or nfields < 1");
+    if (precision != MCG_F64 && precision != MCG_F32) return fail(MCG_BAD_ARG, "bad precision");
+    int rc = check_params(params);
+    if (rc) return rc;
+    std::vector<FieldSpec> fs(nfields);
+    for (int f = 0; f < nfields; ++f)
+        if ((rc = field_spec(fields[f], precision, &fs[f]))) return rc;
+    return fix_fields(fs, precision, params, R_out, sweeps_out, nullptr, nullptr, stream);
+}
+
+int mcg_gribov_search(const mcg_field* copies, int ncopies, const int* config_of_copy, int nconfigs, int precision,
+                      const mcg_params* params, double* R_out, int* sweeps_out, int* best_copy, double* best_V,
+                      cudaStream_t stream) {
+    if (!copies || ncopies < 1 || !config_of_copy || nconfigs < 1) return fail(MCG_BAD_ARG, "bad copy list");
+    if (precision != MCG_F64 && precision != MCG_F32) return fail(MCG_BAD_ARG, "bad precision");
+    int rc = check_params(params);
+    if (rc) return rc;
+    std::vector<FieldSpec> fs(ncopies);
+    for (int f = 0; f < ncopies; ++f) {
+        if ((rc = field_spec(copies[f], precision, &fs[f]))) return rc;
+        if (config_of_copy[f] < 0 || config_of_copy[f] >= nconfigs) return fail(MCG_BAD_ARG, "config index out of range");
+    }
+    // each copy starts as U^Omega0 with its own random Omega0; the fix then
+    // accumulates onto Omega0, so G ends as the total transform of the copy
+    for (int f = 0; f < ncopies; ++f)
+        if ((rc = launch_apply_gauge(fs[f].U, fs[f].G, precision, fs[f].g, 1, stream))) return rc;
+    std::vector<double> R(ncopies);
+    std::vector<int> sw(ncopies);
+    int st = fix_fields(fs, precision, params, R.data(), sw.data(), nullptr, nullptr, stream);
+    if (st != MCG_OK && st != MCG_NOT_CONVERGED) return st;
+    std::vector<double> bestV(nconfigs, -1.0);
+    std::vector<int> best(nconfigs, -1);
+    for (int f = 0; f < ncopies; ++f) {
+        const double V = R[f] / (9.0 * 8.0 * fs[f].g.vh);
+        const int c = config_of_copy[f];
+        if (V > bestV[c]) {  // ties keep the lower copy index
+            bestV[c] = V;
+            best[c] = f;
+        }
+        if (R_out) R_out[f] = R[f];
+        if (sweeps_out) sweeps_out[f] = sw[f];
+    }
+    for (int c = 0; c < nconfigs; ++c) {
+        if (best_copy) best_copy[c] = best[c];
+        if (best_V) best_V[c] = bestV[c];
+    }
+    return st;
 }
 
 }  // extern "C"

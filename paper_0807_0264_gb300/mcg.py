@@ -45,6 +45,10 @@ class mcg_params(ctypes.Structure):
                 ("fp32_window", ctypes.c_int), ("fp32_overrelax", ctypes.c_double)]
 
 
+class mcg_field(ctypes.Structure):
+    _fields_ = [("U", ctypes.c_void_p), ("G", ctypes.c_void_p), ("dims", ctypes.c_int * 4)]
+
+
 class mcg_precond_result(ctypes.Structure):
     _fields_ = [("V_smeared", ctypes.c_double), ("V_fixed", ctypes.c_double), ("plaquette_in", ctypes.c_double),
                 ("plaquette_out", ctypes.c_double), ("vortices", ctypes.c_longlong),
@@ -88,6 +92,9 @@ def _load() -> ctypes.CDLL:
         "mcg_kernel_launches": ([], ctypes.c_longlong),
         "mcg_plaquette_static": ([P, P, L, P], I),
         "mcg_set_sweep_block": ([I, I], I),
+        "mcg_fix_batch": ([ctypes.POINTER(mcg_field), I, I, PR, P, P, P], I),
+        "mcg_gribov_search": ([ctypes.POINTER(mcg_field), I, ctypes.POINTER(ctypes.c_int), I, I, PR, P, P, P, P, P],
+                              I),
         "mcg_get_sweep_block": ([I], I),
     }
     for name, (args, res) in sig.items():
@@ -104,7 +111,8 @@ EXPORTS = ("mcg_version", "mcg_last_error", "mcg_release", "mcg_pack_links", "mc
            "mcg_unpack_gauge", "mcg_unpack_center", "mcg_convert", "mcg_set_identity_gauge", "mcg_plaquette",
            "mcg_functional", "mcg_apply_gauge", "mcg_reunitarise", "mcg_smear", "mcg_fix", "mcg_center_project",
            "mcg_precondition_fix", "mcg_precondition_levels", "mcg_time_halfsweep", "mcg_kernel_launches",
-           "mcg_plaquette_static", "mcg_set_sweep_block", "mcg_get_sweep_block")
+           "mcg_plaquette_static", "mcg_set_sweep_block", "mcg_get_sweep_block", "mcg_fix_batch",
+           "mcg_gribov_search")
 
 
 def library() -> ctypes.CDLL:
@@ -437,3 +445,86 @@ def autotune_sweep_block(U: torch.Tensor, dims, reps: int = 10) -> dict:
     best = min(times, key=times.get)
     mcg_set_sweep_block(prec, best)
     return {"chosen": best, "ms_per_launch": times}
+
+
+def _field_array(Us, Gs, dims_list):
+    n = len(Us)
+    arr = (mcg_field * n)()
+    for k, (U, G, d) in enumerate(zip(Us, Gs, dims_list)):
+        _need_cuda(U, G)
+        arr[k].U = U.data_ptr()
+        arr[k].G = G.data_ptr()
+        for j in range(4):
+            arr[k].dims[j] = int(d[j])
+    return arr
+
+
+def mcg_fix_batch(Us, Gs, dims_list, params: Params | None = None, stream=None) -> dict:
+    """MCG relaxation of fields of any sizes in one batch (in place).  Us, Gs:
+    single-field tensors (1, ...) of one precision.  Returns dict(R, sweeps, converged)."""
+    params = params or Params()
+    n = len(Us)
+    prec = precision_of(Us[0])
+    arr = _field_array(Us, Gs, dims_list)
+    R = (ctypes.c_double * n)()
+    sw = (ctypes.c_int * n)()
+    cp = params.c()
+    rc = _check("mcg_fix_batch", _lib.mcg_fix_batch(arr, n, prec, ctypes.byref(cp), R, sw, _stream(stream)),
+                allow=(OK, NOT_CONVERGED))
+    return dict(R=list(R), sweeps=list(sw), converged=(rc == OK))
+
+
+def mcg_gribov_search(Us, Gs, dims_list, config_of_copy, nconfigs: int, params: Params | None = None,
+                      stream=None) -> dict:
+    """Gribov-copy search in place: U_k (the configuration's links) and G_k (a
+    random initial transform) per copy; returns dict(R, sweeps, best_copy,
+    best_V, converged) with best_copy[c] the copy of configuration c with the
+    largest V_U."""
+    params = params or Params()
+    n = len(Us)
+    prec = precision_of(Us[0])
+    arr = _field_array(Us, Gs, dims_list)
+    cfg = (ctypes.c_int * n)(*[int(c) for c in config_of_copy])
+    R = (ctypes.c_double * n)()
+    sw = (ctypes.c_int * n)()
+    best = (ctypes.c_int * nconfigs)()
+    bestV = (ctypes.c_double * nconfigs)()
+    cp = params.c()
+    rc = _check("mcg_gribov_search",
+                _lib.mcg_gribov_search(arr, n, cfg, int(nconfigs), prec, ctypes.byref(cp), R, sw, best, bestV,
+                                       _stream(stream)), allow=(OK, NOT_CONVERGED))
+    return dict(R=list(R), sweeps=list(sw), best_copy=list(best), best_V=list(bestV), converged=(rc == OK))
+
+
+def autotune_schedule(Us, dims_list, params: Params, trial_sweeps: int = 40,
+                      chunks=(10, 25, 50)) -> dict:
+    """Tile and sweep-schedule autotuner for a batch: for every half-sweep
+    block size of the sweep precision and every graph chunk length
+    (check_every), time `trial_sweeps` sweeps of mcg_fix_batch on clones of
+    the batch (no stop test), keep the fastest: the block size is set for the
+    process, the chunk length is returned in params.check_every.  Only the
+    clones are modified."""
+    prec = F32 if (params.fp32_sweeps > 0 or precision_of(Us[0]) == F32) else F64
+    Uc = [mcg_convert(U, F32) if prec == F32 and precision_of(U) == F64 else U.clone() for U in Us]
+    Gc = [identity_gauge(d, 1, prec, U.device) for U, d in zip(Uc, dims_list)]
+    blocks = (64, 128, 256) if prec == F32 else (64, 128)
+    best = None
+    timings = {}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for nt in blocks:
+        mcg_set_sweep_block(prec, nt)
+        for ch in chunks:
+            p = Params(tol=-1e300, max_sweeps=trial_sweeps, check_every=ch, reunit_every=params.reunit_every)
+            mcg_fix_batch(Uc, Gc, dims_list, p)  # warm-up: graph build, caches
+            ev0.record()
+            mcg_fix_batch(Uc, Gc, dims_list, p)
+            ev1.record()
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1) / trial_sweeps
+            timings[f"{nt}x{ch}"] = ms
+            if best is None or ms < best[0]:
+                best = (ms, nt, ch)
+    mcg_set_sweep_block(prec, best[1])
+    params.check_every = best[2]
+    return {"precision": "f32" if prec == F32 else "f64", "block": best[1], "check_every": best[2],
+            "ms_per_sweep": timings}
