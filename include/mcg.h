@@ -268,6 +268,36 @@ int mcg_gribov_search(const mcg_field* copies, int ncopies, const int* config_of
                       const mcg_params* params, double* R_out, int* sweeps_out, int* best_copy, double* best_V,
                       cudaStream_t stream);
 
+/* ---- differentiation (not in the paper: the training pattern that
+ * differentiates the method) ------------------------------------------------
+ * Matrix-gradient convention: for a real loss L and a link U,
+ * G = dL/dRe U + i dL/dIm U (dL = Re tr(G^dag dU)); G arrays are FP64 in the
+ * link layout, i.e. the (re, im) pairs a real-view autograd gradient holds.
+ * The derivative along U -> exp(i eta T_a) U is Re tr(G^dag i T_a U). */
+
+/* Reverse-mode derivative of one smearing step U' = exp(iQ(U)) U (the step of
+ * mcg_smear, Sec. II.B): Gin = gradient w.r.t. U given Gout w.r.t. U'.
+ * Chain rule per link: Gin += exp(iQ)^dag Gout; the adjoint of exp's Frechet
+ * derivative B = L(iQ, U Gout^dag); its traceless anti-Hermitian part K; then
+ * Gin += K C on the link and rho U^dag K scattered over every factor of every
+ * staple (atomic FP64 adds: summation order, hence the last bits, vary).
+ * U: the step's input field (FP64); Gout, Gin: FP64, link layout, distinct. */
+int mcg_smear_backward_step(const void* U, const double* Gout, double* Gin, const mcg_lattice* lat, double rho,
+                            double eps, cudaStream_t stream);
+
+/* Matrix gradient of R = sum |tr U|^2 (Sec. II.A): G = 2 tr(U) 1 per link. */
+int mcg_functional_matrix_grad(const void* U, double* G, const mcg_lattice* lat, cudaStream_t stream);
+
+/* Lie-algebra gradient of R with respect to the gauge transform:
+ * grad[f][i][a] = dR/d eps for Omega(x_i) -> exp(i eps lambda_a/2) Omega(x_i),
+ * i the lexicographic site index, a = 0..7 (Gell-Mann order).  FP64, device. */
+int mcg_grad_R(const void* U, double* grad, const mcg_lattice* lat, cudaStream_t stream);
+
+/* Gradient-ascent step on the gauge transform: W(x) = exp(i alpha sum_a
+ * grad_a(x) lambda_a/2), Omega(x) <- W(x) Omega(x), U_mu(x) <- W(x) U_mu(x)
+ * W(x+mu)^dag for all sites at once (uses library scratch for W). */
+int mcg_ascent_step(void* U, void* G, const double* grad, double alpha, const mcg_lattice* lat, cudaStream_t stream);
+
 /* ---- measurement ---------------------------------------------------------- */
 
 /* Mean duration of one launch of the half-sweep kernel (parity 0: even sites;

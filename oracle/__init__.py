@@ -67,6 +67,11 @@ def _load():
             lib.orc_vortex_count.restype = ctypes.c_longlong
             lib.orc_grad_R.argtypes = [P, P, P]
             lib.orc_generators.argtypes = [P]
+            lib.orc_expm_frechet.argtypes = [P, P, P]
+            lib.orc_staple_sum_paths.argtypes = [P, P, L, I, D, D, P]
+            lib.orc_staple_sum.argtypes = [P, P, L, I, D, D, P]
+            lib.orc_smear_step_backward.argtypes = [P, P, P, P, D, D]
+            lib.orc_functional_matrix_grad.argtypes = [P, P, P]
             _lib = lib
     return _lib
 
@@ -235,3 +240,51 @@ def precondition_and_fix(dims, U, rho: float, eps: float, nsmear: int, tol: floa
     out["vortex_density"] = tot / (6.0 * vol)
     out["G_total"] = compose_gauge(r2["G"], G1)
     return out
+
+
+def expm_frechet(X, A) -> np.ndarray:
+    """L(X, A) = d/dt exp(X + tA) at t = 0 for 3x3 complex X, A."""
+    X = np.ascontiguousarray(X, dtype=np.complex128).reshape(3, 3)
+    A = np.ascontiguousarray(A, dtype=np.complex128).reshape(3, 3)
+    L = np.zeros((3, 3), np.complex128)
+    _load().orc_expm_frechet(_p(X), _p(A), _p(L))
+    return L
+
+
+def staple_sum(dims, U, x: int, mu: int, cp: float, cr: float, from_paths: bool = False) -> np.ndarray:
+    U = _cfield(U)
+    C = np.zeros((3, 3), np.complex128)
+    fn = _load().orc_staple_sum_paths if from_paths else _load().orc_staple_sum
+    fn(_p(_dims(dims)), _p(U), int(x), int(mu), float(cp), float(cr), _p(C))
+    return C
+
+
+def functional_matrix_grad(dims, U) -> np.ndarray:
+    """dR/dRe U + i dR/dIm U = 2 tr(U) 1 per link, shape (V, 4, 3, 3)."""
+    U = _cfield(U)
+    G = np.zeros_like(U)
+    _load().orc_functional_matrix_grad(_p(_dims(dims)), _p(U), _p(G))
+    return G
+
+
+def smear_step_backward(dims, U, Gout, rho: float, eps: float) -> np.ndarray:
+    """Gradient w.r.t. the input of one smearing step, given the gradient
+    Gout (= dL/dRe U' + i dL/dIm U') w.r.t. its output."""
+    U = _cfield(U)
+    Gout = _cfield(Gout)
+    Gin = np.zeros_like(U)
+    _load().orc_smear_step_backward(_p(_dims(dims)), _p(U), _p(Gout), _p(Gin), float(rho), float(eps))
+    return Gin
+
+
+def smear_backward(dims, U, Gout, rho: float, eps: float, nsteps: int) -> np.ndarray:
+    """Gradient w.r.t. U of a loss of smear(U, rho, eps, nsteps), given its
+    gradient Gout w.r.t. the smeared field; the intermediate fields are
+    recomputed (stored) by forward smearing."""
+    fields = [_cfield(U)]
+    for _ in range(nsteps - 1):
+        fields.append(smear(dims, fields[-1], rho, eps, 1))
+    G = _cfield(Gout)
+    for k in range(nsteps - 1, -1, -1):
+        G = smear_step_backward(dims, fields[k], G, rho, eps)
+    return G

@@ -772,4 +772,265 @@ void orc_grad_R(const int* dims, const cplx* U, double* grad) {
     }
 }
 
+
+/* ------------------------------------------------------------------ */
+/* Differentiation through stout / over-improved stout smearing         */
+/* ------------------------------------------------------------------ */
+
+/* n x n complex matrix exponential (Taylor + scaling and squaring), used on
+ * the 6x6 block matrix of the Frechet identity below. */
+static void expm_n(int n, const cplx* X, cplx* E) {
+    double nrm = 0;
+    for (int k = 0; k < n * n; ++k) nrm += creal(X[k] * conj(X[k]));
+    nrm = sqrt(nrm);
+    int s = 0;
+    while (nrm > 0.25) {
+        nrm *= 0.5;
+        ++s;
+    }
+    double sc = ldexp(1.0, -s);
+    cplx Y[36], term[36], t2[36];
+    for (int k = 0; k < n * n; ++k) Y[k] = X[k] * sc;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) E[n * i + j] = term[n * i + j] = (i == j) ? 1.0 : 0.0;
+    for (int m = 1; m < 60; ++m) {
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                cplx acc = 0;
+                for (int k = 0; k < n; ++k) acc += term[n * i + k] * Y[n * k + j];
+                t2[n * i + j] = acc / (double)m;
+            }
+        double tn = 0;
+        for (int k = 0; k < n * n; ++k) {
+            term[k] = t2[k];
+            E[k] += term[k];
+            tn += creal(term[k] * conj(term[k]));
+        }
+        if (sqrt(tn) < 1e-18) break;
+    }
+    for (int r = 0; r < s; ++r) {
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                cplx acc = 0;
+                for (int k = 0; k < n; ++k) acc += E[n * i + k] * E[n * k + j];
+                t2[n * i + j] = acc;
+            }
+        for (int k = 0; k < n * n; ++k) E[k] = t2[k];
+    }
+}
+
+/* Frechet derivative of exp at X in direction A, L(X, A) = d/dt exp(X + tA)
+ * at t = 0, as the upper-right block of exp([[X, A], [0, X]]) (the block
+ * triangular identity of Van Loan 1978 / Mathias 1996). */
+void orc_expm_frechet(const cplx* X, const cplx* A, cplx* L) {
+    cplx M[36], E[36];
+    for (int k = 0; k < 36; ++k) M[k] = 0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            M[6 * i + j] = X[3 * i + j];
+            M[6 * (i + 3) + (j + 3)] = X[3 * i + j];
+            M[6 * i + (j + 3)] = A[3 * i + j];
+        }
+    expm_n(6, M, E);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) L[3 * i + j] = E[6 * i + (j + 3)];
+}
+
+/* One staple as a path of links from x to x+mu: factor k is U_dir(site) or
+ * its dagger. */
+typedef struct {
+    int n;
+    long site[5];
+    int dir[5];
+    int dag[5];
+    double w;
+} staple_path;
+
+static int add_path(staple_path* P, int np, double w, int n, const long* site, const int* dir, const int* dag) {
+    P[np].n = n;
+    P[np].w = w;
+    for (int k = 0; k < n; ++k) {
+        P[np].site[k] = site[k];
+        P[np].dir[k] = dir[k];
+        P[np].dag[k] = dag[k];
+    }
+    return np + 1;
+}
+
+/* The staples of U_mu(x) entering the smearing step, as paths with their
+ * weights: per nu != mu two plaquette staples (weight cp) and, if cr != 0,
+ * six rectangle staples (weight cr), the same set as staple_sum(). */
+static int staple_paths(const geom* g, long x, int mu, double cp, double cr, staple_path* P) {
+    int np = 0;
+    long xpm = shift(g, x, mu, 1), xmm = shift(g, x, mu, -1);
+    for (int nu = 0; nu < 4; ++nu) {
+        if (nu == mu) continue;
+        long xpn = shift(g, x, nu, 1), xmn = shift(g, x, nu, -1);
+        long xmn_pm = shift(g, xmn, mu, 1);
+        {
+            long s[3] = {x, xpn, xpm};
+            int d[3] = {nu, mu, nu}, h[3] = {0, 0, 1};
+            np = add_path(P, np, cp, 3, s, d, h);
+        }
+        {
+            long s[3] = {xmn, xmn, xmn_pm};
+            int d[3] = {nu, mu, nu}, h[3] = {1, 0, 0};
+            np = add_path(P, np, cp, 3, s, d, h);
+        }
+        if (cr == 0) continue;
+        long xp2n = shift(g, xpn, nu, 1), xm2n = shift(g, xmn, nu, -1);
+        long xp2m = shift(g, xpm, mu, 1);
+        {   /* 1x2 up */
+            long s[5] = {x, xpn, xp2n, shift(g, xpm, nu, 1), xpm};
+            int d[5] = {nu, nu, mu, nu, nu}, h[5] = {0, 0, 0, 1, 1};
+            np = add_path(P, np, cr, 5, s, d, h);
+        }
+        {   /* 1x2 down */
+            long s[5] = {xmn, xm2n, xm2n, shift(g, xm2n, mu, 1), xmn_pm};
+            int d[5] = {nu, nu, mu, nu, nu}, h[5] = {1, 1, 0, 0, 0};
+            np = add_path(P, np, cr, 5, s, d, h);
+        }
+        {   /* 2x1 forward up */
+            long s[5] = {x, xpn, shift(g, xpn, mu, 1), xp2m, xpm};
+            int d[5] = {nu, mu, mu, nu, mu}, h[5] = {0, 0, 0, 1, 1};
+            np = add_path(P, np, cr, 5, s, d, h);
+        }
+        {   /* 2x1 forward down */
+            long s[5] = {xmn, xmn, xmn_pm, shift(g, xmn_pm, mu, 1), xpm};
+            int d[5] = {nu, mu, mu, nu, mu}, h[5] = {1, 0, 0, 0, 1};
+            np = add_path(P, np, cr, 5, s, d, h);
+        }
+        {   /* 2x1 backward up */
+            long s[5] = {xmm, xmm, shift(g, xmm, nu, 1), xpn, xpm};
+            int d[5] = {mu, nu, mu, mu, nu}, h[5] = {1, 0, 0, 0, 1};
+            np = add_path(P, np, cr, 5, s, d, h);
+        }
+        {   /* 2x1 backward down */
+            long xmm_mn = shift(g, xmm, nu, -1);
+            long s[5] = {xmm, xmm_mn, xmm_mn, xmn, xmn_pm};
+            int d[5] = {mu, nu, mu, mu, nu}, h[5] = {1, 1, 0, 0, 0};
+            np = add_path(P, np, cr, 5, s, d, h);
+        }
+    }
+    return np;
+}
+
+static void factor(const cplx* U, const staple_path* p, int k, cplx* out) {
+    const cplx* m = clink(U, p->site[k], p->dir[k]);
+    if (p->dag[k])
+        m_dag(out, m);
+    else
+        memcpy(out, m, 9 * sizeof(cplx));
+}
+
+/* Staple sum rebuilt from the path list (for checking staple_paths against
+ * staple_sum). */
+void orc_staple_sum_paths(const int* dims, const cplx* U, long x, int mu, double cp, double cr, cplx* C) {
+    geom g = make_geom(dims);
+    staple_path P[24];
+    int np = staple_paths(&g, x, mu, cp, cr, P);
+    for (int k = 0; k < 9; ++k) C[k] = 0;
+    for (int s = 0; s < np; ++s) {
+        cplx W[9], f[9];
+        factor(U, &P[s], 0, W);
+        for (int k = 1; k < P[s].n; ++k) {
+            factor(U, &P[s], k, f);
+            m_mul(W, W, f);
+        }
+        for (int k = 0; k < 9; ++k) C[k] += P[s].w * W[k];
+    }
+}
+
+void orc_staple_sum(const int* dims, const cplx* U, long x, int mu, double cp, double cr, cplx* C) {
+    geom g = make_geom(dims);
+    staple_sum(&g, U, x, mu, cp, cr, C);
+}
+
+/*
+ * Reverse-mode derivative of one smearing step U' = exp(iQ(U)) U.
+ * Gout holds the matrix gradient of a real loss with respect to U'
+ * (Gout = dL/dRe U' + i dL/dIm U', so that dL = Re tr(Gout^dag dU')); Gin
+ * receives the gradient with respect to U.  Chain rule, per link:
+ *   direct:     Gin += exp(iQ)^dag Gout
+ *   exp:        B = L(iQ, U Gout^dag)  (Frechet adjoint: tr(A L(X,E)) = tr(L(X,A) E))
+ *   projection: K = (B - B^dag)/2 - tr((B - B^dag)/2)/3   (from Q's definition)
+ *   Omega = C U^dag:  Gin += K C,  and Re tr(rho U^dag K dS) is scattered
+ *               over every factor of every staple of the link.
+ */
+void orc_smear_step_backward(const int* dims, const cplx* U, const cplx* Gout, cplx* Gin, double rho, double eps) {
+    geom g = make_geom(dims);
+    const double cp = (5.0 - 2.0 * eps) / 3.0, cr = -(1.0 - eps) / 12.0;
+    long nl = g.vol * 4;
+    for (long l = 0; l < nl * 9; ++l) Gin[l] = 0;
+    for (long x = 0; x < g.vol; ++x)
+        for (int mu = 0; mu < 4; ++mu) {
+            const cplx* u = clink(U, x, mu);
+            const cplx* go = Gout + (x * 4 + mu) * 9;
+            cplx C[9], Om[9], Q[9], X[9], E[9], t[9], B[9], K[9], Y[9];
+            staple_sum(&g, U, x, mu, cp, cr, C);
+            for (int k = 0; k < 9; ++k) C[k] *= rho;
+            m_mul_nd(Om, C, u);
+            cplx tr = 0;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    cplx d = conj(Om[3 * j + i]) - Om[3 * i + j];
+                    Q[3 * i + j] = 0.5 * I * d;
+                    if (i == j) tr += d;
+                }
+            for (int i = 0; i < 3; ++i) Q[4 * i] -= (I / 6.0) * tr;
+            for (int k = 0; k < 9; ++k) X[k] = I * Q[k];
+            orc_expm(X, E);
+            cplx* gi = Gin + (x * 4 + mu) * 9;
+            m_mul_dn(t, E, go); /* E^dag Gout */
+            for (int k = 0; k < 9; ++k) gi[k] += t[k];
+            m_mul_nd(t, u, go); /* U Gout^dag */
+            orc_expm_frechet(X, t, B);
+            cplx trk = 0;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    K[3 * i + j] = 0.5 * (B[3 * i + j] - conj(B[3 * j + i]));
+                    if (i == j) trk += K[3 * i + j];
+                }
+            for (int i = 0; i < 3; ++i) K[4 * i] -= trk / 3.0;
+            m_mul(t, K, C); /* K C */
+            for (int k = 0; k < 9; ++k) gi[k] += t[k];
+            m_mul_dn(Y, u, K); /* U^dag K */
+            for (int k = 0; k < 9; ++k) Y[k] *= rho;
+            staple_path P[24];
+            int np = staple_paths(&g, x, mu, cp, cr, P);
+            for (int s = 0; s < np; ++s) {
+                int n = P[s].n;
+                cplx F[5][9];
+                for (int k = 0; k < n; ++k) factor(U, &P[s], k, F[k]);
+                for (int j = 0; j < n; ++j) {
+                    /* Z = A_{j+1} ... A_n (w Y) A_1 ... A_{j-1} */
+                    cplx Z[9];
+                    m_set_identity(Z);
+                    for (int k = j + 1; k < n; ++k) m_mul(Z, Z, F[k]);
+                    m_mul(Z, Z, Y);
+                    for (int k = 0; k < j; ++k) m_mul(Z, Z, F[k]);
+                    for (int k = 0; k < 9; ++k) Z[k] *= P[s].w;
+                    cplx* gt = Gin + (P[s].site[j] * 4 + P[s].dir[j]) * 9;
+                    if (P[s].dag[j]) {
+                        for (int k = 0; k < 9; ++k) gt[k] += Z[k];
+                    } else {
+                        cplx Zd[9];
+                        m_dag(Zd, Z);
+                        for (int k = 0; k < 9; ++k) gt[k] += Zd[k];
+                    }
+                }
+            }
+        }
+}
+
+/* Matrix gradient of R = sum |tr U|^2: G = 2 tr(U) 1 per link. */
+void orc_functional_matrix_grad(const int* dims, const cplx* U, cplx* G) {
+    geom g = make_geom(dims);
+    for (long l = 0; l < g.vol * 4; ++l) {
+        cplx t = m_trace(U + l * 9);
+        for (int k = 0; k < 9; ++k) G[l * 9 + k] = 0;
+        G[l * 9 + 0] = G[l * 9 + 4] = G[l * 9 + 8] = 2.0 * t;
+    }
+}
+
 int orc_version(void) { return 1; }

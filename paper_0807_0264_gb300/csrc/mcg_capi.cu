@@ -699,4 +699,43 @@ int mcg_gribov_search(const mcg_field* copies, int ncopies, const int* config_of
     return st;
 }
 
+int mcg_smear_backward_step(const void* U, const double* Gout, double* Gin, const mcg_lattice* lat, double rho,
+                            double eps, cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if (lat->precision != MCG_F64) return fail(MCG_BAD_ARG, "the smearing backward runs on FP64 fields");
+    if (!U || !Gout || !Gin) return fail(MCG_BAD_ARG, "null pointer");
+    if (!(std::isfinite(rho) && std::isfinite(eps))) return fail(MCG_BAD_ARG, "rho/eps not finite");
+    const size_t bytes = 16 * link_elems(g) * lat->nfields;
+    if (overlap(Gin, bytes, Gout, bytes) || overlap(Gin, bytes, U, bytes))
+        return fail(MCG_BAD_ARG, "Gin overlaps U or Gout");
+    return run_smear_step_backward(U, Gout, Gin, g, lat->nfields, rho, eps, stream);
+}
+
+int mcg_functional_matrix_grad(const void* U, double* G, const mcg_lattice* lat, cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if (!U || !G) return fail(MCG_BAD_ARG, "null pointer");
+    return run_functional_matrix_grad(U, lat->precision, G, g, lat->nfields, stream);
+}
+
+int mcg_grad_R(const void* U, double* grad, const mcg_lattice* lat, cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if (!U || !grad) return fail(MCG_BAD_ARG, "null pointer");
+    return run_grad_R(U, lat->precision, grad, g, lat->nfields, stream);
+}
+
+int mcg_ascent_step(void* U, void* G, const double* grad, double alpha, const mcg_lattice* lat, cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if (!U || !G || !grad) return fail(MCG_BAD_ARG, "null pointer");
+    if (!std::isfinite(alpha)) return fail(MCG_BAD_ARG, "alpha not finite");
+    return run_ascent_step(U, G, grad, alpha, lat->precision, g, lat->nfields, stream);
+}
+
 }  // extern "C"

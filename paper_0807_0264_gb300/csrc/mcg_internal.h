@@ -113,4 +113,12 @@ int launch_handoff(const void* W32, double* U64, double* G64, const Geom& g, int
 int run_smear(const void* Uin, void* Uout, int prec, const Geom& g, int nfields, double rho, double eps, int n,
               cudaStream_t st);
 
+// ---- differentiation (mcg_smear.cu) -----------------------------------------
+int run_smear_step_backward(const void* U, const double* Gout, double* Gin, const Geom& g, int nfields, double rho,
+                            double eps, cudaStream_t st);
+int run_functional_matrix_grad(const void* U, int prec, double* G, const Geom& g, int nfields, cudaStream_t st);
+int run_grad_R(const void* U, int prec, double* grad, const Geom& g, int nfields, cudaStream_t st);
+int run_ascent_step(void* U, void* G, const double* grad, double alpha, int prec, const Geom& g, int nfields,
+                    cudaStream_t st);
+
 }  // namespace mcg

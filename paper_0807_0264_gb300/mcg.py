@@ -92,6 +92,10 @@ def _load() -> ctypes.CDLL:
         "mcg_kernel_launches": ([], ctypes.c_longlong),
         "mcg_plaquette_static": ([P, P, L, P], I),
         "mcg_set_sweep_block": ([I, I], I),
+        "mcg_smear_backward_step": ([P, P, P, L, D, D, P], I),
+        "mcg_functional_matrix_grad": ([P, P, L, P], I),
+        "mcg_grad_R": ([P, P, L, P], I),
+        "mcg_ascent_step": ([P, P, P, D, L, P], I),
         "mcg_fix_batch": ([ctypes.POINTER(mcg_field), I, I, PR, P, P, P], I),
         "mcg_gribov_search": ([ctypes.POINTER(mcg_field), I, ctypes.POINTER(ctypes.c_int), I, I, PR, P, P, P, P, P],
                               I),
@@ -112,7 +116,8 @@ EXPORTS = ("mcg_version", "mcg_last_error", "mcg_release", "mcg_pack_links", "mc
            "mcg_functional", "mcg_apply_gauge", "mcg_reunitarise", "mcg_smear", "mcg_fix", "mcg_center_project",
            "mcg_precondition_fix", "mcg_precondition_levels", "mcg_time_halfsweep", "mcg_kernel_launches",
            "mcg_plaquette_static", "mcg_set_sweep_block", "mcg_get_sweep_block", "mcg_fix_batch",
-           "mcg_gribov_search")
+           "mcg_gribov_search", "mcg_smear_backward_step", "mcg_functional_matrix_grad", "mcg_grad_R",
+           "mcg_ascent_step")
 
 
 def library() -> ctypes.CDLL:
@@ -528,3 +533,110 @@ def autotune_schedule(Us, dims_list, params: Params, trial_sweeps: int = 40,
     params.check_every = best[2]
     return {"precision": "f32" if prec == F32 else "f64", "block": best[1], "check_every": best[2],
             "ms_per_sweep": timings}
+
+
+# ---------------------------------------------------------------------------
+# differentiation
+# ---------------------------------------------------------------------------
+def mcg_smear_backward_step(U: torch.Tensor, Gout: torch.Tensor, dims, rho: float, eps: float,
+                            stream=None) -> torch.Tensor:
+    """Gradient w.r.t. the input U of one smearing step, given the gradient
+    Gout w.r.t. its output (FP64, link layout)."""
+    _need_cuda(U, Gout)
+    if U.dtype != torch.float64 or Gout.dtype != torch.float64:
+        raise TypeError("the smearing backward runs on FP64 fields and gradients")
+    Gin = torch.empty_like(Gout)
+    _check("mcg_smear_backward_step",
+           _lib.mcg_smear_backward_step(_ptr(U), _ptr(Gout), _ptr(Gin), lattice(dims, U.shape[0], F64), float(rho),
+                                        float(eps), _stream(stream)))
+    return Gin
+
+
+def mcg_functional_matrix_grad(U: torch.Tensor, dims, stream=None) -> torch.Tensor:
+    _need_cuda(U)
+    G = torch.empty(U.shape, dtype=torch.float64, device=U.device)
+    _check("mcg_functional_matrix_grad",
+           _lib.mcg_functional_matrix_grad(_ptr(U), _ptr(G), lattice(dims, U.shape[0], precision_of(U)),
+                                           _stream(stream)))
+    return G
+
+
+def mcg_grad_R(U: torch.Tensor, dims, stream=None) -> torch.Tensor:
+    """dR/d eps_a(x) for Omega(x) -> exp(i eps lambda_a/2) Omega(x): (nfields, V, 8) FP64."""
+    _need_cuda(U)
+    nf = U.shape[0]
+    grad = torch.empty((nf, 2 * vh_of(dims), 8), dtype=torch.float64, device=U.device)
+    _check("mcg_grad_R", _lib.mcg_grad_R(_ptr(U), _ptr(grad), lattice(dims, nf, precision_of(U)), _stream(stream)))
+    return grad
+
+
+def mcg_ascent_step(U: torch.Tensor, G: torch.Tensor, grad: torch.Tensor, dims, alpha: float, stream=None):
+    _need_cuda(U, G, grad)
+    _check("mcg_ascent_step", _lib.mcg_ascent_step(_ptr(U), _ptr(G), _ptr(grad), float(alpha),
+                                                   lattice(dims, U.shape[0], precision_of(U)), _stream(stream)))
+    return U, G
+
+
+class StoutSmear(torch.autograd.Function):
+    """U -> smear(U, rho, eps, n) with the hand-written backward: the n
+    intermediate fields are kept (full checkpointing) and the steps are
+    differentiated in reverse by mcg_smear_backward_step.  FP64 only."""
+
+    @staticmethod
+    def forward(ctx, U, dims, rho, eps, n):
+        fields = [U]
+        for _ in range(int(n)):
+            fields.append(mcg_smear(fields[-1], dims, rho, eps, 1))
+        ctx.save_for_backward(*fields[:-1])
+        ctx.params = (tuple(dims), float(rho), float(eps))
+        return fields[-1] if n > 0 else U.clone()
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        dims, rho, eps = ctx.params
+        G = grad_out.contiguous().to(torch.float64)
+        for Uk in reversed(ctx.saved_tensors):
+            G = mcg_smear_backward_step(Uk, G, dims, rho, eps)
+        return G, None, None, None, None
+
+
+class MCGFunctional(torch.autograd.Function):
+    """R(U) = sum |tr U_mu(x)|^2 per field with its matrix-gradient backward."""
+
+    @staticmethod
+    def forward(ctx, U, dims):
+        ctx.save_for_backward(U)
+        ctx.dims = tuple(dims)
+        return torch.tensor(mcg_functional(U, dims), dtype=torch.float64, device=U.device)
+
+    @staticmethod
+    def backward(ctx, gR):
+        (U,) = ctx.saved_tensors
+        G = mcg_functional_matrix_grad(U, ctx.dims)
+        return G * gR.view(-1, *([1] * (G.dim() - 1))), None
+
+
+def ascent_refine(U: torch.Tensor, G: torch.Tensor, dims, steps: int = 20, alpha: float = 0.05,
+                  min_alpha: float = 1e-8) -> dict:
+    """Gradient-ascent refinement of the MCG functional over the gauge
+    transform (in place on U, G): each step moves along dR/d eps with step
+    alpha, halving alpha whenever R would fall (the trial runs on clones)."""
+    R = mcg_functional(U, dims)[0]
+    hist = [R]
+    for _ in range(int(steps)):
+        grad = mcg_grad_R(U, dims)
+        while alpha >= min_alpha:
+            Ut, Gt = U.clone(), G.clone()
+            mcg_ascent_step(Ut, Gt, grad, dims, alpha)
+            Rt = mcg_functional(Ut, dims)[0]
+            if Rt >= R:
+                U.copy_(Ut)
+                G.copy_(Gt)
+                R = Rt
+                hist.append(R)
+                alpha *= 1.5
+                break
+            alpha *= 0.5
+        else:
+            break
+    return {"R": R, "R_hist": hist, "alpha": alpha}

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def header_functions():
     src = open(os.path.join(ROOT, "include", "mcg.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(mcg_[a-z0-9_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(mcg_[A-Za-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -31,7 +31,7 @@ def test_library_exports_every_declared_symbol(mcg):
     for name in declared:
         assert hasattr(lib, name), name
     out = subprocess.run(["nm", "-D", "--defined-only", mcg.library_path()], capture_output=True, text=True).stdout
-    exported = set(re.findall(r"\bT (mcg_[a-z0-9_]+)$", out, flags=re.M))
+    exported = set(re.findall(r"\bT (mcg_[A-Za-z0-9_]+)$", out, flags=re.M))
     assert set(declared) <= exported
     assert set(mcg.EXPORTS) == set(declared)
 
