@@ -184,8 +184,9 @@ int mcg_smear(const void* U_in, void* U_out, const mcg_lattice* lat, double rho,
  * fresh, or a random transform for a Gribov copy).  Per field, stops at the
  * first sweep with dV_U < params->tol, or at params->max_sweeps.
  * With lat->precision = MCG_F64 and params->fp32_sweeps > 0 the early sweeps
- * run in FP32 (links and the transform of this call in FP32, R accumulated in
- * FP64); the FP32 transform is then re-unitarised in FP64 and applied to the
+ * run in FP32 (links and the transform of this call in FP32, stored as rows 0
+ * and 1 with row 2 implied by unitarity, R accumulated in FP64); the FP32
+ * transform is then re-unitarised in FP64 and applied to the
  * FP64 links, which keeps them on the gauge orbit, and FP64 sweeps finish.
  * R_out (host, nfields, may be NULL): R after the last sweep.
  * sweeps_out (host, nfields, may be NULL): sweeps performed (FP32 + FP64).
@@ -304,7 +305,10 @@ int mcg_ascent_step(void* U, void* G, const double* grad, double alpha, const mc
  * parity 1: odd sites with the fused R reduction) on one field, over nreps
  * launches each bracketed by CUDA events on `stream`; with flush_l2 != 0 a
  * 256 MB buffer is overwritten between launches, outside the timed interval,
- * so every launch reads its links from HBM.  The sweeps are applied to U and G.
+ * so every launch reads its links from HBM.  FP64: the sweeps are applied to
+ * U and G.  FP32: the FP32 kernel works on the library's compact storage
+ * (rows 0 and 1 of each matrix, row 2 implied by unitarity); U and G are
+ * converted to it once, before the timed launches, and left unchanged.
  * ms_out: host float.  Synchronises.  (Instrumentation; not part of the
  * paper's method.) */
 int mcg_time_halfsweep(void* U, void* G, const mcg_lattice* lat, int parity, int nreps, int flush_l2, float* ms_out,
@@ -327,9 +331,8 @@ int mcg_time_halfsweep(void* U, void* G, const mcg_lattice* lat, int parity, int
  */
 int mcg_plaquette_static(const void* U, double* out, const mcg_lattice* lat, cudaStream_t stream);
 
-/* Threads per block of the half-sweep kernel for one precision: FP64 runs one
- * thread per site (64 or 128), FP32 two threads per site (64, 128 or 256);
- * 128 by default.  A process-wide tuning setting (not part of the paper's
+/* Threads per block of the half-sweep kernel for one precision, one thread
+ * per site: FP64 64 or 128, FP32 64, 128 or 256; 128 by default.  A process-wide tuning setting (not part of the paper's
  * method): Python's autotune_sweep_block() times the choices with
  * mcg_time_halfsweep and keeps the fastest.  Returns MCG_BAD_ARG otherwise. */
 int mcg_set_sweep_block(int precision, int threads);

@@ -213,29 +213,39 @@ static int fix_fields(const std::vector<FieldSpec>& fs, int prec, const mcg_para
     std::vector<int> s32(nf, 0);
     bool fresh = true;
 
-    if (prec == MCG_F64 && prm->fp32_sweeps > 0) {
-        // FP32 phase on copies of the links and on the transform of this call
-        size_t le_tot = 0, ge_tot = 0;
+    // FP32 sweeps run on compact working copies (rows 0 and 1 of each matrix)
+    auto compact_copies = [&](std::vector<FieldDesc>& fds, int* rcp) {
+        size_t lo_tot = 0, go_tot = 0;
         for (const auto& f : fs) {
-            le_tot += link_elems(f.g);
-            ge_tot += gauge_elems(f.g);
+            lo_tot += c12_link_chunks(f.g);
+            go_tot += c12_gauge_chunks(f.g);
         }
-        char* U32 = (char*)scratch_device("fix.U32", 8 * le_tot, &rc);
-        if (rc) return rc;
-        char* W32 = (char*)scratch_device("fix.W32", 8 * ge_tot, &rc);
-        if (rc) return rc;
-        std::vector<FieldDesc> fds(nf);
+        char* U12 = (char*)scratch_device("fix.U12", 16 * lo_tot, rcp);
+        if (*rcp) return;
+        char* W12 = (char*)scratch_device("fix.W12", 16 * go_tot, rcp);
+        if (*rcp) return;
+        fds.resize(nf);
         size_t lo = 0, go = 0;
         for (int f = 0; f < nf; ++f) {
             const Geom& g = fs[f].g;
-            fds[f].U = U32 + 8 * lo;
-            fds[f].G = W32 + 8 * go;
+            fds[f].U = U12 + 16 * lo;
+            fds[f].G = W12 + 16 * go;
             fds[f].geo = g;
             fds[f].norm = 1.0 / (9.0 * 8.0 * g.vh);
-            if ((rc = launch_convert(fs[f].U, MCG_F64, fds[f].U, MCG_F32, link_elems(g), st))) return rc;
-            if ((rc = launch_identity_gauge(fds[f].G, MCG_F32, g, 1, st))) return rc;
-            lo += link_elems(g);
-            go += gauge_elems(g);
+            lo += c12_link_chunks(g);
+            go += c12_gauge_chunks(g);
+        }
+    };
+
+    if (prec == MCG_F64 && prm->fp32_sweeps > 0) {
+        // FP32 phase on compact copies of the links and on the transform W of
+        // this call (starting from the identity)
+        std::vector<FieldDesc> fds;
+        compact_copies(fds, &rc);
+        if (rc) return rc;
+        for (int f = 0; f < nf; ++f) {
+            if ((rc = launch_to_c12(fs[f].U, MCG_F64, fds[f].U, fs[f].g, 4, 1, st))) return rc;
+            if ((rc = launch_identity_c12(fds[f].G, fs[f].g, 1, st))) return rc;
         }
         const int cap = std::min(prm->fp32_sweeps, prm->max_sweeps);
         rc = run_fix_phase<float>(fds, d_state, h_state, d_hist, hist_len, prm->fp32_tol, prm->fp32_window,
@@ -247,19 +257,33 @@ static int fix_fields(const std::vector<FieldSpec>& fs, int prec, const mcg_para
             if ((rc = launch_handoff(fds[f].G, (double*)fs[f].U, (double*)fs[f].G, fs[f].g, 1, st))) return rc;
         fresh = false;
     }
-    std::vector<FieldDesc> fds(nf);
-    for (int f = 0; f < nf; ++f) {
-        fds[f].U = fs[f].U;
-        fds[f].G = fs[f].G;
-        fds[f].geo = fs[f].g;
-        fds[f].norm = 1.0 / (9.0 * 8.0 * fs[f].g.vh);
-    }
-    if (prec == MCG_F64)
+    if (prec == MCG_F64) {
+        std::vector<FieldDesc> fds(nf);
+        for (int f = 0; f < nf; ++f) {
+            fds[f].U = fs[f].U;
+            fds[f].G = fs[f].G;
+            fds[f].geo = fs[f].g;
+            fds[f].norm = 1.0 / (9.0 * 8.0 * fs[f].g.vh);
+        }
         rc = run_fix_phase<double>(fds, d_state, h_state, d_hist, hist_len, prm->tol, 1, 1.0, prm->reunit_every,
                                    prm->max_sweeps, prm->check_every, fresh, st);
-    else
+    } else {
+        // FP32 fields: compact copies in, full layout (row 2 rebuilt) out
+        std::vector<FieldDesc> fds;
+        compact_copies(fds, &rc);
+        if (rc) return rc;
+        for (int f = 0; f < nf; ++f) {
+            if ((rc = launch_to_c12(fs[f].U, MCG_F32, fds[f].U, fs[f].g, 4, 1, st))) return rc;
+            if ((rc = launch_to_c12(fs[f].G, MCG_F32, fds[f].G, fs[f].g, 1, 1, st))) return rc;
+        }
         rc = run_fix_phase<float>(fds, d_state, h_state, d_hist, hist_len, prm->tol, 1, 1.0, 0, prm->max_sweeps,
                                   prm->check_every, fresh, st);
+        if (rc) return rc;
+        for (int f = 0; f < nf; ++f) {
+            if ((rc = launch_from_c12(fds[f].U, fs[f].U, fs[f].g, 4, 1, st))) return rc;
+            if ((rc = launch_from_c12(fds[f].G, fs[f].G, fs[f].g, 1, 1, st))) return rc;
+        }
+    }
     if (rc) return rc;
     bool all = true;
     for (int f = 0; f < nf; ++f) {
@@ -547,7 +571,15 @@ int mcg_time_halfsweep(void* U, void* G, const mcg_lattice* lat, int parity, int
     if (lat->nfields != 1) return fail(MCG_BAD_ARG, "mcg_time_halfsweep takes one field");
     if (nreps < 1 || (parity != 0 && parity != 1)) return fail(MCG_BAD_ARG, "nreps >= 1, parity 0 or 1");
     if (lat->precision == MCG_F64) return time_halfsweep<double>(U, G, g, parity, nreps, flush_l2, ms_out, stream);
-    return time_halfsweep<float>(U, G, g, parity, nreps, flush_l2, ms_out, stream);
+    // FP32: the kernel runs on the compact working storage; time it on
+    // compact copies of U and G (the caller's arrays are left unchanged)
+    void* U12 = scratch_device("time.U12", 16 * c12_link_chunks(g), &rc);
+    if (rc) return rc;
+    void* W12 = scratch_device("time.W12", 16 * c12_gauge_chunks(g), &rc);
+    if (rc) return rc;
+    if ((rc = launch_to_c12(U, MCG_F32, U12, g, 4, 1, stream))) return rc;
+    if ((rc = launch_to_c12(G, MCG_F32, W12, g, 1, 1, stream))) return rc;
+    return time_halfsweep<float>(U12, W12, g, parity, nreps, flush_l2, ms_out, stream);
 }
 
 int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_out, const mcg_lattice* lat,

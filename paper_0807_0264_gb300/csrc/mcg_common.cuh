@@ -270,6 +270,79 @@ __device__ __forceinline__ void store_link(cplx<T>* __restrict__ U, const Geom& 
 }
 
 // ---------------------------------------------------------------------------
+// Compact FP32 working storage (the FP32 sweep phase): rows 0 and 1 of each
+// SU(3) matrix, 12 reals; row 2 is implied, row2 = conj(row0 x row1).  A
+// matrix is three float4 chunks, chunk q holding entries 2q and 2q+1 of
+// (M00 M01 M02 M10 M11 M12):
+//   link U_mu, chunk q:  C[((mu*2 + p)*3 + q)*Vh + s]
+//   gauge W, chunk q:    C[(p*3 + q)*Vh + s]
+// so one chunk of 32 consecutive sites is one 512-byte coalesced access.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ size_t c12_link_chunks(const Geom& g) { return (size_t)24 * g.vh; }
+__host__ __device__ __forceinline__ size_t c12_gauge_chunks(const Geom& g) { return (size_t)6 * g.vh; }
+__device__ __forceinline__ size_t c12_lidx(const Geom& g, int mu, int p, int q, int s) {
+    return ((size_t)((mu * 2 + p) * 3 + q)) * g.vh + s;
+}
+__device__ __forceinline__ size_t c12_gidx(const Geom& g, int p, int q, int s) {
+    return ((size_t)(p * 3 + q)) * g.vh + s;
+}
+
+// entry (2, k) of an SU(3) matrix from its first two rows: the complex
+// conjugate of the cofactor, conj(M0i M1j - M0j M1i) with (i, j) = (k+1, k+2)
+// mod 3.  m holds rows 0 and 1 row-major (m[3*row + col]).
+template <typename T>
+__device__ __forceinline__ cplx<T> row2_entry(const cplx<T>* m, int k) {
+    const int i = (k + 1) % 3, j = (k + 2) % 3;
+    cplx<T> c = cmul(m[i], m[3 + j]);
+    c.x = fma(-m[j].x, m[3 + i].x, c.x);
+    c.x = fma(m[j].y, m[3 + i].y, c.x);
+    c.y = fma(-m[j].x, m[3 + i].y, c.y);
+    c.y = fma(-m[j].y, m[3 + i].x, c.y);
+    return mk(c.x, -c.y);
+}
+
+__device__ __forceinline__ void c12_load(const float4* __restrict__ src, size_t stride, cplx<float>* m) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float4 v = src[q * stride];
+        m[2 * q] = mk(v.x, v.y);
+        m[2 * q + 1] = mk(v.z, v.w);
+    }
+}
+__device__ __forceinline__ void c12_store(float4* __restrict__ dst, size_t stride, const cplx<float>* m) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) dst[q * stride] = make_float4(m[2 * q].x, m[2 * q].y, m[2 * q + 1].x, m[2 * q + 1].y);
+}
+
+// Re-unitarisation in the compact form (same precision): normalise row 0,
+// remove its component from row 1, normalise row 1; row 2 stays implied.
+template <typename T>
+__device__ __forceinline__ void c12_reunitarise(cplx<T>* m) {
+    T n0 = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) n0 = fma(m[k].x, m[k].x, fma(m[k].y, m[k].y, n0));
+    n0 = rsqrt(n0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) m[k] = mk(m[k].x * n0, m[k].y * n0);
+    T px = T(0), py = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        px = fma(m[k].x, m[3 + k].x, fma(m[k].y, m[3 + k].y, px));
+        py = fma(m[k].x, m[3 + k].y, fma(-m[k].y, m[3 + k].x, py));
+    }
+    T n1 = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        m[3 + k].x = fma(-px, m[k].x, fma(py, m[k].y, m[3 + k].x));
+        m[3 + k].y = fma(-px, m[k].y, fma(-py, m[k].x, m[3 + k].y));
+        n1 = fma(m[3 + k].x, m[3 + k].x, fma(m[3 + k].y, m[3 + k].y, n1));
+    }
+    n1 = rsqrt(n1);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) m[3 + k] = mk(m[3 + k].x * n1, m[3 + k].y * n1);
+}
+
+// ---------------------------------------------------------------------------
 // asynchronous global -> shared copies (cp.async, no register staging)
 // ---------------------------------------------------------------------------
 template <int BYTES>

@@ -205,9 +205,10 @@ __global__ void __launch_bounds__(FT) k_reunit_all(cplx<T>* __restrict__ M, int 
     }
 }
 
-// Mixed-precision hand-off, pass 1: W64 = reunit(W32) written to scratch,
-// G64 <- reunit(W64 G64).
-__global__ void __launch_bounds__(FT) k_handoff_gauge(const cplx<float>* __restrict__ W, cplx<double>* __restrict__ W64,
+// Mixed-precision hand-off, pass 1: W64 = reunit(W) written to scratch (W in
+// the compact FP32 form: rows 0 and 1; the FP64 re-unitarisation rebuilds row
+// 2 from them), G64 <- reunit(W64 G64).
+__global__ void __launch_bounds__(FT) k_handoff_gauge(const float4* __restrict__ W, cplx<double>* __restrict__ W64,
                                                       cplx<double>* __restrict__ G, Geom g, int nfields) {
     const long long n = 2LL * g.vh * nfields;
     const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -216,13 +217,18 @@ __global__ void __launch_bounds__(FT) k_handoff_gauge(const cplx<float>* __restr
     const int r = (int)(id - (long long)f * 2 * g.vh);
     const int p = r / g.vh, s = r - p * g.vh;
     const size_t off = (size_t)f * gauge_elems(g);
+    const float4* Wf = W + (size_t)f * c12_gauge_chunks(g);
     cplx<double> w[9], o[9], t[9];
 #pragma unroll
-    for (int e = 0; e < 9; ++e) {
-        const cplx<float> v = W[off + gidx(g, p, e, s)];
-        w[e] = mk((double)v.x, (double)v.y);
-        o[e] = G[off + gidx(g, p, e, s)];
+    for (int q = 0; q < 3; ++q) {
+        const float4 v = Wf[c12_gidx(g, p, q, s)];
+        w[2 * q] = mk((double)v.x, (double)v.y);
+        w[2 * q + 1] = mk((double)v.z, (double)v.w);
     }
+#pragma unroll
+    for (int e = 6; e < 9; ++e) w[e] = mk(0.0, 0.0);
+#pragma unroll
+    for (int e = 0; e < 9; ++e) o[e] = G[off + gidx(g, p, e, s)];
     m3_reunitarise(w);
     m3_mul(w, o, t);
     m3_reunitarise(t);
@@ -231,6 +237,59 @@ __global__ void __launch_bounds__(FT) k_handoff_gauge(const cplx<float>* __restr
         W64[off + gidx(g, p, e, s)] = w[e];
         G[off + gidx(g, p, e, s)] = t[e];
     }
+}
+
+// Full layout (FP64 or FP32) -> compact FP32 working storage, for `nmat`
+// matrices per site and parity (4: links, 1: gauge transform): rows 0 and 1
+// rounded to FP32.
+template <typename TS>
+__global__ void __launch_bounds__(FT) k_to_c12(const cplx<TS>* __restrict__ src, float4* __restrict__ dst, Geom g,
+                                               int nmat, int nfields) {
+    const long long per_field = 2LL * nmat * g.vh;
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= per_field * nfields) return;
+    const int f = (int)(id / per_field);
+    const int r = (int)(id - (long long)f * per_field);
+    const int mp = r / g.vh, s = r - mp * g.vh;  // mp = matrix * 2 + parity
+    const cplx<TS>* sf = src + (size_t)f * 18 * nmat * g.vh + (size_t)mp * 9 * g.vh + s;
+    float4* df = dst + (size_t)f * 6 * nmat * g.vh + (size_t)mp * 3 * g.vh + s;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const cplx<TS> a = sf[(size_t)(2 * q) * g.vh], b = sf[(size_t)(2 * q + 1) * g.vh];
+        df[(size_t)q * g.vh] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+    }
+}
+
+// Compact FP32 -> full FP32 layout, row 2 rebuilt as conj(row0 x row1).
+__global__ void __launch_bounds__(FT) k_from_c12(const float4* __restrict__ src, cplx<float>* __restrict__ dst,
+                                                 Geom g, int nmat, int nfields) {
+    const long long per_field = 2LL * nmat * g.vh;
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= per_field * nfields) return;
+    const int f = (int)(id / per_field);
+    const int r = (int)(id - (long long)f * per_field);
+    const int mp = r / g.vh, s = r - mp * g.vh;
+    const float4* sf = src + (size_t)f * 6 * nmat * g.vh + (size_t)mp * 3 * g.vh + s;
+    cplx<float>* df = dst + (size_t)f * 18 * nmat * g.vh + (size_t)mp * 9 * g.vh + s;
+    cplx<float> m[6];
+    c12_load(sf, (size_t)g.vh, m);
+#pragma unroll
+    for (int e = 0; e < 6; ++e) df[(size_t)e * g.vh] = m[e];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) df[(size_t)(6 + k) * g.vh] = row2_entry(m, k);
+}
+
+__global__ void __launch_bounds__(FT) k_identity_c12(float4* __restrict__ W, Geom g, int nfields) {
+    const long long n = 2LL * g.vh * nfields;
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n) return;
+    const int f = (int)(id / (2LL * g.vh));
+    const int r = (int)(id - (long long)f * 2 * g.vh);
+    const int p = r / g.vh, s = r - p * g.vh;
+    float4* Wf = W + (size_t)f * c12_gauge_chunks(g);
+    Wf[c12_gidx(g, p, 0, s)] = make_float4(1.f, 0.f, 0.f, 0.f);  // (W00, W01)
+    Wf[c12_gidx(g, p, 1, s)] = make_float4(0.f, 0.f, 0.f, 0.f);  // (W02, W10)
+    Wf[c12_gidx(g, p, 2, s)] = make_float4(1.f, 0.f, 0.f, 0.f);  // (W11, W12)
 }
 
 // ---------------------------------------------------------------------------
@@ -549,10 +608,37 @@ int launch_handoff(const void* W32, double* U64, double* G64, const Geom& g, int
         (cplx<double>*)scratch_device("handoff.W64", sizeof(cplx<double>) * gauge_elems(g) * nfields, &rc);
     if (rc) return rc;
     const long long n = 2LL * g.vh * nfields;
-    k_handoff_gauge<<<blocks_for(n, FT), FT, 0, st>>>((const cplx<float>*)W32, W64, (cplx<double>*)G64, g, nfields);
+    k_handoff_gauge<<<blocks_for(n, FT), FT, 0, st>>>((const float4*)W32, W64, (cplx<double>*)G64, g, nfields);
     k_apply_gauge<double><<<blocks_for(n, FT), FT, 0, st>>>((cplx<double>*)U64, W64, g, nfields);
     MCG_CK(cudaGetLastError());
     note_launches(2);
+    return 0;
+}
+
+int launch_to_c12(const void* src, int src_prec, void* dst, const Geom& g, int nmat, int nfields, cudaStream_t st) {
+    const long long n = 2LL * nmat * g.vh * nfields;
+    if (src_prec == MCG_F64)
+        k_to_c12<double><<<blocks_for(n, FT), FT, 0, st>>>((const cplx<double>*)src, (float4*)dst, g, nmat, nfields);
+    else
+        k_to_c12<float><<<blocks_for(n, FT), FT, 0, st>>>((const cplx<float>*)src, (float4*)dst, g, nmat, nfields);
+    MCG_CK(cudaGetLastError());
+    note_launches(1);
+    return 0;
+}
+
+int launch_from_c12(const void* src, void* dst, const Geom& g, int nmat, int nfields, cudaStream_t st) {
+    const long long n = 2LL * nmat * g.vh * nfields;
+    k_from_c12<<<blocks_for(n, FT), FT, 0, st>>>((const float4*)src, (cplx<float>*)dst, g, nmat, nfields);
+    MCG_CK(cudaGetLastError());
+    note_launches(1);
+    return 0;
+}
+
+int launch_identity_c12(void* W, const Geom& g, int nfields, cudaStream_t st) {
+    const long long n = 2LL * g.vh * nfields;
+    k_identity_c12<<<blocks_for(n, FT), FT, 0, st>>>((float4*)W, g, nfields);
+    MCG_CK(cudaGetLastError());
+    note_launches(1);
     return 0;
 }
 

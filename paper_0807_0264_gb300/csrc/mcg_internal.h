@@ -37,8 +37,8 @@ void release_all();
 
 // ---- batched sweep machinery -------------------------------------------------
 struct FieldDesc {
-    void* U;      // links, precision of the sweep kernel
-    void* G;      // gauge transform, same precision
+    void* U;      // links: FP64 full layout, or FP32 compact (rows 0 and 1)
+    void* G;      // gauge transform, same storage as the links
     Geom geo;
     int blk0;     // first block of this field in the flattened grid
     int nblk;     // blocks of this field
@@ -105,9 +105,15 @@ int compute_plaquette(const void* U, int prec, const Geom& g, int nfields, doubl
 int compute_functional(const void* U, int prec, const Geom& g, int nfields, double* out_host, cudaStream_t st);
 int compute_center(const void* U, int prec, int8_t* Z, const Geom& g, int nfields, long long* counts_host,
                    cudaStream_t st);
-// FP32 transform W (of this call) -> FP64: W64 = reunit(W); U64 <- W64 U64 W64(x+mu)^dag;
-// G64 <- reunit(W64 G64).
+// FP32 transform W of this call (compact form) -> FP64: W64 = reunit(W);
+// U64 <- W64 U64 W64(x+mu)^dag; G64 <- reunit(W64 G64).
 int launch_handoff(const void* W32, double* U64, double* G64, const Geom& g, int nfields, cudaStream_t st);
+// compact FP32 working storage (rows 0 and 1 of each matrix) of the FP32
+// sweep phase: from / to the full layout; nmat = 4 for links, 1 for a gauge
+// transform
+int launch_to_c12(const void* src, int src_prec, void* dst, const Geom& g, int nmat, int nfields, cudaStream_t st);
+int launch_from_c12(const void* src, void* dst, const Geom& g, int nmat, int nfields, cudaStream_t st);
+int launch_identity_c12(void* W, const Geom& g, int nfields, cudaStream_t st);
 
 // ---- smearing (mcg_smear.cu) ------------------------------------------------
 int run_smear(const void* Uin, void* Uout, int prec, const Geom& g, int nfields, double rho, double eps, int n,

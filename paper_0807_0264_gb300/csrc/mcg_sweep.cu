@@ -272,7 +272,11 @@ __device__ __forceinline__ void ldlt4_solve(const T (&L)[4][4], const T (&Dinv)[
 // success (converged, and mu - A positive definite: the global maximum of the
 // trust-region subproblem) returns true with a normalised, mu, and the LDL^T
 // factors of (mu - A) for later use.
-template <typename T>
+// EARLY: also stop once the quadratic rate seen over the last two
+// corrections (e_next ~ e^3 / e_prev^2) puts the next correction below the
+// tolerance (the FP32 sweep; the FP64 path refines from this solution and
+// takes the full iteration).
+template <typename T, bool EARLY = false>
 __device__ __forceinline__ bool kkt_newton(const T (&A)[4][4], const T (&b)[4], T (&a)[4], T& mu, T (&L)[4][4],
                                            T (&Dinv)[4], T& pd) {
     const T conv = sizeof(T) == 8 ? T(1e-13) : T(2e-6);
@@ -280,6 +284,7 @@ __device__ __forceinline__ bool kkt_newton(const T (&A)[4][4], const T (&b)[4], 
     a[1] = a[2] = a[3] = T(0);
     mu = A[0][0] + b[0];
     bool ok = false;
+    T dprev = T(-1);
 #pragma unroll 1
     for (int it = 0; it < 8; ++it) {
         T M[4][4];
@@ -306,10 +311,11 @@ __device__ __forceinline__ bool kkt_newton(const T (&A)[4][4], const T (&b)[4], 
             dmax = fmax(dmax, fabs(da));
         }
         mu += dmu;
-        if (dmax <= conv) {
+        if (dmax <= conv || (EARLY && dprev > T(0) && dmax * dmax * dmax <= conv * dprev * dprev)) {
             ok = true;
             break;
         }
+        dprev = dmax;
     }
     if (!ok) return false;
     const T inv = rsqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
@@ -406,18 +412,6 @@ __device__ __noinline__ void solve_f64_full(const double* Ain, const double* b_i
 
 template <typename T>
 struct Solver;
-
-template <>
-struct Solver<float> {
-    // returns 1 when the Jacobi path was needed (Newton failed or uncertified)
-    __device__ __forceinline__ static int solve(const float (&A)[4][4], const float (&b)[4], float (&a)[4]) {
-        float L[4][4], Dinv[4], mu, pd;
-        if (kkt_newton<float>(A, b, a, mu, L, Dinv, pd)) return 0;
-        float S[4][4], V[4][4];
-        solve_f32(A, b, a, mu, S, V);
-        return 1;
-    }
-};
 
 // FP64 refinement with the FP32 LDL^T factors of (mu32 - A) as the fixed
 // approximate inverse (same iteration as kkt_refine).
@@ -666,22 +660,6 @@ __global__ void __launch_bounds__(NT, 2) k_halfsweep(SweepBatch bt, int parity) 
             fb += subgroup_step<T>(lk, P, Q, 3 - P - Q, omega);
             asm volatile("" ::: "memory");
         }
-        if (sizeof(T) == 4) {
-            // FP32 sweeps re-unitarise in FP32 every sweep (Omega every
-            // half-sweep, the 8 links in the odd one, which touches every link
-            // once): FP32 rounding would otherwise inflate |tr U|^2 by ~1e-6
-            // per sweep and swamp the convergence signal.
-#pragma unroll 1
-            for (int l = ACC ? 0 : 8; l < 9; ++l) {
-                cplx<T> m[9];
-#pragma unroll
-                for (int e = 0; e < 9; ++e) m[e] = lk(l, e);
-                m3_reunitarise_same(m);
-#pragma unroll
-                for (int e = 0; e < 9; ++e) lk(l, e) = m[e];
-            }
-            asm volatile("" ::: "memory");
-        }
 
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) {
@@ -718,188 +696,249 @@ __global__ void __launch_bounds__(NT, 2) k_halfsweep(SweepBatch bt, int parity) 
     }
 }
 
-// Pair-split half-sweep (FP32): the two lanes 2j, 2j+1 of a warp share site j
-// of the block.  Lane h = 0 holds the forward links U_mu(x) and Omega(x), lane
-// h = 1 the backward links U_mu(x - mu).  Each builds its part of (A, b), the
-// pair adds the parts with one shuffle per entry (a + b == b + a exactly, so
-// both lanes hold identical sums), both lanes solve the 4x4 problem (the
-// solve is cheap next to the link traffic) and each updates its own links.
-// Halving the shared memory per thread doubles the resident warps.
-template <typename T, bool ACC, int NT>
-__global__ void __launch_bounds__(NT) k_halfsweep_pair(SweepBatch bt, int parity) {
-    constexpr int SPB = NT / 2;  // sites per block
+// ---------------------------------------------------------------------------
+// FP32 half-sweep on the compact storage: one thread per site, the site's
+// nine matrices (forward links U_mu(x), backward links U_mu(x - mu), W(x)) in
+// registers as their rows 0 and 1 (108 floats), the three subgroup steps
+// unrolled with compile-time indices.  Row-2 entries are rebuilt where a step
+// needs them; G acting on rows (P, 2) of a forward link changes row P only in
+// the stored part (row 2 stays implied), and M G^dag acts on each row of a
+// backward link separately.  No shared memory: the loads of all nine matrices
+// are in flight at once, straight into registers.
+// ---------------------------------------------------------------------------
+
+// FP32 fallback of the local solve (Jacobi + secular), out of line with its
+// arguments and result passed by value so that the caller's A and b stay in
+// registers.
+__device__ __noinline__ float4 solve_f32_fallback(float a00, float a01, float a02, float a03, float a11, float a12,
+                                                  float a13, float a22, float a23, float a33, float b0, float b1,
+                                                  float b2, float b3) {
+    float S[4][4] = {{a00, a01, a02, a03}, {a01, a11, a12, a13}, {a02, a12, a22, a23}, {a03, a13, a23, a33}};
+    const float b[4] = {b0, b1, b2, b3};
+    float V[4][4], a[4], mu;
+    jacobi4<float>(S, V, 8, 5e-7f);
+    trs_from_eigen<float>(S, V, b, a, mu);
+    return make_float4(a[0], a[1], a[2], a[3]);
+}
+
+// Makes the compiler treat the site's links as redefined here (no code
+// emitted): values derived from them before this point (row-2 entries built
+// for A and b) are recomputed after it instead of being held in registers
+// across the local solve.
+__device__ __forceinline__ void c12_opaque(cplx<float> (&m)[8][6]) {
+#pragma unroll
+    for (int l = 0; l < 8; ++l)
+#pragma unroll
+        for (int e = 0; e < 6; ++e) asm volatile("" : "+f"(m[l][e].x), "+f"(m[l][e].y));
+}
+
+template <int I, int J>
+__device__ __forceinline__ cplx<float> c12_entry(const cplx<float>* m) {
+    if constexpr (I < 2)
+        return m[3 * I + J];
+    else
+        return row2_entry(m, J);
+}
+
+// M <- G M for the subgroup element G = a0 + i a.sigma embedded at rows and
+// columns (P, Q), on a compact matrix (rows 0 and 1).  For Q = 2 only row P
+// of the stored part changes; the new row 2 stays implied.
+template <int P, int Q>
+__device__ __forceinline__ void c12_left_update(cplx<float>* m, const float (&a)[4]) {
+    const cplx<float> g11 = mk(a[0], a[3]), g12 = mk(a[2], a[1]), g21 = mk(-a[2], a[1]), g22 = mk(a[0], -a[3]);
+    if constexpr (Q < 2) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const cplx<float> xp = m[3 * P + k], xq = m[3 * Q + k];
+            m[3 * P + k] = cfma(g12, xq, cmul(g11, xp));
+            m[3 * Q + k] = cfma(g22, xq, cmul(g21, xp));
+        }
+    } else {
+        cplx<float> r2[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) r2[k] = row2_entry(m, k);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) m[3 * P + k] = cfma(g12, r2[k], cmul(g11, m[3 * P + k]));
+    }
+}
+
+// One SU(2)-subgroup step (rows/columns P < Q, R the third index) on the
+// compact links m[0..3] (forward U_mu(x)) and m[4..7] (backward U_mu(x-mu)).
+// Writes the (over-relaxed) subgroup element to a_out for the update of W;
+// returns 1 if the local solve left the Newton path.
+template <int P, int Q, int R>
+__device__ __forceinline__ int c12_subgroup_step(cplx<float> (&m)[8][6], const float omega, float (&a)[4]) {
+    float A[4][4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        b[i] = 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) A[i][j] = 0.f;
+    }
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+        const cplx<float> m11 = c12_entry<P, P>(m[l]), m12 = c12_entry<P, Q>(m[l]);
+        const cplx<float> m21 = c12_entry<Q, P>(m[l]), m22 = c12_entry<Q, Q>(m[l]);
+        const cplx<float> cc = c12_entry<R, R>(m[l]);
+        // tr(G M) = cc + w.a for a forward link; tr(M G^dag) = cc + w'.a for
+        // a backward link, w' = w with the signs of w1..w3 flipped
+        cplx<float> w[4];
+        w[0] = cadd(m11, m22);
+        w[1] = mk(-(m21.y + m12.y), m21.x + m12.x);
+        w[2] = csub(m21, m12);
+        w[3] = mk(-(m11.y - m22.y), m11.x - m22.x);
+        if (l >= 4) {
+#pragma unroll
+            for (int k = 1; k < 4; ++k) w[k] = mk(-w[k].x, -w[k].y);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            b[k] = fmaf(cc.x, w[k].x, fmaf(cc.y, w[k].y, b[k]));
+#pragma unroll
+            for (int j = k; j < 4; ++j) A[k][j] = fmaf(w[k].x, w[j].x, fmaf(w[k].y, w[j].y, A[k][j]));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int j = 0; j < k; ++j) A[k][j] = A[j][k];
+    c12_opaque(m);
+    int fb = 0;
+    {
+        float L[4][4], Dinv[4], mu, pd;
+        if (!kkt_newton<float, true>(A, b, a, mu, L, Dinv, pd)) {
+            const float4 r = solve_f32_fallback(A[0][0], A[0][1], A[0][2], A[0][3], A[1][1], A[1][2], A[1][3],
+                                                A[2][2], A[2][3], A[3][3], b[0], b[1], b[2], b[3]);
+            a[0] = r.x;
+            a[1] = r.y;
+            a[2] = r.z;
+            a[3] = r.w;
+            fb = 1;
+        }
+    }
+    if (omega != 1.f) {
+        // over-relaxation: a -> normalise((1 - omega) e0 + omega a)
+        a[0] = (1.f - omega) + omega * a[0];
+        a[1] *= omega;
+        a[2] *= omega;
+        a[3] *= omega;
+        const float inv = rsqrtf(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a[k] *= inv;
+    }
+    // forward links: rows P, Q of G M
+#pragma unroll
+    for (int l = 0; l < 4; ++l) c12_left_update<P, Q>(m[l], a);
+    // backward links: columns P, Q of M G^dag, rows 0 and 1
+    const cplx<float> g11 = mk(a[0], a[3]), g12 = mk(a[2], a[1]), g21 = mk(-a[2], a[1]), g22 = mk(a[0], -a[3]);
+#pragma unroll
+    for (int l = 4; l < 8; ++l) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const cplx<float> xp = m[l][3 * i + P], xq = m[l][3 * i + Q];
+            m[l][3 * i + P] = cfmac(xq, g12, cmulc(xp, g11));
+            m[l][3 * i + Q] = cfmac(xq, g22, cmulc(xp, g21));
+        }
+    }
+    return fb;
+}
+
+// One thread per site.  The 8 links are loaded straight into registers (24
+// 16-byte loads in flight at once); W(x), needed only after the three steps,
+// is staged into shared memory by cp.async meanwhile and updated at the end
+// with the three subgroup elements, which keeps its 12 registers free during
+// the solves.
+template <bool ACC, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_halfsweep_c12(SweepBatch bt, int parity) {
+    extern __shared__ float4 wstage[];  // 3 chunks x NT
     const int f = field_of_block(bt.desc, bt.nf, blockIdx.x);
     if (bt.state[f].done) return;  // block-uniform
     const FieldDesc fd = bt.desc[f];
     const Geom g = fd.geo;
-    cplx<T>* __restrict__ U = reinterpret_cast<cplx<T>*>(fd.U);
-    cplx<T>* __restrict__ G = reinterpret_cast<cplx<T>*>(fd.G);
-    const int h = threadIdx.x & 1;
-    const int s = (blockIdx.x - fd.blk0) * SPB + (threadIdx.x >> 1);
-    const bool active = s < g.vh;
-    const unsigned mask = __ballot_sync(0xffffffffu, active);
-
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SmemLinks<T, NT> lk;  // slots 0..3: own links; slot 4: Omega (lane 0)
-    lk.base = reinterpret_cast<cplx<T>*>(smem_raw);
-
-    double rsum = 0.0;
+    float4* __restrict__ U = reinterpret_cast<float4*>(fd.U);
+    float4* __restrict__ W = reinterpret_cast<float4*>(fd.G);
+    const int s = (blockIdx.x - fd.blk0) * NT + threadIdx.x;
+    const size_t vh = (size_t)g.vh;
+    float rsum = 0.f;
     int fb = 0;
-    if (active) {
+    if (s < g.vh) {
+        {
+            const float4* src = W + c12_gidx(g, parity, 0, s);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) cp_async<16>(&wstage[q * NT + threadIdx.x], src + q * vh);
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+        }
         int c[4];
         eo_coords(g, parity, s, c);
-        const int pl = parity ^ h;  // parity of the sites the own links start at
-        int sl[4];
+        int sb[4];
 #pragma unroll
-        for (int mu = 0; mu < 4; ++mu) sl[mu] = h ? eo_neighbor(g, c, mu, -1) : s;
+        for (int mu = 0; mu < 4; ++mu) sb[mu] = eo_neighbor(g, c, mu, -1);
+        cplx<float> m[8][6];
 #pragma unroll
-        for (int mu = 0; mu < 4; ++mu) {
-            const cplx<T>* src = U + lidx(g, mu, pl, 0, sl[mu]);
-#pragma unroll 1
-            for (int e = 0; e < 9; ++e) cp_async<sizeof(cplx<T>)>(&lk(mu, e), src + (size_t)e * g.vh);
+        for (int mu = 0; mu < 4; ++mu) c12_load(U + c12_lidx(g, mu, parity, 0, s), vh, m[mu]);
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) c12_load(U + c12_lidx(g, mu, parity ^ 1, 0, sb[mu]), vh, m[4 + mu]);
+
+        const float omega = (float)bt.omega;
+        float a01[4], a02[4], a12[4];
+        fb += c12_subgroup_step<0, 1, 2>(m, omega, a01);
+        fb += c12_subgroup_step<0, 2, 1>(m, omega, a02);
+        fb += c12_subgroup_step<1, 2, 0>(m, omega, a12);
+
+        // FP32 re-unitarisation every sweep: the 8 links in the odd half-sweep
+        // (which touches every link once), W every half-sweep.  FP32 rounding
+        // would otherwise inflate |tr U|^2 by ~1e-6 per sweep and swamp the
+        // convergence signal.
+        if (ACC) {
+#pragma unroll
+            for (int l = 0; l < 8; ++l) c12_reunitarise(m[l]);
         }
-        if (h == 0) {
 #pragma unroll
-            for (int e = 0; e < 9; ++e) cp_async<sizeof(cplx<T>)>(&lk(4, e), &G[gidx(g, parity, e, s)]);
+        for (int mu = 0; mu < 4; ++mu) c12_store(U + c12_lidx(g, mu, parity, 0, s), vh, m[mu]);
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) c12_store(U + c12_lidx(g, mu, parity ^ 1, 0, sb[mu]), vh, m[4 + mu]);
+        if (ACC) {
+            // the site's 8 links (|tr|^2 <= 9 each) summed in FP32, widened once
+#pragma unroll
+            for (int l = 0; l < 8; ++l) {
+                const cplx<float> t = cadd(cadd(m[l][0], m[l][4]), row2_entry(m[l], 2));
+                rsum = fmaf(t.x, t.x, fmaf(t.y, t.y, rsum));
+            }
         }
         cp_async_wait_all();
-
-        const T omega = (T)bt.omega;
-#pragma unroll 1
-        for (int sg = 0; sg < 3; ++sg) {
-            const int P = sg == 2 ? 1 : 0, Q = sg == 0 ? 1 : 2, R = 3 - P - Q;
-            T A[4][4], b[4];
+        cplx<float> w[6];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                b[i] = T(0);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) A[i][j] = T(0);
-            }
-            const int ePP = 3 * P + P, ePQ = 3 * P + Q, eQP = 3 * Q + P, eQQ = 3 * Q + Q, eRR = 3 * R + R;
-#pragma unroll
-            for (int l = 0; l < 4; ++l) {
-                const cplx<T> m11 = lk(l, ePP), m12 = lk(l, ePQ), m21 = lk(l, eQP), m22 = lk(l, eQQ);
-                const cplx<T> cc = lk(l, eRR);
-                cplx<T> w[4];
-                w[0] = cadd(m11, m22);
-                w[1] = mk(-(m21.y + m12.y), m21.x + m12.x);
-                w[2] = csub(m21, m12);
-                w[3] = mk(-(m11.y - m22.y), m11.x - m22.x);
-                if (h) {
-#pragma unroll
-                    for (int k = 1; k < 4; ++k) w[k] = mk(-w[k].x, -w[k].y);
-                }
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    b[k] = fma(cc.x, w[k].x, fma(cc.y, w[k].y, b[k]));
-#pragma unroll
-                    for (int j = k; j < 4; ++j) A[k][j] = fma(w[k].x, w[j].x, fma(w[k].y, w[j].y, A[k][j]));
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                b[k] += __shfl_xor_sync(mask, b[k], 1);
-#pragma unroll
-                for (int j = k; j < 4; ++j) A[k][j] += __shfl_xor_sync(mask, A[k][j], 1);
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-#pragma unroll
-                for (int j = 0; j < k; ++j) A[k][j] = A[j][k];
-            T a[4];
-            asm volatile("" ::: "memory");
-            fb += Solver<T>::solve(A, b, a);
-            if (omega != T(1)) {
-                a[0] = (T(1) - omega) + omega * a[0];
-                a[1] *= omega;
-                a[2] *= omega;
-                a[3] *= omega;
-                const T inv = rsqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) a[k] *= inv;
-            }
-            const cplx<T> g11 = mk(a[0], a[3]), g12 = mk(a[2], a[1]), g21 = mk(-a[2], a[1]), g22 = mk(a[0], -a[3]);
-            if (h == 0) {
-#pragma unroll 1
-                for (int l = 0; l < 5; ++l) {
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {  // rows P, Q of G U and of G Omega
-                        const cplx<T> xp = lk(l, 3 * P + k), xq = lk(l, 3 * Q + k);
-                        lk(l, 3 * P + k) = cfma(g12, xq, cmul(g11, xp));
-                        lk(l, 3 * Q + k) = cfma(g22, xq, cmul(g21, xp));
-                    }
-                }
-            } else {
-#pragma unroll 1
-                for (int l = 0; l < 4; ++l) {
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {  // columns P, Q of U G^dag
-                        const cplx<T> xp = lk(l, 3 * k + P), xq = lk(l, 3 * k + Q);
-                        lk(l, 3 * k + P) = cfmac(xq, g12, cmulc(xp, g11));
-                        lk(l, 3 * k + Q) = cfmac(xq, g22, cmulc(xp, g21));
-                    }
-                }
-            }
-            asm volatile("" ::: "memory");
+        for (int q = 0; q < 3; ++q) {
+            const float4 v = wstage[q * NT + threadIdx.x];
+            w[2 * q] = mk(v.x, v.y);
+            w[2 * q + 1] = mk(v.z, v.w);
         }
-        // FP32 re-unitarisation: Omega every half-sweep, the links in the odd one
-        {
-            const int l0 = ACC ? 0 : 4;
-            const int l1 = h == 0 ? 5 : 4;
-#pragma unroll 1
-            for (int l = l0; l < l1; ++l) {
-                cplx<T> m[9];
-#pragma unroll
-                for (int e = 0; e < 9; ++e) m[e] = lk(l, e);
-                m3_reunitarise_same(m);
-#pragma unroll
-                for (int e = 0; e < 9; ++e) lk(l, e) = m[e];
-            }
-            asm volatile("" ::: "memory");
-        }
-#pragma unroll
-        for (int mu = 0; mu < 4; ++mu) {
-            cplx<T>* dst = U + lidx(g, mu, pl, 0, sl[mu]);
-#pragma unroll 1
-            for (int e = 0; e < 9; ++e) dst[(size_t)e * g.vh] = lk(mu, e);
-        }
-        if (h == 0) {
-#pragma unroll
-            for (int e = 0; e < 9; ++e) G[gidx(g, parity, e, s)] = lk(4, e);
-        }
-        if (ACC) {
-            // the lane's 4 links summed in FP32 (|tr|^2 <= 9 each), widened once;
-            // FP64 work stays off this kernel's critical path
-            T r4 = T(0);
-#pragma unroll
-            for (int l = 0; l < 4; ++l) {
-                const T tr = lk(l, 0).x + lk(l, 4).x + lk(l, 8).x;
-                const T ti = lk(l, 0).y + lk(l, 4).y + lk(l, 8).y;
-                r4 = fma(tr, tr, fma(ti, ti, r4));
-            }
-            rsum = (double)r4;
-        }
+        c12_left_update<0, 1>(w, a01);
+        c12_left_update<0, 2>(w, a02);
+        c12_left_update<1, 2>(w, a12);
+        c12_reunitarise(w);
+        c12_store(W + c12_gidx(g, parity, 0, s), vh, w);
     }
     __shared__ double red[NT / 32];
     if (ACC) {
-        const double tot = block_sum(rsum, red);
+        const double tot = block_sum((double)rsum, red);
         if (threadIdx.x == 0) bt.partial[blockIdx.x] = tot;
     }
     {
-        // lane 0 of each pair reports the pair's fallbacks
-        const int w = __reduce_add_sync(0xffffffffu, h == 0 ? fb : 0);
+        // count local solves that left the Newton path (diagnostic)
+        const int w = __reduce_add_sync(0xffffffffu, fb);
         if ((threadIdx.x & 31) == 0 && w) atomicAdd(&bt.state[f].fallbacks, w);
     }
 }
 
 // R over all links of each field, into per-block partials (same block map as
-// the half-sweep).
+// the half-sweep).  FP64 fields are in the full layout, FP32 fields in the
+// compact one (tr U = U00 + U11 + conj(U00 U11 - U01 U10)).
 template <typename T>
-__global__ void __launch_bounds__(128) k_functional(SweepBatch bt) {
+__global__ void __launch_bounds__(256) k_functional(SweepBatch bt) {
     const int f = field_of_block(bt.desc, bt.nf, blockIdx.x);
     const FieldDesc fd = bt.desc[f];
     const Geom g = fd.geo;
-    const cplx<T>* __restrict__ U = reinterpret_cast<const cplx<T>*>(fd.U);
     const int s = (blockIdx.x - fd.blk0) * blockDim.x + threadIdx.x;
     double r = 0.0;
     if (s < g.vh) {
@@ -907,12 +946,24 @@ __global__ void __launch_bounds__(128) k_functional(SweepBatch bt) {
         for (int p = 0; p < 2; ++p)
 #pragma unroll
             for (int mu = 0; mu < 4; ++mu) {
-                const cplx<T> a = U[lidx(g, mu, p, 0, s)], b = U[lidx(g, mu, p, 4, s)], c = U[lidx(g, mu, p, 8, s)];
-                const double tr = (double)(a.x + b.x + c.x), ti = (double)(a.y + b.y + c.y);
+                double tr, ti;
+                if constexpr (sizeof(T) == 8) {
+                    const cplx<T>* __restrict__ U = reinterpret_cast<const cplx<T>*>(fd.U);
+                    const cplx<T> a = U[lidx(g, mu, p, 0, s)], b = U[lidx(g, mu, p, 4, s)], c = U[lidx(g, mu, p, 8, s)];
+                    tr = (double)(a.x + b.x + c.x);
+                    ti = (double)(a.y + b.y + c.y);
+                } else {
+                    const float4* __restrict__ U = reinterpret_cast<const float4*>(fd.U);
+                    cplx<float> m[6];
+                    c12_load(U + c12_lidx(g, mu, p, 0, s), (size_t)g.vh, m);
+                    const cplx<float> t = cadd(cadd(m[0], m[4]), row2_entry(m, 2));
+                    tr = (double)t.x;
+                    ti = (double)t.y;
+                }
                 r += tr * tr + ti * ti;
             }
     }
-    __shared__ double red[4];
+    __shared__ double red[8];
     const double tot = block_sum(r, red);
     if (threadIdx.x == 0) bt.partial[blockIdx.x] = tot;
 }
@@ -997,19 +1048,14 @@ __global__ void __launch_bounds__(128) k_reunit_pending(SweepBatch bt) {
 // host driver
 // ---------------------------------------------------------------------------
 // Threads per block of the half-sweep kernel, per precision; set by
-// mcg_set_sweep_block (the block-size autotuner).  FP64 runs one thread per
-// site (64 or 128 threads); FP32 runs the pair-split kernel, two threads per
-// site (64, 128 or 256 threads).
+// mcg_set_sweep_block (the block-size autotuner).  Both run one thread per
+// site: FP64 64 or 128 threads, FP32 (compact, register resident) 64, 128 or
+// 256.
 static int g_sweep_nt[2] = {128, 128};
 
 int sweep_block(int prec) { return g_sweep_nt[prec == MCG_F64 ? 0 : 1]; }
 void set_sweep_block(int prec, int nt) { g_sweep_nt[prec == MCG_F64 ? 0 : 1] = nt; }
-int sweep_sites_per_block(int prec) { return prec == MCG_F64 ? sweep_block(prec) : sweep_block(prec) / 2; }
-
-template <typename T>
-static size_t halfsweep_smem(int nt) {
-    return sizeof(T) == 8 ? sizeof(cplx<T>) * 81 * nt : sizeof(cplx<T>) * 45 * nt;
-}
+int sweep_sites_per_block(int prec) { return sweep_block(prec); }
 
 template <typename K>
 static int raise_smem(K kernel, size_t smem) {
@@ -1017,14 +1063,20 @@ static int raise_smem(K kernel, size_t smem) {
     return 0;
 }
 
+// shared memory of the FP64 kernel: 8 links + Omega per thread
+static size_t halfsweep_smem_f64(int nt) { return sizeof(cplx<double>) * 81 * nt; }
+
+// FP32 kernel: dynamic shared memory for the staged W (3 chunks per thread)
+static size_t halfsweep_smem_c12(int nt) { return sizeof(float4) * 3 * nt; }
+
 template <typename T>
 static int prepare_halfsweep(int nt) {
-    static bool done[3] = {false, false, false};
-    const int slot = nt == 64 ? 0 : (nt == 128 ? 1 : 2);
-    if (done[slot]) return 0;
-    const size_t smem = halfsweep_smem<T>(nt);
-    int rc = 0;
     if constexpr (sizeof(T) == 8) {
+        static bool done[2] = {false, false};
+        const int slot = nt == 64 ? 0 : 1;
+        if (done[slot]) return 0;
+        const size_t smem = halfsweep_smem_f64(nt);
+        int rc = 0;
         if (nt == 128) {
             if ((rc = raise_smem(k_halfsweep<T, false, 128>, smem)) || (rc = raise_smem(k_halfsweep<T, true, 128>, smem)))
                 return rc;
@@ -1032,29 +1084,17 @@ static int prepare_halfsweep(int nt) {
             if ((rc = raise_smem(k_halfsweep<T, false, 64>, smem)) || (rc = raise_smem(k_halfsweep<T, true, 64>, smem)))
                 return rc;
         }
-    } else {
-        if (nt == 256) {
-            if ((rc = raise_smem(k_halfsweep_pair<T, false, 256>, smem)) ||
-                (rc = raise_smem(k_halfsweep_pair<T, true, 256>, smem)))
-                return rc;
-        } else if (nt == 128) {
-            if ((rc = raise_smem(k_halfsweep_pair<T, false, 128>, smem)) ||
-                (rc = raise_smem(k_halfsweep_pair<T, true, 128>, smem)))
-                return rc;
-        } else {
-            if ((rc = raise_smem(k_halfsweep_pair<T, false, 64>, smem)) ||
-                (rc = raise_smem(k_halfsweep_pair<T, true, 64>, smem)))
-                return rc;
-        }
+        done[slot] = true;
     }
-    done[slot] = true;
     return 0;
 }
 
+// FP32 occupancy: the register file holds 3 blocks of 128 threads (<= 168
+// registers per thread).
 template <typename T>
 static void launch_halfsweep(int nt, bool acc, const SweepBatch& bt, int parity, int nblocks, cudaStream_t st) {
-    const size_t smem = halfsweep_smem<T>(nt);
     if constexpr (sizeof(T) == 8) {
+        const size_t smem = halfsweep_smem_f64(nt);
         if (nt == 128) {
             if (acc)
                 k_halfsweep<T, true, 128><<<nblocks, 128, smem, st>>>(bt, parity);
@@ -1067,21 +1107,23 @@ static void launch_halfsweep(int nt, bool acc, const SweepBatch& bt, int parity,
                 k_halfsweep<T, false, 64><<<nblocks, 64, smem, st>>>(bt, parity);
         }
     } else {
+        const size_t smem = halfsweep_smem_c12(nt);
+        const int grid = nblocks;
         if (nt == 256) {
             if (acc)
-                k_halfsweep_pair<T, true, 256><<<nblocks, 256, smem, st>>>(bt, parity);
+                k_halfsweep_c12<true, 256, 1><<<grid, 256, smem, st>>>(bt, parity);
             else
-                k_halfsweep_pair<T, false, 256><<<nblocks, 256, smem, st>>>(bt, parity);
+                k_halfsweep_c12<false, 256, 1><<<grid, 256, smem, st>>>(bt, parity);
         } else if (nt == 128) {
             if (acc)
-                k_halfsweep_pair<T, true, 128><<<nblocks, 128, smem, st>>>(bt, parity);
+                k_halfsweep_c12<true, 128, 3><<<grid, 128, smem, st>>>(bt, parity);
             else
-                k_halfsweep_pair<T, false, 128><<<nblocks, 128, smem, st>>>(bt, parity);
+                k_halfsweep_c12<false, 128, 3><<<grid, 128, smem, st>>>(bt, parity);
         } else {
             if (acc)
-                k_halfsweep_pair<T, true, 64><<<nblocks, 64, smem, st>>>(bt, parity);
+                k_halfsweep_c12<true, 64, 6><<<grid, 64, smem, st>>>(bt, parity);
             else
-                k_halfsweep_pair<T, false, 64><<<nblocks, 64, smem, st>>>(bt, parity);
+                k_halfsweep_c12<false, 64, 6><<<grid, 64, smem, st>>>(bt, parity);
         }
     }
 }
@@ -1091,7 +1133,9 @@ static int enqueue_sweep(const SweepBatch& bt, int nt, int spb, cudaStream_t st)
     launch_halfsweep<T>(nt, false, bt, 0, bt.total_blocks, st);
     launch_halfsweep<T>(nt, true, bt, 1, bt.total_blocks, st);
     k_finalize<<<bt.nf, 256, 0, st>>>(bt, 0);
-    if (bt.reunit_every > 0) k_reunit_pending<T><<<bt.total_blocks, spb, 0, st>>>(bt);
+    // FP32 sweeps re-unitarise inside the half-sweep kernel
+    if constexpr (sizeof(T) == 8)
+        if (bt.reunit_every > 0) k_reunit_pending<T><<<bt.total_blocks, spb, 0, st>>>(bt);
     return 0;
 }
 
@@ -1177,7 +1221,7 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
         cudaGraphDestroy(graph);
         return cuda_fail(ce, "cudaGraphInstantiate");
     }
-    const int nodes_per_chunk = chunk * (reunit_every > 0 ? 4 : 3);
+    const int nodes_per_chunk = chunk * ((sizeof(T) == 8 && reunit_every > 0) ? 4 : 3);
     const int max_chunks = (phase_len + chunk - 1) / chunk + 1;
     int status = 0;
     for (int c = 0; c < max_chunks; ++c) {
