@@ -272,11 +272,7 @@ __device__ __forceinline__ void ldlt4_solve(const T (&L)[4][4], const T (&Dinv)[
 // success (converged, and mu - A positive definite: the global maximum of the
 // trust-region subproblem) returns true with a normalised, mu, and the LDL^T
 // factors of (mu - A) for later use.
-// EARLY: also stop once the quadratic rate seen over the last two
-// corrections (e_next ~ e^3 / e_prev^2) puts the next correction below the
-// tolerance (the FP32 sweep; the FP64 path refines from this solution and
-// takes the full iteration).
-template <typename T, bool EARLY = false>
+template <typename T>
 __device__ __forceinline__ bool kkt_newton(const T (&A)[4][4], const T (&b)[4], T (&a)[4], T& mu, T (&L)[4][4],
                                            T (&Dinv)[4], T& pd) {
     const T conv = sizeof(T) == 8 ? T(1e-13) : T(2e-6);
@@ -284,7 +280,6 @@ __device__ __forceinline__ bool kkt_newton(const T (&A)[4][4], const T (&b)[4], 
     a[1] = a[2] = a[3] = T(0);
     mu = A[0][0] + b[0];
     bool ok = false;
-    T dprev = T(-1);
 #pragma unroll 1
     for (int it = 0; it < 8; ++it) {
         T M[4][4];
@@ -311,11 +306,10 @@ __device__ __forceinline__ bool kkt_newton(const T (&A)[4][4], const T (&b)[4], 
             dmax = fmax(dmax, fabs(da));
         }
         mu += dmu;
-        if (dmax <= conv || (EARLY && dprev > T(0) && dmax * dmax * dmax <= conv * dprev * dprev)) {
+        if (dmax <= conv) {
             ok = true;
             break;
         }
-        dprev = dmax;
     }
     if (!ok) return false;
     const T inv = rsqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
@@ -707,6 +701,84 @@ __global__ void __launch_bounds__(NT, 2) k_halfsweep(SweepBatch bt, int parity) 
 // are in flight at once, straight into registers.
 // ---------------------------------------------------------------------------
 
+// Newton solve of the FP32 sweep.  The KKT system (mu - A) a = b, |a| = 1 is
+// iterated from a = e0 (the current links) in the form
+//   u = (mu - A)^-1 b,  y = (mu - A)^-1 a,
+//   dmu = (a.u - 1 + s) / a.y  with s = (1 - a.a)/2,   a <- u - dmu y,
+// which is the Newton step written without the residual b - (mu - A) a (the
+// two solves share one LDL^T and run interleaved).  Stops when the correction
+// is below 2e-6 or when the quadratic rate over the last two corrections puts
+// the next one below it.  Returns true with a normalised when the last
+// factorisation shows mu - A positive definite with pivots above 1e-5 of the
+// largest (mu >= lambda_max: the global maximum), false otherwise.
+__device__ __forceinline__ bool kkt_newton_f32(const float (&A)[4][4], const float (&b)[4], float (&a)[4]) {
+    const float conv = 2e-6f;
+    a[0] = 1.f;
+    a[1] = a[2] = a[3] = 0.f;
+    float mu = A[0][0] + b[0];
+    float dprev = -1.f, dmin = 0.f, dabs = 0.f;
+    bool ok = false;
+#pragma unroll 1
+    for (int it = 0; it < 8; ++it) {
+        // LDL^T of M = mu - A
+        float D[4], Dinv[4], L10, L20, L30, L21, L31, L32;
+        D[0] = mu - A[0][0];
+        Dinv[0] = frcp(D[0]);
+        L10 = -A[1][0] * Dinv[0];
+        L20 = -A[2][0] * Dinv[0];
+        L30 = -A[3][0] * Dinv[0];
+        D[1] = (mu - A[1][1]) - L10 * L10 * D[0];
+        Dinv[1] = frcp(D[1]);
+        L21 = (-A[2][1] - L20 * L10 * D[0]) * Dinv[1];
+        L31 = (-A[3][1] - L30 * L10 * D[0]) * Dinv[1];
+        D[2] = (mu - A[2][2]) - L20 * L20 * D[0] - L21 * L21 * D[1];
+        Dinv[2] = frcp(D[2]);
+        L32 = (-A[3][2] - L30 * L20 * D[0] - L31 * L21 * D[1]) * Dinv[2];
+        D[3] = (mu - A[3][3]) - L30 * L30 * D[0] - L31 * L31 * D[1] - L32 * L32 * D[2];
+        Dinv[3] = frcp(D[3]);
+        dmin = fminf(fminf(D[0], D[1]), fminf(D[2], D[3]));
+        dabs = fmaxf(fmaxf(fabsf(D[0]), fabsf(D[1])), fmaxf(fabsf(D[2]), fabsf(D[3])));
+        const float dsmall = fminf(fminf(fabsf(D[0]), fabsf(D[1])), fminf(fabsf(D[2]), fabsf(D[3])));
+        if (!(dsmall > 1e-12f * dabs)) return false;  // singular or NaN
+        // u = M^-1 b, y = M^-1 a (forward, diagonal, backward substitution)
+        float zu0 = b[0], zy0 = a[0];
+        float zu1 = b[1] - L10 * zu0, zy1 = a[1] - L10 * zy0;
+        float zu2 = b[2] - L20 * zu0 - L21 * zu1, zy2 = a[2] - L20 * zy0 - L21 * zy1;
+        float zu3 = b[3] - L30 * zu0 - L31 * zu1 - L32 * zu2, zy3 = a[3] - L30 * zy0 - L31 * zy1 - L32 * zy2;
+        zu0 *= Dinv[0]; zy0 *= Dinv[0];
+        zu1 *= Dinv[1]; zy1 *= Dinv[1];
+        zu2 *= Dinv[2]; zy2 *= Dinv[2];
+        zu3 *= Dinv[3]; zy3 *= Dinv[3];
+        const float u3 = zu3, y3 = zy3;
+        const float u2 = zu2 - L32 * u3, y2 = zy2 - L32 * y3;
+        const float u1 = zu1 - L21 * u2 - L31 * u3, y1 = zy1 - L21 * y2 - L31 * y3;
+        const float u0 = zu0 - L10 * u1 - L20 * u2 - L30 * u3, y0 = zy0 - L10 * y1 - L20 * y2 - L30 * y3;
+        const float aa = a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3];
+        const float au = a[0] * u0 + a[1] * u1 + a[2] * u2 + a[3] * u3;
+        const float ay = a[0] * y0 + a[1] * y1 + a[2] * y2 + a[3] * y3;
+        const float dmu = fdiv(au - 0.5f - 0.5f * aa, ay);
+        const float n0 = u0 - dmu * y0, n1 = u1 - dmu * y1, n2 = u2 - dmu * y2, n3 = u3 - dmu * y3;
+        const float dmax = fmaxf(fmaxf(fabsf(n0 - a[0]), fabsf(n1 - a[1])), fmaxf(fabsf(n2 - a[2]), fabsf(n3 - a[3])));
+        a[0] = n0;
+        a[1] = n1;
+        a[2] = n2;
+        a[3] = n3;
+        mu += dmu;
+        if (dmax <= conv || (dprev > 0.f && dmax * dmax * dmax <= conv * dprev * dprev)) {
+            ok = true;
+            break;
+        }
+        dprev = dmax;
+    }
+    if (!ok) return false;
+    const float inv = rsqrtf(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a[k] *= inv;
+    // certificate from the last factorisation (at mu - dmu, |dmu| far below
+    // the pivot margin)
+    return dmin > 1e-5f * dabs;
+}
+
 // FP32 fallback of the local solve (Jacobi + secular), out of line with its
 // arguments and result passed by value so that the caller's A and b stay in
 // registers.
@@ -805,8 +877,7 @@ __device__ __forceinline__ int c12_subgroup_step(cplx<float> (&m)[8][6], const f
     c12_opaque(m);
     int fb = 0;
     {
-        float L[4][4], Dinv[4], mu, pd;
-        if (!kkt_newton<float, true>(A, b, a, mu, L, Dinv, pd)) {
+        if (!kkt_newton_f32(A, b, a)) {
             const float4 r = solve_f32_fallback(A[0][0], A[0][1], A[0][2], A[0][3], A[1][1], A[1][2], A[1][3],
                                                 A[2][2], A[2][3], A[3][3], b[0], b[1], b[2], b[3]);
             a[0] = r.x;
