@@ -452,9 +452,61 @@ __device__ __forceinline__ bool kkt_refine_ldlt(const double (&A)[4][4], const d
     return false;
 }
 
+struct Vec4d {
+    double v[4];
+};
+
+// The rare FP64 local solves the warm-started path cannot settle: FP32 Jacobi
+// + secular seed refined in FP64 (kkt_refine), else the full FP64 Jacobi +
+// secular solve.  Out of line with A and b passed by value, so the caller's
+// copies stay in registers; the result is normalised.
+__device__ __noinline__ Vec4d solve_f64_fallback(double a00, double a01, double a02, double a03, double a11,
+                                                 double a12, double a13, double a22, double a23, double a33,
+                                                 double b0, double b1, double b2, double b3) {
+    const double A[4][4] = {{a00, a01, a02, a03}, {a01, a11, a12, a13}, {a02, a12, a22, a23}, {a03, a13, a23, a33}};
+    const double b[4] = {b0, b1, b2, b3};
+    float Af[4][4], bf[4], af[4], muf;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        bf[i] = (float)b[i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) Af[i][j] = (float)A[i][j];
+    }
+    Vec4d r;
+    bool ok = false;
+    float S[4][4], V[4][4];
+    const int hard = solve_f32(Af, bf, af, muf, S, V);
+    if (!hard) {
+        float amax = S[0][0], amin = S[0][0];
+#pragma unroll
+        for (int i = 1; i < 4; ++i) {
+            amax = fmaxf(amax, S[i][i]);
+            amin = fminf(amin, S[i][i]);
+        }
+        const float gap = muf - amax;
+        if (gap > 2e-4f * (muf - amin + 1e-30f)) {
+            double mu;
+            ok = kkt_refine(A, b, S, V, af, muf, r.v, mu);
+        }
+    }
+    if (!ok) {
+        double Aflat[16];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) Aflat[4 * i + j] = A[i][j];
+        solve_f64_full(Aflat, b, r.v);
+        return r;
+    }
+    const double inv = rsqrt(r.v[0] * r.v[0] + r.v[1] * r.v[1] + r.v[2] * r.v[2] + r.v[3] * r.v[3]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r.v[k] *= inv;
+    return r;
+}
+
 template <>
 struct Solver<double> {
-    // returns 1 when the full FP64 fallback was used
+    // returns 1 when the warm-started path did not settle the problem
     __device__ __forceinline__ static int solve(const double (&A)[4][4], const double (&b)[4], double (&a)[4]) {
         float Af[4][4], bf[4], af[4], muf;
 #pragma unroll
@@ -472,29 +524,10 @@ struct Solver<double> {
                 ok = kkt_refine_ldlt(A, b, L, Dinv, af, muf, a);
         }
         if (!ok) {
-            float S[4][4], V[4][4];
-            const int hard = solve_f32(Af, bf, af, muf, S, V);
-            if (!hard) {
-                float amax = S[0][0], amin = S[0][0];
+            const Vec4d r = solve_f64_fallback(A[0][0], A[0][1], A[0][2], A[0][3], A[1][1], A[1][2], A[1][3],
+                                               A[2][2], A[2][3], A[3][3], b[0], b[1], b[2], b[3]);
 #pragma unroll
-                for (int i = 1; i < 4; ++i) {
-                    amax = fmaxf(amax, S[i][i]);
-                    amin = fminf(amin, S[i][i]);
-                }
-                const float gap = muf - amax;
-                if (gap > 2e-4f * (muf - amin + 1e-30f)) {
-                    double mu;
-                    ok = kkt_refine(A, b, S, V, af, muf, a, mu);
-                }
-            }
-        }
-        if (!ok) {
-            double Aflat[16];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) Aflat[4 * i + j] = A[i][j];
-            solve_f64_full(Aflat, b, a);
+            for (int k = 0; k < 4; ++k) a[k] = r.v[k];
             return 1;
         }
         const double inv = rsqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
