@@ -72,6 +72,9 @@ def _load():
             lib.orc_staple_sum.argtypes = [P, P, L, I, D, D, P]
             lib.orc_smear_step_backward.argtypes = [P, P, P, P, D, D]
             lib.orc_functional_matrix_grad.argtypes = [P, P, P]
+            lib.orc_vortex_remove.argtypes = [P, P, P, P]
+            lib.orc_center_links.argtypes = [P, P, P]
+            lib.orc_wilson_loops.argtypes = [P, P, I, I, P]
             _lib = lib
     return _lib
 
@@ -288,3 +291,29 @@ def smear_backward(dims, U, Gout, rho: float, eps: float, nsteps: int) -> np.nda
     for k in range(nsteps - 1, -1, -1):
         G = smear_step_backward(dims, fields[k], G, rho, eps)
     return G
+
+
+def vortex_remove(dims, U, m) -> np.ndarray:
+    """Vortex-removed field U' = Z^dag U (Sec. III.D) for center sectors m (V, 4)."""
+    U = _cfield(U)
+    m = np.ascontiguousarray(m, dtype=np.int8)
+    out = np.empty_like(U)
+    _load().orc_vortex_remove(_p(_dims(dims)), _p(U), _p(m), _p(out))
+    return out
+
+
+def center_links(dims, m) -> np.ndarray:
+    """The vortex-only field Z = exp(2 pi i m / 3) * 1 (Sec. III.D), shape (V, 4, 3, 3)."""
+    m = np.ascontiguousarray(m, dtype=np.int8)
+    out = np.empty((m.shape[0], 4, 3, 3), np.complex128)
+    _load().orc_center_links(_p(_dims(dims)), _p(m), _p(out))
+    return out
+
+
+def wilson_loops(dims, U, Rmax: int, Tmax: int) -> np.ndarray:
+    """Planar Wilson loops W(R, T) (Sec. III.D), R spatial (averaged over x, y, z),
+    T along t, averaged over all translations; shape (Rmax, Tmax)."""
+    U = _cfield(U)
+    out = np.zeros(Rmax * Tmax)
+    _load().orc_wilson_loops(_p(_dims(dims)), _p(U), int(Rmax), int(Tmax), _p(out))
+    return out.reshape(Rmax, Tmax)

@@ -716,6 +716,103 @@ long long orc_vortex_count(const int* dims, const int8_t* m, long long* per_plan
 }
 
 /* ------------------------------------------------------------------ */
+/* Vortex removal, the vortex-only field and Wilson loops (Sec. III.D)   */
+/* ------------------------------------------------------------------ */
+
+/* The center element exp(2 pi i m / 3) of sector m as (cos, sin); the
+ * values for m = +-1 are the literals -1/2 and +-sqrt(3)/2. */
+static void center_phase(int m, double* c, double* s) {
+    if (m == 0) {
+        *c = 1.0;
+        *s = 0.0;
+    } else {
+        *c = -0.5;
+        *s = m > 0 ? 0.8660254037844386 : -0.8660254037844386;
+    }
+}
+
+/* Vortex-removed field U'_mu(x) = Z_mu(x)^dag U_mu(x), Z the center element
+ * of the link's sector m (Sec. III.D): every entry u becomes conj(Z) u, i.e.
+ * re' = c re + s im, im' = c im - s re (products and sums written out, never
+ * fused). */
+void orc_vortex_remove(const int* dims, const cplx* U, const int8_t* m, cplx* Uout) {
+    geom g = make_geom(dims);
+#pragma omp parallel for schedule(static)
+    for (long l = 0; l < g.vol * 4; ++l) {
+        double c, sn;
+        center_phase(m[l], &c, &sn);
+        for (int e = 0; e < 9; ++e) {
+            const double re = creal(U[l * 9 + e]), im = cimag(U[l * 9 + e]);
+            volatile double a = c * re, b = sn * im, d = c * im, f = sn * re;
+            Uout[l * 9 + e] = (a + b) + I * (d - f);
+        }
+    }
+}
+
+/* The vortex-only field: Z_mu(x) = exp(2 pi i m_mu(x) / 3) times the identity. */
+void orc_center_links(const int* dims, const int8_t* m, cplx* Z) {
+    geom g = make_geom(dims);
+    for (long l = 0; l < g.vol * 4; ++l) {
+        double c, sn;
+        center_phase(m[l], &c, &sn);
+        for (int e = 0; e < 9; ++e) Z[l * 9 + e] = (e % 4 == 0) ? c + I * sn : 0;
+    }
+}
+
+/* product of L links along mu from site x: U_mu(x) U_mu(x+mu) ... */
+static void line_product(const geom* g, const cplx* U, long x, int mu, int L, cplx* out) {
+    m_set_identity(out);
+    cplx t[9];
+    long y = x;
+    for (int k = 0; k < L; ++k) {
+        m_mul(t, out, clink(U, y, mu));
+        memcpy(out, t, sizeof t);
+        y = shift(g, y, mu, 1);
+    }
+}
+
+/* Planar Wilson loops W(R, T) (Sec. III.D): R links along a spatial axis i
+ * in {x, y, z}, T links along t (mu = 3), averaged over all V translations
+ * and the three spatial axes,
+ *   W(R,T) = < (1/3) Re tr [ S_i^R(x) S_t^T(x + R i) S_i^R(x + T t)^dag S_t^T(x)^dag ] >,
+ * S_mu^L(x) the product of L links along mu from x.  out[(R-1)*Tmax + T-1]
+ * for 1 <= R <= Rmax, 1 <= T <= Tmax; sums in fixed chunks. */
+void orc_wilson_loops(const int* dims, const cplx* U, int Rmax, int Tmax, double* out) {
+    geom g = make_geom(dims);
+    const int npair = Rmax * Tmax;
+    double* part = calloc((size_t)NCHUNK * npair, sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (int ch = 0; ch < NCHUNK; ++ch) {
+        const long x0 = g.vol * ch / NCHUNK, x1 = g.vol * (ch + 1) / NCHUNK;
+        for (long x = x0; x < x1; ++x)
+            for (int i = 0; i < 3; ++i)
+                for (int R = 1; R <= Rmax; ++R) {
+                    cplx S[9], A[9], B[9], C[9], D[9], t1[9], t2[9];
+                    line_product(&g, U, x, i, R, S);
+                    long xr = x;
+                    for (int k = 0; k < R; ++k) xr = shift(&g, xr, i, 1);
+                    for (int T = 1; T <= Tmax; ++T) {
+                        long xt = x;
+                        for (int k = 0; k < T; ++k) xt = shift(&g, xt, 3, 1);
+                        line_product(&g, U, xr, 3, T, A);  /* S_t^T(x + R i) */
+                        line_product(&g, U, xt, i, R, B);  /* S_i^R(x + T t) */
+                        line_product(&g, U, x, 3, T, C);   /* S_t^T(x)       */
+                        m_mul(t1, S, A);
+                        m_mul_nd(t2, t1, B);
+                        m_mul_nd(D, t2, C);
+                        part[(size_t)ch * npair + (R - 1) * Tmax + (T - 1)] += creal(m_trace(D)) / 3.0;
+                    }
+                }
+    }
+    for (int k = 0; k < npair; ++k) {
+        double acc = 0;
+        for (int ch = 0; ch < NCHUNK; ++ch) acc += part[(size_t)ch * npair + k];
+        out[k] = acc / (3.0 * g.vol);
+    }
+    free(part);
+}
+
+/* ------------------------------------------------------------------ */
 /* Gradient of R with respect to the gauge transform                    */
 /* ------------------------------------------------------------------ */
 
