@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--dims", type=int, nargs=4, default=list(DIMS))
     ap.add_argument("--levels", type=int, nargs="+", default=list(LEVELS))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-observables", action="store_true",
+                    help="skip the Sec. III.D measurement (vortex removal, Wilson loops) on the level-0 result")
     ap.add_argument("--profile-slice", action="store_true",
                     help="one bench step with sweeps capped (FP32 100 + FP64 1 per fix, levels 0 and 4, block sizes "
                          "128): the same kernels and launch shapes in ~1000 launches, for an ncu launch list")
@@ -408,6 +410,31 @@ def main():
     roof["step_share_estimate"] = {"fp32": share32 / max(share32 + share64, 1e-9),
                                    "fp64": share64 / max(share32 + share64, 1e-9)}
 
+    # Sec. III.D on the level-0 result: center decomposition (vortex-removed
+    # and vortex-only fields) and on-axis Wilson loops of the three fields
+    sec3d = None
+    if not args.no_observables:
+        Uf, Zf = U_out[0:1], Z_out[0:1]
+        RT = (8, 8)
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        q2 = torch.cuda.Event(enable_timing=True)
+        mcg.mcg_vortex_remove(Uf, Zf, dims)  # warm-up (scratch, module load)
+        q0.record(stream)
+        Ur, Zl = mcg.mcg_vortex_remove(Uf, Zf, dims)
+        q1.record(stream)
+        Ws = {name: mcg.mcg_wilson_loops(F, dims, *RT)[0] for name, F in
+              (("full", Uf), ("vortex_removed", Ur), ("vortex_only", Zl))}
+        q2.record(stream)
+        torch.cuda.synchronize(dev)
+        vr_ms = q0.elapsed_time(q1)
+        vr_bytes = 3 * V * 4 * 144 + V * 4  # read U and Z, write U' and Z (FP64 links)
+        sec3d = {"field": "level 0 fixed field", "vortex_remove_ms": vr_ms,
+                 "vortex_remove_GBps": vr_bytes / (vr_ms / 1e3) / 1e9,
+                 "wilson_ms_3_fields": q1.elapsed_time(q2), "Rmax": RT[0], "Tmax": RT[1],
+                 "W_RxT_diag": {k: [float(w[i, i]) for i in range(RT[0])] for k, w in Ws.items()}}
+        del Ur, Zl
+
     # end to end through the public API: host canonical field in, results out
     barrier()
     z_host = torch.empty((nl, V, 4), dtype=torch.int8).pin_memory()
@@ -454,7 +481,7 @@ def main():
                 "roofline": roof, "cpu_baseline": cpu, "autotune": tuned,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": canon_pinned.numel() * 16,
                         "d2h_bytes_per_step": z_host.numel(), "ms_per_step": e2e_ms / args.steps},
-                "clocks": clk.summary(), "gpu_launches": launches}
+                "clocks": clk.summary(), "gpu_launches": launches, "sec3d": sec3d}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

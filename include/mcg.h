@@ -209,6 +209,33 @@ int mcg_center_project(const void* U, int8_t* Z, long long* counts, const mcg_la
                        cudaStream_t stream);
 
 /*
+ * Center decomposition of a fixed field (Sec. III.D): with Z the center
+ * sectors of U (from mcg_center_project, same batch), U_removed <- Z^dag U
+ * (the vortex-removed field U' of the paper) and U_center <- Z times the
+ * identity (the vortex-only field), in the link layout and precision of U.
+ * Either output may be NULL (not both); U_removed may be U itself (in place)
+ * but may not overlap it otherwise; U_center may not overlap U or U_removed.
+ * conj(Z) multiplies each entry with the products and sums rounded
+ * separately (Z = 1 or -1/2 +- i sqrt(3)/2 as literals).  Device pointers;
+ * asynchronous on `stream`.
+ */
+int mcg_vortex_remove(const void* U, const int8_t* Z, void* U_removed, void* U_center, const mcg_lattice* lat,
+                      cudaStream_t stream);
+
+/*
+ * Planar Wilson loops (Sec. III.D): W(R, T) is the mean over all V
+ * translations and the three spatial axes i of
+ *   (1/3) Re tr [ S_i^R(x) S_t^T(x + R i) S_i^R(x + T t)^dag S_t^T(x)^dag ],
+ * S_mu^L(x) = U_mu(x) U_mu(x+mu) ... U_mu(x+(L-1)mu), t the fourth axis
+ * (mu = 3), for 1 <= R <= Rmax (at most the smallest spatial extent) and
+ * 1 <= T <= Tmax (at most N_t).  On-axis loops only: the paper's off-axis
+ * spatial paths are not built.  Arithmetic in the field's precision, sums in
+ * FP64.  W_out: host, nfields x Rmax x Tmax doubles, [f][R-1][T-1].  Uses
+ * library scratch of (Tmax + 6) x 9V complex numbers.  Synchronises.
+ */
+int mcg_wilson_loops(const void* U, const mcg_lattice* lat, int Rmax, int Tmax, double* W_out, cudaStream_t stream);
+
+/*
  * The preconditioning pipeline of Sec. II.B for every field of the batch:
  * S = smear(U, rho, eps, nsmear); fix S (transform Omega_1 from identity);
  * apply Omega_1 (re-unitarised) to the original U; fix that field (transform

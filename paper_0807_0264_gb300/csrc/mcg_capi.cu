@@ -475,6 +475,32 @@ int mcg_center_project(const void* U, int8_t* Z, long long* counts, const mcg_la
     return compute_center(U, lat->precision, Z, g, lat->nfields, counts, stream);
 }
 
+int mcg_vortex_remove(const void* U, const int8_t* Z, void* U_removed, void* U_center, const mcg_lattice* lat,
+                      cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if (!U || !Z) return fail(MCG_BAD_ARG, "null pointer");
+    if (!U_removed && !U_center) return fail(MCG_BAD_ARG, "no output requested");
+    const size_t bytes = elem_bytes(lat->precision) * link_elems(g) * lat->nfields;
+    if (U_center && (overlap(U, bytes, U_center, bytes) || (U_removed && overlap(U_removed, bytes, U_center, bytes))))
+        return fail(MCG_BAD_ARG, "U_center overlaps an input or U_removed");
+    if (U_removed && U_removed != U && overlap(U, bytes, U_removed, bytes))
+        return fail(MCG_BAD_ARG, "U_removed partially overlaps U");
+    return launch_vortex_remove(U, Z, U_removed, U_center, lat->precision, g, lat->nfields, stream);
+}
+
+int mcg_wilson_loops(const void* U, const mcg_lattice* lat, int Rmax, int Tmax, double* W_out, cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if (!U || !W_out) return fail(MCG_BAD_ARG, "null pointer");
+    const int nmin = std::min(g.n[0], std::min(g.n[1], g.n[2]));
+    if (Rmax < 1 || Rmax > nmin || Tmax < 1 || Tmax > g.n[3])
+        return fail(MCG_BAD_ARG, "need 1 <= Rmax <= smallest spatial extent and 1 <= Tmax <= N_t");
+    return compute_wilson_loops(U, lat->precision, g, lat->nfields, Rmax, Tmax, W_out, stream);
+}
+
 int mcg_precondition_fix(void* U, void* G, int8_t* Z, const mcg_lattice* lat, const mcg_params* params, double rho,
                          double eps, int nsmear, int smear_precision, mcg_precond_result* results,
                          cudaStream_t stream) {

@@ -115,6 +115,12 @@ int launch_to_c12(const void* src, int src_prec, void* dst, const Geom& g, int n
 int launch_from_c12(const void* src, void* dst, const Geom& g, int nmat, int nfields, cudaStream_t st);
 int launch_identity_c12(void* W, const Geom& g, int nfields, cudaStream_t st);
 
+// ---- center decomposition and Wilson loops (mcg_observables.cu) --------------
+int launch_vortex_remove(const void* U, const int8_t* Z, void* Ur, void* Zl, int prec, const Geom& g, int nfields,
+                         cudaStream_t st);
+int compute_wilson_loops(const void* U, int prec, const Geom& g, int nfields, int Rmax, int Tmax, double* W_host,
+                         cudaStream_t st);
+
 // ---- smearing (mcg_smear.cu) ------------------------------------------------
 int run_smear(const void* Uin, void* Uout, int prec, const Geom& g, int nfields, double rho, double eps, int n,
               cudaStream_t st);

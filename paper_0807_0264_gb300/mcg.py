@@ -85,6 +85,8 @@ def _load() -> ctypes.CDLL:
         "mcg_smear": ([P, P, L, D, D, I, P], I),
         "mcg_fix": ([P, P, L, PR, P, P, P, P], I),
         "mcg_center_project": ([P, P, P, L, P], I),
+        "mcg_vortex_remove": ([P, P, P, P, L, P], I),
+        "mcg_wilson_loops": ([P, L, I, I, P, P], I),
         "mcg_precondition_fix": ([P, P, P, L, PR, D, D, I, I, ctypes.POINTER(mcg_precond_result), P], I),
         "mcg_precondition_levels": ([P, P, P, P, L, PR, D, D, ctypes.POINTER(ctypes.c_int), I, I,
                                      ctypes.POINTER(mcg_precond_result), P], I),
@@ -117,7 +119,7 @@ EXPORTS = ("mcg_version", "mcg_last_error", "mcg_release", "mcg_pack_links", "mc
            "mcg_precondition_fix", "mcg_precondition_levels", "mcg_time_halfsweep", "mcg_kernel_launches",
            "mcg_plaquette_static", "mcg_set_sweep_block", "mcg_get_sweep_block", "mcg_fix_batch",
            "mcg_gribov_search", "mcg_smear_backward_step", "mcg_functional_matrix_grad", "mcg_grad_R",
-           "mcg_ascent_step")
+           "mcg_ascent_step", "mcg_vortex_remove", "mcg_wilson_loops")
 
 
 def library() -> ctypes.CDLL:
@@ -351,6 +353,36 @@ def mcg_center_project(U: torch.Tensor, dims, Z: torch.Tensor | None = None, str
     _check("mcg_center_project",
            _lib.mcg_center_project(_ptr(U), _ptr(Z), counts, lattice(dims, nf, precision_of(U)), _stream(stream)))
     return Z, [list(counts[7 * f: 7 * f + 7]) for f in range(nf)]
+
+
+def mcg_vortex_remove(U: torch.Tensor, Z: torch.Tensor, dims, removed: bool = True, center: bool = True,
+                      stream=None):
+    """Center decomposition of a fixed field (Sec. III.D) with its center
+    sectors Z: returns (U_removed = Z^dag U, U_center = Z * 1), each None when
+    not requested."""
+    _need_cuda(U, Z)
+    if Z.dtype != torch.int8:
+        raise TypeError("Z must be int8 center sectors")
+    Ur = torch.empty_like(U) if removed else None
+    Zl = torch.empty_like(U) if center else None
+    _check("mcg_vortex_remove",
+           _lib.mcg_vortex_remove(_ptr(U), _ptr(Z), _ptr(Ur) if Ur is not None else None,
+                                  _ptr(Zl) if Zl is not None else None, lattice(dims, U.shape[0], precision_of(U)),
+                                  _stream(stream)))
+    return Ur, Zl
+
+
+def mcg_wilson_loops(U: torch.Tensor, dims, Rmax: int, Tmax: int, stream=None):
+    """Planar on-axis Wilson loops W(R, T) (Sec. III.D), averaged over all
+    translations and the three spatial axes; numpy array (nfields, Rmax, Tmax)."""
+    import numpy as np
+
+    _need_cuda(U)
+    nf = U.shape[0]
+    out = (ctypes.c_double * (nf * Rmax * Tmax))()
+    _check("mcg_wilson_loops", _lib.mcg_wilson_loops(_ptr(U), lattice(dims, nf, precision_of(U)), int(Rmax), int(Tmax),
+                                                     out, _stream(stream)))
+    return np.ctypeslib.as_array(out).reshape(nf, Rmax, Tmax).copy()
 
 
 def mcg_precondition_fix(U: torch.Tensor, G: torch.Tensor, dims, params: Params | None = None, rho: float = 0.1,
