@@ -75,6 +75,7 @@ def _load():
             lib.orc_vortex_remove.argtypes = [P, P, P, P]
             lib.orc_center_links.argtypes = [P, P, P]
             lib.orc_wilson_loops.argtypes = [P, P, I, I, P]
+            lib.orc_wilson_loops_offaxis.argtypes = [P, P, P, I, I, P]
             _lib = lib
     return _lib
 
@@ -317,3 +318,14 @@ def wilson_loops(dims, U, Rmax: int, Tmax: int) -> np.ndarray:
     out = np.zeros(Rmax * Tmax)
     _load().orc_wilson_loops(_p(_dims(dims)), _p(U), int(Rmax), int(Tmax), _p(out))
     return out.reshape(Rmax, Tmax)
+
+
+def wilson_loops_offaxis(dims, U, vectors, Tmax: int) -> np.ndarray:
+    """Wilson loops with spatial side r (any integer 3-vector, off-axis
+    allowed) and temporal side T (Sec. III.D), averaged over all translations
+    and the distinct cubic images of r; shape (len(vectors), Tmax)."""
+    U = _cfield(U)
+    v = np.ascontiguousarray(np.asarray(vectors, dtype=np.int32).reshape(-1, 3))
+    out = np.zeros(v.shape[0] * Tmax)
+    _load().orc_wilson_loops_offaxis(_p(_dims(dims)), _p(U), _p(v), int(v.shape[0]), int(Tmax), _p(out))
+    return out.reshape(v.shape[0], Tmax)

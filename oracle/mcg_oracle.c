@@ -812,6 +812,119 @@ void orc_wilson_loops(const int* dims, const cplx* U, int Rmax, int Tmax, double
     free(part);
 }
 
+/* Off-axis spatial paths (Sec. III.D mentions off-axis loops without
+ * fixing the paths; reading): the path from x to x + r, r = (r0, r1, r2),
+ * takes L = |r0| + |r1| + |r2| unit steps; step k (1-based) goes along the
+ * axis j with the largest deficit k |r_j| / L - n_j (n_j: steps taken along j
+ * so far), ties to the lowest j, in the direction of sign(r_j).  For an
+ * on-axis r this is the straight path.  Writes the axes (0..2) and signs of
+ * the L steps; returns L. */
+static int path_steps(const int* r, int* axis, int* sign) {
+    const int L = abs(r[0]) + abs(r[1]) + abs(r[2]);
+    int n[3] = {0, 0, 0};
+    for (int k = 1; k <= L; ++k) {
+        int best = -1;
+        double bd = -1e300;
+        for (int j = 0; j < 3; ++j) {
+            if (n[j] >= abs(r[j])) continue;
+            const double d = (double)k * abs(r[j]) / L - n[j];
+            if (d > bd) {
+                bd = d;
+                best = j;
+            }
+        }
+        axis[k - 1] = best;
+        sign[k - 1] = r[best] > 0 ? 1 : -1;
+        n[best]++;
+    }
+    return L;
+}
+
+/* product of the links along the path of r from x (backward steps use
+ * U_j(y - j)^dag) */
+static void path_product(const geom* g, const cplx* U, long x, const int* r, cplx* out) {
+    int axis[64], sign[64];
+    const int L = path_steps(r, axis, sign);
+    m_set_identity(out);
+    cplx t[9], d[9];
+    long y = x;
+    for (int k = 0; k < L; ++k) {
+        if (sign[k] > 0) {
+            m_mul(t, out, clink(U, y, axis[k]));
+            y = shift(g, y, axis[k], 1);
+        } else {
+            y = shift(g, y, axis[k], -1);
+            m_dag(d, clink(U, y, axis[k]));
+            m_mul(t, out, d);
+        }
+        memcpy(out, t, sizeof t);
+    }
+}
+
+/* the distinct images of r under axis permutations and sign flips */
+static int cubic_images(const int* r, int img[48][3]) {
+    static const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    int n = 0;
+    for (int p = 0; p < 6; ++p)
+        for (int sgn = 0; sgn < 8; ++sgn) {
+            int v[3];
+            for (int j = 0; j < 3; ++j) v[j] = r[perm[p][j]] * ((sgn >> j) & 1 ? -1 : 1);
+            int dup = 0;
+            for (int q = 0; q < n && !dup; ++q) dup = img[q][0] == v[0] && img[q][1] == v[1] && img[q][2] == v[2];
+            if (!dup) {
+                img[n][0] = v[0];
+                img[n][1] = v[1];
+                img[n][2] = v[2];
+                ++n;
+            }
+        }
+    return n;
+}
+
+/* Wilson loops with off-axis spatial sides (Sec. III.D): for each vector
+ * r of vecs (nvec x 3) and 1 <= T <= Tmax, the mean over all translations x
+ * and all distinct cubic images r' of r of
+ *   (1/3) Re tr [ P_r'(x) S_t^T(x + r') P_r'(x + T t)^dag S_t^T(x)^dag ],
+ * P the path product above.  out[v * Tmax + T - 1]; sums in fixed chunks. */
+void orc_wilson_loops_offaxis(const int* dims, const cplx* U, const int* vecs, int nvec, int Tmax, double* out) {
+    geom g = make_geom(dims);
+    for (int v = 0; v < nvec; ++v) {
+        int img[48][3];
+        const int ni = cubic_images(vecs + 3 * v, img);
+        double* part = calloc((size_t)NCHUNK * Tmax, sizeof(double));
+#pragma omp parallel for schedule(static)
+        for (int ch = 0; ch < NCHUNK; ++ch) {
+            const long x0 = g.vol * ch / NCHUNK, x1 = g.vol * (ch + 1) / NCHUNK;
+            for (long x = x0; x < x1; ++x)
+                for (int q = 0; q < ni; ++q) {
+                    cplx P[9], A[9], B[9], C[9], t1[9], t2[9], D[9];
+                    path_product(&g, U, x, img[q], P);
+                    long xr = x;
+                    for (int j = 0; j < 3; ++j) {
+                        for (int k = 0; k < abs(img[q][j]); ++k) xr = shift(&g, xr, j, img[q][j] > 0 ? 1 : -1);
+                    }
+                    for (int T = 1; T <= Tmax; ++T) {
+                        long xt = x;
+                        for (int k = 0; k < T; ++k) xt = shift(&g, xt, 3, 1);
+                        line_product(&g, U, xr, 3, T, A);
+                        path_product(&g, U, xt, img[q], B);
+                        line_product(&g, U, x, 3, T, C);
+                        m_mul(t1, P, A);
+                        m_mul_nd(t2, t1, B);
+                        m_mul_nd(D, t2, C);
+                        part[(size_t)ch * Tmax + (T - 1)] += creal(m_trace(D)) / 3.0;
+                    }
+                }
+        }
+        for (int T = 0; T < Tmax; ++T) {
+            double acc = 0;
+            for (int ch = 0; ch < NCHUNK; ++ch) acc += part[(size_t)ch * Tmax + T];
+            out[v * Tmax + T] = acc / ((double)ni * g.vol);
+        }
+        free(part);
+    }
+}
+
 /* ------------------------------------------------------------------ */
 /* Gradient of R with respect to the gauge transform                    */
 /* ------------------------------------------------------------------ */

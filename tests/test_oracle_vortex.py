@@ -121,3 +121,51 @@ def test_wilson_on_center_field_counts_flux():
                     n -= np.roll(g[..., 3], -k, axis=ax[3])
                 vals.append(np.where(n % 3 == 0, 1.0, -0.5).mean())
             assert abs(W[R - 1, T - 1] - np.mean(vals)) < 1e-14
+
+
+OFFAXIS = [(1, 1, 0), (2, 1, 0), (1, 1, 1), (2, 0, 0)]
+
+
+def test_offaxis_reduces_to_onaxis():
+    """An on-axis vector averaged over its 6 cubic images (+-x, +-y, +-z)
+    equals the on-axis loops along +x, +y, +z (a -i loop is a +i loop
+    translated and traversed backwards: same real trace)."""
+    U = synth.make_field(DIMS, 0.5, 21)
+    W = oracle.wilson_loops(DIMS, U, 3, 4)
+    Wo = oracle.wilson_loops_offaxis(DIMS, U, [(1, 0, 0), (2, 0, 0), (3, 0, 0)], 4)
+    assert np.abs(W - Wo).max() < 1e-14
+
+
+def test_offaxis_closed_loops_gauge_invariant_and_pure_gauge():
+    U = synth.make_field(DIMS, 0.5, 22)
+    Om = synth.random_gauge(DIMS, 23)
+    W0 = oracle.wilson_loops_offaxis(DIMS, U, OFFAXIS, 3)
+    W1 = oracle.wilson_loops_offaxis(DIMS, oracle.apply_gauge(DIMS, U, Om), OFFAXIS, 3)
+    assert np.abs(W0 - W1).max() < 1e-13
+    P = synth.make_field(DIMS, 0.0, 24)
+    assert np.abs(oracle.wilson_loops_offaxis(DIMS, P, OFFAXIS, 3) - 1.0).max() < 1e-13
+
+
+def test_offaxis_constant_abelian_flux_closed_form():
+    """Spatial links diag(e^{i F_k t}), U_t = 1: the spatial path product is
+    diag(e^{i F_k t s}) with s the signed sum of the vector's components, so a
+    loop is diag(e^{-i F_k T s}); W is the mean of (1/3) sum_k cos(F_k T s)
+    over the distinct images of the vector (enumerated here with itertools)."""
+    import itertools
+
+    nt = DIMS[3]
+    F = 2 * np.pi * np.array([1, 2, -3]) / nt
+    V = int(np.prod(DIMS))
+    t = (np.arange(V) // (DIMS[0] * DIMS[1] * DIMS[2])).astype(float)
+    U = np.zeros((V, 4, 3, 3), np.complex128)
+    for mu in range(3):
+        for k in range(3):
+            U[:, mu, k, k] = np.exp(1j * F[k] * t)
+    U[:, 3] = np.eye(3)
+    W = oracle.wilson_loops_offaxis(DIMS, U, OFFAXIS, 4)
+    for v, r in enumerate(OFFAXIS):
+        imgs = {tuple(sg * c for sg, c in zip(signs, perm))
+                for perm in itertools.permutations(r) for signs in itertools.product((1, -1), repeat=3)}
+        for T in range(1, 5):
+            ref = np.mean([np.cos(F * T * sum(im)).sum() / 3.0 for im in imgs])
+            assert abs(W[v, T - 1] - ref) < 1e-14
