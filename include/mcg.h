@@ -236,6 +236,24 @@ int mcg_vortex_remove(const void* U, const int8_t* Z, void* U_removed, void* U_c
 int mcg_wilson_loops(const void* U, const mcg_lattice* lat, int Rmax, int Tmax, double* W_out, cudaStream_t stream);
 
 /*
+ * Wilson loops with off-axis spatial sides (Sec. III.D, which uses off-axis
+ * paths for non-integer separations without fixing them; this library's
+ * reading): for each integer vector r of `vectors` (host, nvec x 3) and
+ * 1 <= T <= Tmax (at most N_t), the mean over all translations x and all
+ * distinct images r' of r under axis permutations and sign flips of
+ *   (1/3) Re tr [ P_r'(x) S_t^T(x + r') P_r'(x + T t)^dag S_t^T(x)^dag ],
+ * P_r'(x) the product of links along the lattice path from x to x + r' that
+ * steps, at step k of L = |r'0|+|r'1|+|r'2|, along the axis j with the largest
+ * deficit k |r'_j| / L - n_j (n_j: steps taken along j; ties to the lowest
+ * axis), backward steps contributing U^dag; on-axis r gives mcg_wilson_loops.
+ * Each |r_j| must be below the smallest spatial extent, 1 <= L <= 64.
+ * W_out: host, nfields x nvec x Tmax doubles.  Uses the same scratch as
+ * mcg_wilson_loops.  Synchronises.
+ */
+int mcg_wilson_loops_offaxis(const void* U, const mcg_lattice* lat, const int* vectors, int nvec, int Tmax,
+                             double* W_out, cudaStream_t stream);
+
+/*
  * The preconditioning pipeline of Sec. II.B for every field of the batch:
  * S = smear(U, rho, eps, nsmear); fix S (transform Omega_1 from identity);
  * apply Omega_1 (re-unitarised) to the original U; fix that field (transform

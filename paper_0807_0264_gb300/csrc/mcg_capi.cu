@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -499,6 +500,27 @@ int mcg_wilson_loops(const void* U, const mcg_lattice* lat, int Rmax, int Tmax, 
     if (Rmax < 1 || Rmax > nmin || Tmax < 1 || Tmax > g.n[3])
         return fail(MCG_BAD_ARG, "need 1 <= Rmax <= smallest spatial extent and 1 <= Tmax <= N_t");
     return compute_wilson_loops(U, lat->precision, g, lat->nfields, Rmax, Tmax, W_out, stream);
+}
+
+int mcg_wilson_loops_offaxis(const void* U, const mcg_lattice* lat, const int* vectors, int nvec, int Tmax,
+                             double* W_out, cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if (!U || !vectors || !W_out) return fail(MCG_BAD_ARG, "null pointer");
+    if (nvec < 1) return fail(MCG_BAD_ARG, "nvec must be >= 1");
+    if (Tmax < 1 || Tmax > g.n[3]) return fail(MCG_BAD_ARG, "need 1 <= Tmax <= N_t");
+    const int nmin = std::min(g.n[0], std::min(g.n[1], g.n[2]));
+    for (int v = 0; v < nvec; ++v) {
+        int len = 0;
+        for (int j = 0; j < 3; ++j) {
+            const int c = std::abs(vectors[3 * v + j]);
+            if (c >= nmin) return fail(MCG_BAD_ARG, "each |component| must be below the smallest spatial extent");
+            len += c;
+        }
+        if (len < 1 || len > 64) return fail(MCG_BAD_ARG, "path length |r0|+|r1|+|r2| must be in 1..64");
+    }
+    return compute_wilson_loops_offaxis(U, lat->precision, g, lat->nfields, vectors, nvec, Tmax, W_out, stream);
 }
 
 int mcg_precondition_fix(void* U, void* G, int8_t* Z, const mcg_lattice* lat, const mcg_params* params, double rho,

@@ -120,6 +120,8 @@ int launch_vortex_remove(const void* U, const int8_t* Z, void* Ur, void* Zl, int
                          cudaStream_t st);
 int compute_wilson_loops(const void* U, int prec, const Geom& g, int nfields, int Rmax, int Tmax, double* W_host,
                          cudaStream_t st);
+int compute_wilson_loops_offaxis(const void* U, int prec, const Geom& g, int nfields, const int* vecs, int nvec,
+                                 int Tmax, double* W_host, cudaStream_t st);
 
 // ---- smearing (mcg_smear.cu) ------------------------------------------------
 int run_smear(const void* Uin, void* Uout, int prec, const Geom& g, int nfields, double rho, double eps, int n,

@@ -87,6 +87,7 @@ def _load() -> ctypes.CDLL:
         "mcg_center_project": ([P, P, P, L, P], I),
         "mcg_vortex_remove": ([P, P, P, P, L, P], I),
         "mcg_wilson_loops": ([P, L, I, I, P, P], I),
+        "mcg_wilson_loops_offaxis": ([P, L, P, I, I, P, P], I),
         "mcg_precondition_fix": ([P, P, P, L, PR, D, D, I, I, ctypes.POINTER(mcg_precond_result), P], I),
         "mcg_precondition_levels": ([P, P, P, P, L, PR, D, D, ctypes.POINTER(ctypes.c_int), I, I,
                                      ctypes.POINTER(mcg_precond_result), P], I),
@@ -119,7 +120,8 @@ EXPORTS = ("mcg_version", "mcg_last_error", "mcg_release", "mcg_pack_links", "mc
            "mcg_precondition_fix", "mcg_precondition_levels", "mcg_time_halfsweep", "mcg_kernel_launches",
            "mcg_plaquette_static", "mcg_set_sweep_block", "mcg_get_sweep_block", "mcg_fix_batch",
            "mcg_gribov_search", "mcg_smear_backward_step", "mcg_functional_matrix_grad", "mcg_grad_R",
-           "mcg_ascent_step", "mcg_vortex_remove", "mcg_wilson_loops")
+           "mcg_ascent_step", "mcg_vortex_remove", "mcg_wilson_loops",
+           "mcg_wilson_loops_offaxis")
 
 
 def library() -> ctypes.CDLL:
@@ -383,6 +385,22 @@ def mcg_wilson_loops(U: torch.Tensor, dims, Rmax: int, Tmax: int, stream=None):
     _check("mcg_wilson_loops", _lib.mcg_wilson_loops(_ptr(U), lattice(dims, nf, precision_of(U)), int(Rmax), int(Tmax),
                                                      out, _stream(stream)))
     return np.ctypeslib.as_array(out).reshape(nf, Rmax, Tmax).copy()
+
+
+def mcg_wilson_loops_offaxis(U: torch.Tensor, dims, vectors, Tmax: int, stream=None):
+    """Wilson loops with (possibly off-axis) spatial side r for each integer
+    3-vector of `vectors`, averaged over translations and cubic images
+    (Sec. III.D); numpy array (nfields, len(vectors), Tmax)."""
+    import numpy as np
+
+    _need_cuda(U)
+    v = np.ascontiguousarray(np.asarray(vectors, dtype=np.int32).reshape(-1, 3))
+    nf, nv = U.shape[0], v.shape[0]
+    out = (ctypes.c_double * (nf * nv * Tmax))()
+    _check("mcg_wilson_loops_offaxis",
+           _lib.mcg_wilson_loops_offaxis(_ptr(U), lattice(dims, nf, precision_of(U)),
+                                         v.ctypes.data_as(ctypes.c_void_p), nv, int(Tmax), out, _stream(stream)))
+    return np.ctypeslib.as_array(out).reshape(nf, nv, Tmax).copy()
 
 
 def mcg_precondition_fix(U: torch.Tensor, G: torch.Tensor, dims, params: Params | None = None, rho: float = 0.1,
