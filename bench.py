@@ -426,13 +426,19 @@ def main():
         Ws = {name: mcg.mcg_wilson_loops(F, dims, *RT)[0] for name, F in
               (("full", Uf), ("vortex_removed", Ur), ("vortex_only", Zl))}
         q2.record(stream)
+        offaxis = [(1, 1, 0), (2, 1, 0), (2, 2, 0), (1, 1, 1), (2, 1, 1), (2, 2, 1)]
+        Wo = mcg.mcg_wilson_loops_offaxis(Uf, dims, offaxis, RT[1])[0]
+        q3 = torch.cuda.Event(enable_timing=True)
+        q3.record(stream)
         torch.cuda.synchronize(dev)
         vr_ms = q0.elapsed_time(q1)
         vr_bytes = 3 * V * 4 * 144 + V * 4  # read U and Z, write U' and Z (FP64 links)
         sec3d = {"field": "level 0 fixed field", "vortex_remove_ms": vr_ms,
                  "vortex_remove_GBps": vr_bytes / (vr_ms / 1e3) / 1e9,
                  "wilson_ms_3_fields": q1.elapsed_time(q2), "Rmax": RT[0], "Tmax": RT[1],
-                 "W_RxT_diag": {k: [float(w[i, i]) for i in range(RT[0])] for k, w in Ws.items()}}
+                 "W_RxT_diag": {k: [float(w[i, i]) for i in range(RT[0])] for k, w in Ws.items()},
+                 "offaxis_vectors": offaxis, "offaxis_ms": q2.elapsed_time(q3),
+                 "W_offaxis_T4": [float(Wo[v, 3]) for v in range(len(offaxis))]}
         del Ur, Zl
 
     # end to end through the public API: host canonical field in, results out
