@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 # (profiles/k_halfsweep_pair_f32_24x24x24x24.md, 24^4 scaled to the 160 000
 # sites of a 20^3 x 40 launch); reported only while the kernel source is the
 # one that was profiled
-TRAFFIC_FP32 = {"bytes_per_launch": 89.58e6, "source_sha256_prefix": "da559cdd24305473",
+TRAFFIC_FP32 = {"bytes_per_launch": 81.27e6, "source_sha256_prefix": "1678f2fc4b073ade",
                 "profile": "profiles/k_halfsweep_c12_f32_20x20x20x40.md"}
 
 METRIC = "MCG site-updates/s & time-to-ΔR<1e-10 at 20^3x40: batched/mixed vs plain FP64"

@@ -826,13 +826,13 @@ __device__ __noinline__ float4 solve_f32_fallback(float a00, float a01, float a0
     return make_float4(a[0], a[1], a[2], a[3]);
 }
 
-// Makes the compiler treat the site's links as redefined here (no code
+// Makes the compiler treat the forward links as redefined here (no code
 // emitted): values derived from them before this point (row-2 entries built
 // for A and b) are recomputed after it instead of being held in registers
 // across the local solve.
-__device__ __forceinline__ void c12_opaque(cplx<float> (&m)[8][6]) {
+__device__ __forceinline__ void c12_opaque(cplx<float> (&m)[4][6]) {
 #pragma unroll
-    for (int l = 0; l < 8; ++l)
+    for (int l = 0; l < 4; ++l)
 #pragma unroll
         for (int e = 0; e < 6; ++e) asm volatile("" : "+f"(m[l][e].x), "+f"(m[l][e].y));
 }
@@ -867,12 +867,32 @@ __device__ __forceinline__ void c12_left_update(cplx<float>* m, const float (&a)
     }
 }
 
+// Backward links U_mu(x - mu) of the site live in shared memory as compact
+// chunks, slot (l, q) of thread t at bst[(l*3 + q)*NT + t] (consecutive
+// threads, consecutive 16-byte words).
+template <int NT>
+__device__ __forceinline__ void bwd_load(const float4* bst, int l, cplx<float>* m) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float4 v = bst[(l * 3 + q) * NT + threadIdx.x];
+        m[2 * q] = mk(v.x, v.y);
+        m[2 * q + 1] = mk(v.z, v.w);
+    }
+}
+template <int NT>
+__device__ __forceinline__ void bwd_store(float4* bst, int l, const cplx<float>* m) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        bst[(l * 3 + q) * NT + threadIdx.x] = make_float4(m[2 * q].x, m[2 * q].y, m[2 * q + 1].x, m[2 * q + 1].y);
+}
+
 // One SU(2)-subgroup step (rows/columns P < Q, R the third index) on the
-// compact links m[0..3] (forward U_mu(x)) and m[4..7] (backward U_mu(x-mu)).
-// Writes the (over-relaxed) subgroup element to a_out for the update of W;
-// returns 1 if the local solve left the Newton path.
-template <int P, int Q, int R>
-__device__ __forceinline__ int c12_subgroup_step(cplx<float> (&m)[8][6], const float omega, float (&a)[4]) {
+// compact forward links m[0..3] (registers) and the compact backward links
+// in shared memory.  Writes the (over-relaxed) subgroup element to `a` for the
+// update of W; returns 1 if the local solve left the Newton path.
+template <int P, int Q, int R, int NT>
+__device__ __forceinline__ int c12_subgroup_step(cplx<float> (&m)[4][6], float4* bst, const float omega,
+                                                 float (&a)[4]) {
     float A[4][4], b[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -882,9 +902,12 @@ __device__ __forceinline__ int c12_subgroup_step(cplx<float> (&m)[8][6], const f
     }
 #pragma unroll
     for (int l = 0; l < 8; ++l) {
-        const cplx<float> m11 = c12_entry<P, P>(m[l]), m12 = c12_entry<P, Q>(m[l]);
-        const cplx<float> m21 = c12_entry<Q, P>(m[l]), m22 = c12_entry<Q, Q>(m[l]);
-        const cplx<float> cc = c12_entry<R, R>(m[l]);
+        cplx<float> mb[6];
+        if (l >= 4) bwd_load<NT>(bst, l - 4, mb);
+        const cplx<float>* M = l < 4 ? m[l] : mb;
+        const cplx<float> m11 = c12_entry<P, P>(M), m12 = c12_entry<P, Q>(M);
+        const cplx<float> m21 = c12_entry<Q, P>(M), m22 = c12_entry<Q, Q>(M);
+        const cplx<float> cc = c12_entry<R, R>(M);
         // tr(G M) = cc + w.a for a forward link; tr(M G^dag) = cc + w'.a for
         // a backward link, w' = w with the signs of w1..w3 flipped
         cplx<float> w[4];
@@ -908,17 +931,16 @@ __device__ __forceinline__ int c12_subgroup_step(cplx<float> (&m)[8][6], const f
 #pragma unroll
         for (int j = 0; j < k; ++j) A[k][j] = A[j][k];
     c12_opaque(m);
+    asm volatile("" ::: "memory");
     int fb = 0;
-    {
-        if (!kkt_newton_f32(A, b, a)) {
-            const float4 r = solve_f32_fallback(A[0][0], A[0][1], A[0][2], A[0][3], A[1][1], A[1][2], A[1][3],
-                                                A[2][2], A[2][3], A[3][3], b[0], b[1], b[2], b[3]);
-            a[0] = r.x;
-            a[1] = r.y;
-            a[2] = r.z;
-            a[3] = r.w;
-            fb = 1;
-        }
+    if (!kkt_newton_f32(A, b, a)) {
+        const float4 r = solve_f32_fallback(A[0][0], A[0][1], A[0][2], A[0][3], A[1][1], A[1][2], A[1][3], A[2][2],
+                                            A[2][3], A[3][3], b[0], b[1], b[2], b[3]);
+        a[0] = r.x;
+        a[1] = r.y;
+        a[2] = r.z;
+        a[3] = r.w;
+        fb = 1;
     }
     if (omega != 1.f) {
         // over-relaxation: a -> normalise((1 - omega) e0 + omega a)
@@ -936,25 +958,33 @@ __device__ __forceinline__ int c12_subgroup_step(cplx<float> (&m)[8][6], const f
     // backward links: columns P, Q of M G^dag, rows 0 and 1
     const cplx<float> g11 = mk(a[0], a[3]), g12 = mk(a[2], a[1]), g21 = mk(-a[2], a[1]), g22 = mk(a[0], -a[3]);
 #pragma unroll
-    for (int l = 4; l < 8; ++l) {
+    for (int l = 0; l < 4; ++l) {
+        cplx<float> mb[6];
+        bwd_load<NT>(bst, l, mb);
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
-            const cplx<float> xp = m[l][3 * i + P], xq = m[l][3 * i + Q];
-            m[l][3 * i + P] = cfmac(xq, g12, cmulc(xp, g11));
-            m[l][3 * i + Q] = cfmac(xq, g22, cmulc(xp, g21));
+            const cplx<float> xp = mb[3 * i + P], xq = mb[3 * i + Q];
+            mb[3 * i + P] = cfmac(xq, g12, cmulc(xp, g11));
+            mb[3 * i + Q] = cfmac(xq, g22, cmulc(xp, g21));
         }
+        bwd_store<NT>(bst, l, mb);
     }
+    asm volatile("" ::: "memory");
     return fb;
 }
 
-// One thread per site.  The 8 links are loaded straight into registers (24
-// 16-byte loads in flight at once); W(x), needed only after the three steps,
-// is staged into shared memory by cp.async meanwhile and updated at the end
-// with the three subgroup elements, which keeps its 12 registers free during
-// the solves.
+// One thread per site.  The 4 forward links are loaded straight into
+// registers (12 16-byte loads in flight); the 4 backward links and W are
+// staged into shared memory by cp.async meanwhile.  The backward links are
+// read and written there by each subgroup step; W, needed only after the
+// three steps, is updated at the end with the three subgroup elements.
+// Keeping half of the site's state out of registers removes most spills at
+// the 168-register budget of 3 blocks of 128 threads per SM.
 template <bool ACC, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_halfsweep_c12(SweepBatch bt, int parity) {
-    extern __shared__ float4 wstage[];  // 3 chunks x NT
+    extern __shared__ float4 c12_smem[];  // W: 3 chunks x NT, then backward links: 12 chunks x NT
+    float4* wstage = c12_smem;
+    float4* bst = c12_smem + 3 * NT;
     const int f = field_of_block(bt.desc, bt.nf, blockIdx.x);
     if (bt.state[f].done) return;  // block-uniform
     const FieldDesc fd = bt.desc[f];
@@ -966,50 +996,63 @@ __global__ void __launch_bounds__(NT, MINB) k_halfsweep_c12(SweepBatch bt, int p
     float rsum = 0.f;
     int fb = 0;
     if (s < g.vh) {
-        {
-            const float4* src = W + c12_gidx(g, parity, 0, s);
-#pragma unroll
-            for (int q = 0; q < 3; ++q) cp_async<16>(&wstage[q * NT + threadIdx.x], src + q * vh);
-            asm volatile("cp.async.commit_group;\n" ::: "memory");
-        }
         int c[4];
         eo_coords(g, parity, s, c);
         int sb[4];
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) sb[mu] = eo_neighbor(g, c, mu, -1);
-        cplx<float> m[8][6];
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            const float4* src = U + c12_lidx(g, mu, parity ^ 1, 0, sb[mu]);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) cp_async<16>(&bst[(mu * 3 + q) * NT + threadIdx.x], src + q * vh);
+        }
+        {
+            const float4* src = W + c12_gidx(g, parity, 0, s);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) cp_async<16>(&wstage[q * NT + threadIdx.x], src + q * vh);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        cplx<float> m[4][6];
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) c12_load(U + c12_lidx(g, mu, parity, 0, s), vh, m[mu]);
-#pragma unroll
-        for (int mu = 0; mu < 4; ++mu) c12_load(U + c12_lidx(g, mu, parity ^ 1, 0, sb[mu]), vh, m[4 + mu]);
+        cp_async_wait_all();
 
         const float omega = (float)bt.omega;
         float a01[4], a02[4], a12[4];
-        fb += c12_subgroup_step<0, 1, 2>(m, omega, a01);
-        fb += c12_subgroup_step<0, 2, 1>(m, omega, a02);
-        fb += c12_subgroup_step<1, 2, 0>(m, omega, a12);
+        fb += c12_subgroup_step<0, 1, 2, NT>(m, bst, omega, a01);
+        fb += c12_subgroup_step<0, 2, 1, NT>(m, bst, omega, a02);
+        fb += c12_subgroup_step<1, 2, 0, NT>(m, bst, omega, a12);
 
         // FP32 re-unitarisation every sweep: the 8 links in the odd half-sweep
         // (which touches every link once), W every half-sweep.  FP32 rounding
         // would otherwise inflate |tr U|^2 by ~1e-6 per sweep and swamp the
-        // convergence signal.
+        // convergence signal.  R: the site's 8 links (|tr|^2 <= 9 each) summed
+        // in FP32, widened once.
         if (ACC) {
 #pragma unroll
-            for (int l = 0; l < 8; ++l) c12_reunitarise(m[l]);
+            for (int l = 0; l < 4; ++l) c12_reunitarise(m[l]);
         }
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) c12_store(U + c12_lidx(g, mu, parity, 0, s), vh, m[mu]);
-#pragma unroll
-        for (int mu = 0; mu < 4; ++mu) c12_store(U + c12_lidx(g, mu, parity ^ 1, 0, sb[mu]), vh, m[4 + mu]);
         if (ACC) {
-            // the site's 8 links (|tr|^2 <= 9 each) summed in FP32, widened once
 #pragma unroll
-            for (int l = 0; l < 8; ++l) {
+            for (int l = 0; l < 4; ++l) {
                 const cplx<float> t = cadd(cadd(m[l][0], m[l][4]), row2_entry(m[l], 2));
                 rsum = fmaf(t.x, t.x, fmaf(t.y, t.y, rsum));
             }
         }
-        cp_async_wait_all();
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            cplx<float> mb[6];
+            bwd_load<NT>(bst, mu, mb);
+            if (ACC) {
+                c12_reunitarise(mb);
+                const cplx<float> t = cadd(cadd(mb[0], mb[4]), row2_entry(mb, 2));
+                rsum = fmaf(t.x, t.x, fmaf(t.y, t.y, rsum));
+            }
+            c12_store(U + c12_lidx(g, mu, parity ^ 1, 0, sb[mu]), vh, mb);
+        }
         cplx<float> w[6];
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
@@ -1170,8 +1213,9 @@ static int raise_smem(K kernel, size_t smem) {
 // shared memory of the FP64 kernel: 8 links + Omega per thread
 static size_t halfsweep_smem_f64(int nt) { return sizeof(cplx<double>) * 81 * nt; }
 
-// FP32 kernel: dynamic shared memory for the staged W (3 chunks per thread)
-static size_t halfsweep_smem_c12(int nt) { return sizeof(float4) * 3 * nt; }
+// FP32 kernel: dynamic shared memory for the staged W and backward links
+// (15 chunks per thread: 30 KB for 128 threads)
+static size_t halfsweep_smem_c12(int nt) { return sizeof(float4) * 15 * nt; }
 
 template <typename T>
 static int prepare_halfsweep(int nt) {
@@ -1186,6 +1230,26 @@ static int prepare_halfsweep(int nt) {
                 return rc;
         } else {
             if ((rc = raise_smem(k_halfsweep<T, false, 64>, smem)) || (rc = raise_smem(k_halfsweep<T, true, 64>, smem)))
+                return rc;
+        }
+        done[slot] = true;
+    } else {
+        static bool done[3] = {false, false, false};
+        const int slot = nt == 64 ? 0 : (nt == 128 ? 1 : 2);
+        if (done[slot]) return 0;
+        const size_t smem = halfsweep_smem_c12(nt);
+        int rc = 0;
+        if (nt == 256) {
+            if ((rc = raise_smem(k_halfsweep_c12<false, 256, 1>, smem)) ||
+                (rc = raise_smem(k_halfsweep_c12<true, 256, 1>, smem)))
+                return rc;
+        } else if (nt == 128) {
+            if ((rc = raise_smem(k_halfsweep_c12<false, 128, 3>, smem)) ||
+                (rc = raise_smem(k_halfsweep_c12<true, 128, 3>, smem)))
+                return rc;
+        } else {
+            if ((rc = raise_smem(k_halfsweep_c12<false, 64, 6>, smem)) ||
+                (rc = raise_smem(k_halfsweep_c12<true, 64, 6>, smem)))
                 return rc;
         }
         done[slot] = true;
