@@ -1,0 +1,39 @@
+"""The comparison of preconditioning levels across configurations (Tables 2
+and 3 of Sec. III) on the GPU: the per-configuration, per-level maxima and
+P-vortex counts of precondition_study equal the oracle's pipeline run level
+by level, and its tables equal the host statistics of the oracle's values."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0807_0264_gb300 import synth
+from paper_0807_0264_gb300.analysis import precondition_study, transition_tables
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def test_precondition_study_matches_oracle():
+    from paper_0807_0264_gb300 import mcg
+
+    dims = (4, 4, 4, 4)
+    levels = (0, 2, 4)
+    fields = [synth.make_field(dims, 0.9, seed) for seed in (31, 32, 33)]
+    dev = [mcg.mcg_pack_links(torch.from_numpy(U).unsqueeze(0).cuda(), dims) for U in fields]
+    p = mcg.Params(tol=1e-10, max_sweeps=1500)
+    st = precondition_study(dev, dims, levels, p, rho=0.1, eps=1.0, smear_precision=mcg.F64)
+    Vo, no = [], []
+    for U in fields:
+        row_v, row_n = [], []
+        for ns in levels:
+            o = oracle.precondition_and_fix(dims, U, rho=0.1, eps=1.0, nsmear=ns, tol=1e-10, max_sweeps=1500)
+            row_v.append(o["fixed"]["R_hist"][-1] / (36 * 256))
+            row_n.append(o["vortices"])
+        Vo.append(row_v)
+        no.append(row_n)
+    assert np.abs(np.array(st["V"]) - np.array(Vo)).max() < 1e-10
+    assert st["vortices"] == no
+    ref = transition_tables(Vo, no)
+    for k in ("fewer_vortices_pct", "higher_max_pct", "fewer_given_higher_pct", "vortex_reduction_pct"):
+        np.testing.assert_allclose(st["tables"][k], ref[k], equal_nan=True)
