@@ -27,10 +27,9 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# DRAM traffic of the dominant kernel per launch, from one ncu capture
-# (profiles/k_halfsweep_pair_f32_24x24x24x24.md, 24^4 scaled to the 160 000
-# sites of a 20^3 x 40 launch); reported only while the kernel source is the
-# one that was profiled
+# DRAM traffic of the dominant kernel per launch, from one ncu capture of a
+# full 20^3 x 40 launch (the profile named below); reported only while the
+# kernel source is the one that was profiled
 TRAFFIC_FP32 = {"bytes_per_launch": 81.27e6, "source_sha256_prefix": "1678f2fc4b073ade",
                 "profile": "profiles/k_halfsweep_c12_f32_20x20x20x40.md"}
 

@@ -91,7 +91,7 @@ int time_halfsweep(void* U, void* G, const Geom& g, int parity, int nreps, int f
                    cudaStream_t stream);
 
 // threads per block of the half-sweep kernel for a precision, and the sites
-// each block covers (FP32 uses two threads per site)
+// each block covers (one thread per site in both precisions)
 int sweep_block(int prec);
 void set_sweep_block(int prec, int nt);
 int sweep_sites_per_block(int prec);

@@ -485,7 +485,7 @@ def mcg_get_sweep_block(precision: int) -> int:
 
 def autotune_sweep_block(U: torch.Tensor, dims, reps: int = 10) -> dict:
     """Pick the half-sweep block size for U's precision (64/128 threads for
-    FP64, 64/128/256 for the pair-split FP32 kernel) by timing each on a
+    FP64, 64/128/256 for FP32; one thread per site) by timing each on a
     scratch copy of U (L2 flushed between launches); keeps the fastest for the
     process and returns the timings in ms per launch."""
     prec = precision_of(U)

@@ -7,8 +7,8 @@ Bars (from the method's arithmetic):
   - Z3 projection and vortex counts: bit-exact on identical links;
   - layout conversion, plaquette, R, gauge transforms: rounding level;
   - FP32 paths: errors stated per test from FP32 rounding (~1e-7 per op).
-Sizes span several thread blocks with a ragged tail (64 threads per block
-for FP64, 128 for FP32) plus the 2^4 degenerate lattice.
+Sizes span several thread blocks with a ragged tail (128 threads per block
+by default, both precisions) plus the 2^4 degenerate lattice.
 """
 import numpy as np
 import pytest
