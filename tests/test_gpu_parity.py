@@ -235,6 +235,22 @@ def test_fp32_sweep_close_to_fp64(mcg, dims):
     assert abs(res["R"][0] - r["R_hist"][-1]) < 1e-5 * r["R_hist"][-1]
 
 
+def test_fp32_fields_with_random_transform_stay_on_orbit(mcg):
+    """FP32 fields go through the compact working storage (rows 0 and 1 of
+    links and transform, row 2 rebuilt on the way out): from a random initial
+    transform G0 the result is still U0 transformed by the returned G, to FP32
+    precision, and both stay in SU(3)."""
+    dims = (6, 4, 4, 6)
+    U0 = synth.make_field(dims, 0.5, 15)
+    G0 = synth.random_gauge(dims, 16)
+    Uin = oracle.apply_gauge(dims, U0, G0)  # the field as transformed by G0
+    Ug, Gg, res = gpu_sweeps(mcg, Uin, G0, dims, 20, prec=1, reunit_every=0)
+    assert np.abs(oracle.apply_gauge(dims, U0, Gg) - Ug).max() < 5e-5
+    for M in (Ug.reshape(-1, 3, 3), Gg.reshape(-1, 3, 3)):
+        assert np.abs(np.einsum("...ji,...jk->...ik", M.conj(), M) - np.eye(3)).max() < 5e-6
+        assert np.abs(np.linalg.det(M) - 1).max() < 5e-6
+
+
 def test_fp32_R_monotone(mcg):
     dims = (6, 4, 4, 6)
     U = synth.make_field(dims, 0.5, 13)
