@@ -179,6 +179,18 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def reduce_over_ranks(dist, x: float, op: str, device) -> float:
+    """MAX or SUM of a scalar over the ranks of the default process group
+    (identity without one)."""
+    if not dist:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def config_of(args, form):
     d = tuple(args.dims)
     return {"workload": f"Sec. II.B preconditioned MCG, {d[0]}x{d[1]}x{d[2]}x{d[3]} SU(3), stout rho={RHO} "
@@ -280,18 +292,10 @@ def main():
         torch.cuda.synchronize(dev)
 
     def max_over_ranks(x: float) -> float:
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_over_ranks(dist, x, "max", dev)
 
     def sum_over_ranks(x: float) -> float:
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+        return reduce_over_ranks(dist, x, "sum", dev)
 
     for _ in range(args.warmup):
         res = step(mixed, mcg.F32)
