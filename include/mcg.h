@@ -88,6 +88,12 @@ typedef struct {
                        /* applies normalise((1-omega) + omega a) instead of a.  */
                        /* Not part of the paper's method; FP64 sweeps always    */
                        /* use the plain relaxation.                             */
+    int fp64_solve32;  /* FP64 sweeps: 0 = the local 4x4 problem is solved to   */
+                       /* FP64 precision (default); 1 = it is built and solved  */
+                       /* in FP32 and only the solution is normalised and       */
+                       /* applied in FP64 (G stays unitary, the field stays on  */
+                       /* its gauge orbit, R and the stop rule stay FP64; each  */
+                       /* site lands within ~1e-7 of its exact local maximum).  */
 } mcg_params;
 
 /* One field of a heterogeneous batch: device pointers to its links and its

@@ -178,6 +178,7 @@ static int check_params(const mcg_params* p) {
     if (p->reunit_every < 0 || p->fp32_sweeps < 0) return fail(MCG_BAD_ARG, "negative schedule parameter");
     if (p->fp32_sweeps > 0 && !(p->fp32_overrelax > 0.0 && p->fp32_overrelax < 2.0))
         return fail(MCG_BAD_ARG, "fp32_overrelax must be in (0, 2)");
+    if (p->fp64_solve32 != 0 && p->fp64_solve32 != 1) return fail(MCG_BAD_ARG, "fp64_solve32 must be 0 or 1");
     if (p->fp32_sweeps > 0 && (p->fp32_window < 1 || p->fp32_window > 31))
         return fail(MCG_BAD_ARG, "fp32_window must be in 1..31");
     if (!(p->tol == p->tol)) return fail(MCG_BAD_ARG, "tol is NaN");
@@ -267,7 +268,7 @@ static int fix_fields(const std::vector<FieldSpec>& fs, int prec, const mcg_para
             fds[f].norm = 1.0 / (9.0 * 8.0 * fs[f].g.vh);
         }
         rc = run_fix_phase<double>(fds, d_state, h_state, d_hist, hist_len, prm->tol, 1, 1.0, prm->reunit_every,
-                                   prm->max_sweeps, prm->check_every, fresh, st);
+                                   prm->max_sweeps, prm->check_every, fresh, st, prm->fp64_solve32 != 0);
     } else {
         // FP32 fields: compact copies in, full layout (row 2 rebuilt) out
         std::vector<FieldDesc> fds;

@@ -71,6 +71,7 @@ struct SweepBatch {
     int window;  // stop when the dV_U averaged over `window` sweeps < tol
     int reunit_every;
     double omega;  // over-relaxation parameter (1: plain relaxation)
+    int solve32;   // FP64 sweeps: local problem built and solved in FP32
 };
 
 // Run MCG relaxation on a batch (all fields same precision T) until every
@@ -80,7 +81,7 @@ struct SweepBatch {
 template <typename T>
 int run_fix_phase(const std::vector<FieldDesc>& fields, FieldState* d_state, FieldState* h_state, double* d_hist,
                   int hist_len, double tol, int window, double omega, int reunit_every, int abs_cap,
-                  int check_every, bool fresh, cudaStream_t stream);
+                  int check_every, bool fresh, cudaStream_t stream, bool solve32 = false);
 
 // Time `nreps` launches of one half-sweep kernel (parity 1 includes the fused
 // R reduction) on a single field, each bracketed by CUDA events on `stream`;

@@ -537,203 +537,6 @@ struct Solver<double> {
     }
 };
 
-// ---------------------------------------------------------------------------
-// link storage for one site's 8 links: shared memory, entry-major so that the
-// threads of a warp touch consecutive addresses (conflict-free)
-// ---------------------------------------------------------------------------
-template <typename T, int NT>
-struct SmemLinks {
-    cplx<T>* base;
-    __device__ __forceinline__ cplx<T>& operator()(int l, int e) { return base[(l * 9 + e) * NT + threadIdx.x]; }
-};
-
-// One SU(2)-subgroup step (subgroup rows/columns P, Q; R the third index) on
-// the 8 links in shared memory (l < 4: forward U_l(x), 4 <= l < 8: backward
-// U_{l-4}(x - l)) and Omega(x) (slot 8).  Returns 1 if the local solve left
-// the fast path.
-template <typename T, typename L>
-__device__ __forceinline__ int subgroup_step(L& lk, const int P, const int Q, const int R, const T omega) {
-    T A[4][4], b[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        b[i] = T(0);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) A[i][j] = T(0);
-    }
-    const int ePP = 3 * P + P, ePQ = 3 * P + Q, eQP = 3 * Q + P, eQQ = 3 * Q + Q, eRR = 3 * R + R;
-#pragma unroll
-    for (int l = 0; l < 8; ++l) {
-        const cplx<T> m11 = lk(l, ePP), m12 = lk(l, ePQ), m21 = lk(l, eQP), m22 = lk(l, eQQ);
-        const cplx<T> c = lk(l, eRR);
-        cplx<T> w[4];
-        w[0] = cadd(m11, m22);
-        w[1] = mk(-(m21.y + m12.y), m21.x + m12.x);  // i (m21 + m12)
-        w[2] = csub(m21, m12);
-        w[3] = mk(-(m11.y - m22.y), m11.x - m22.x);  // i (m11 - m22)
-        if (l >= 4) {
-#pragma unroll
-            for (int k = 1; k < 4; ++k) w[k] = mk(-w[k].x, -w[k].y);
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            b[k] = fma(c.x, w[k].x, fma(c.y, w[k].y, b[k]));
-#pragma unroll
-            for (int j = k; j < 4; ++j) A[k][j] = fma(w[k].x, w[j].x, fma(w[k].y, w[j].y, A[k][j]));
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int j = 0; j < k; ++j) A[k][j] = A[j][k];
-    T a[4];
-    asm volatile("" ::: "memory");
-    const int fb = Solver<T>::solve(A, b, a);
-    if (omega != T(1)) {
-        // over-relaxation: a -> normalise((1 - omega) e0 + omega a)
-        a[0] = (T(1) - omega) + omega * a[0];
-        a[1] *= omega;
-        a[2] *= omega;
-        a[3] *= omega;
-        const T inv = rsqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) a[k] *= inv;
-    }
-    const cplx<T> g11 = mk(a[0], a[3]), g12 = mk(a[2], a[1]), g21 = mk(-a[2], a[1]), g22 = mk(a[0], -a[3]);
-#pragma unroll 1
-    for (int l = 0; l < 9; ++l) {
-        if (l < 4 || l == 8) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {  // rows P, Q of G U (and of G Omega)
-                const cplx<T> xp = lk(l, 3 * P + k), xq = lk(l, 3 * Q + k);
-                lk(l, 3 * P + k) = cfma(g12, xq, cmul(g11, xp));
-                lk(l, 3 * Q + k) = cfma(g22, xq, cmul(g21, xp));
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {  // columns P, Q of U G^dag
-                const cplx<T> xp = lk(l, 3 * k + P), xq = lk(l, 3 * k + Q);
-                lk(l, 3 * k + P) = cfmac(xq, g12, cmulc(xp, g11));
-                lk(l, 3 * k + Q) = cfmac(xq, g22, cmulc(xp, g21));
-            }
-        }
-    }
-    return fb;
-}
-
-__device__ __forceinline__ int field_of_block(const FieldDesc* __restrict__ d, int nf, int b) {
-    int lo = 0, hi = nf - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (d[mid].blk0 <= b)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
-
-// ---------------------------------------------------------------------------
-// kernels
-// ---------------------------------------------------------------------------
-// Shared memory per thread: 8 links + Omega (81 complex): 41.5 KB for 64 FP32
-// threads (5 blocks per SM), 83 KB for 128 FP32 or 64 FP64 threads (2 per SM).
-template <typename T, bool ACC, int NT>
-__global__ void __launch_bounds__(NT, 2) k_halfsweep(SweepBatch bt, int parity) {
-    const int f = field_of_block(bt.desc, bt.nf, blockIdx.x);
-    if (bt.state[f].done) return;  // block-uniform
-    const FieldDesc fd = bt.desc[f];
-    const Geom g = fd.geo;
-    cplx<T>* __restrict__ U = reinterpret_cast<cplx<T>*>(fd.U);
-    cplx<T>* __restrict__ G = reinterpret_cast<cplx<T>*>(fd.G);
-    const int s = (blockIdx.x - fd.blk0) * NT + threadIdx.x;
-    const bool active = s < g.vh;
-
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SmemLinks<T, NT> lk;
-    lk.base = reinterpret_cast<cplx<T>*>(smem_raw);
-
-    double rsum = 0.0;
-    int fb = 0;
-    if (active) {
-        int c[4];
-        eo_coords(g, parity, s, c);
-        int sb[4];
-#pragma unroll
-        for (int mu = 0; mu < 4; ++mu) sb[mu] = eo_neighbor(g, c, mu, -1);
-        // stage the 8 links and Omega in shared memory without passing
-        // through registers
-#pragma unroll
-        for (int mu = 0; mu < 4; ++mu) {
-            const cplx<T>* src = U + lidx(g, mu, parity, 0, s);
-#pragma unroll 1
-            for (int e = 0; e < 9; ++e) cp_async<sizeof(cplx<T>)>(&lk(mu, e), src + (size_t)e * g.vh);
-        }
-#pragma unroll
-        for (int mu = 0; mu < 4; ++mu) {
-            const cplx<T>* src = U + lidx(g, mu, parity ^ 1, 0, sb[mu]);
-#pragma unroll 1
-            for (int e = 0; e < 9; ++e) cp_async<sizeof(cplx<T>)>(&lk(4 + mu, e), src + (size_t)e * g.vh);
-        }
-#pragma unroll
-        for (int e = 0; e < 9; ++e) cp_async<sizeof(cplx<T>)>(&lk(8, e), &G[gidx(g, parity, e, s)]);
-        cp_async_wait_all();
-
-        // subgroups (0,1), (0,2), (1,2) in turn; compiler barriers keep the
-        // links in shared memory between the phases of the update
-        const T omega = (T)bt.omega;
-#pragma unroll 1
-        for (int sg = 0; sg < 3; ++sg) {
-            const int P = sg == 2 ? 1 : 0, Q = sg == 0 ? 1 : 2;
-            fb += subgroup_step<T>(lk, P, Q, 3 - P - Q, omega);
-            asm volatile("" ::: "memory");
-        }
-
-#pragma unroll
-        for (int mu = 0; mu < 4; ++mu) {
-            cplx<T>* dst = U + lidx(g, mu, parity, 0, s);
-#pragma unroll 1
-            for (int e = 0; e < 9; ++e) dst[(size_t)e * g.vh] = lk(mu, e);
-        }
-#pragma unroll
-        for (int mu = 0; mu < 4; ++mu) {
-            cplx<T>* dst = U + lidx(g, mu, parity ^ 1, 0, sb[mu]);
-#pragma unroll 1
-            for (int e = 0; e < 9; ++e) dst[(size_t)e * g.vh] = lk(4 + mu, e);
-        }
-#pragma unroll
-        for (int e = 0; e < 9; ++e) G[gidx(g, parity, e, s)] = lk(8, e);
-        if (ACC) {
-#pragma unroll
-            for (int l = 0; l < 8; ++l) {
-                const T tr = lk(l, 0).x + lk(l, 4).x + lk(l, 8).x;
-                const T ti = lk(l, 0).y + lk(l, 4).y + lk(l, 8).y;
-                rsum += (double)tr * (double)tr + (double)ti * (double)ti;
-            }
-        }
-    }
-    __shared__ double red[NT / 32];
-    if (ACC) {
-        const double tot = block_sum(rsum, red);
-        if (threadIdx.x == 0) bt.partial[blockIdx.x] = tot;
-    }
-    {
-        // count local solves that left the fast path (diagnostic)
-        const int w = __reduce_add_sync(0xffffffffu, fb);
-        if ((threadIdx.x & 31) == 0 && w) atomicAdd(&bt.state[f].fallbacks, w);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// FP32 half-sweep on the compact storage: one thread per site, the site's
-// nine matrices (forward links U_mu(x), backward links U_mu(x - mu), W(x)) in
-// registers as their rows 0 and 1 (108 floats), the three subgroup steps
-// unrolled with compile-time indices.  Row-2 entries are rebuilt where a step
-// needs them; G acting on rows (P, 2) of a forward link changes row P only in
-// the stored part (row 2 stays implied), and M G^dag acts on each row of a
-// backward link separately.  No shared memory: the loads of all nine matrices
-// are in flight at once, straight into registers.
-// ---------------------------------------------------------------------------
-
 // Newton solve of the FP32 sweep.  The KKT system (mu - A) a = b, |a| = 1 is
 // iterated from a = e0 (the current links) in the form
 //   u = (mu - A)^-1 b,  y = (mu - A)^-1 a,
@@ -825,6 +628,267 @@ __device__ __noinline__ float4 solve_f32_fallback(float a00, float a01, float a0
     trs_from_eigen<float>(S, V, b, a, mu);
     return make_float4(a[0], a[1], a[2], a[3]);
 }
+
+// ---------------------------------------------------------------------------
+// link storage for one site's 8 links: shared memory, entry-major so that the
+// threads of a warp touch consecutive addresses (conflict-free)
+// ---------------------------------------------------------------------------
+template <typename T, int NT>
+struct SmemLinks {
+    cplx<T>* base;
+    __device__ __forceinline__ cplx<T>& operator()(int l, int e) { return base[(l * 9 + e) * NT + threadIdx.x]; }
+};
+
+// One SU(2)-subgroup step (subgroup rows/columns P, Q; R the third index) on
+// the 8 links in shared memory (l < 4: forward U_l(x), 4 <= l < 8: backward
+// U_{l-4}(x - l)) and Omega(x) (slot 8).  Returns 1 if the local solve left
+// the fast path.
+// S32 (FP64 links only): (A, b) are built and the local problem solved in
+// FP32 (kkt_newton_f32, else the FP32 Jacobi path); the solution is
+// normalised in FP64 so that G stays unitary to FP64 precision, and G is
+// applied to the FP64 links as usual.
+template <typename T, bool S32, typename L>
+__device__ __forceinline__ int subgroup_step_s32(L& lk, const int P, const int Q, const int R, T (&a)[4]) {
+    float A[4][4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        b[i] = 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) A[i][j] = 0.f;
+    }
+    const int ePP = 3 * P + P, ePQ = 3 * P + Q, eQP = 3 * Q + P, eQQ = 3 * Q + Q, eRR = 3 * R + R;
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+        const cplx<T> d11 = lk(l, ePP), d12 = lk(l, ePQ), d21 = lk(l, eQP), d22 = lk(l, eQQ), dc = lk(l, eRR);
+        const cplx<float> m11 = mk((float)d11.x, (float)d11.y), m12 = mk((float)d12.x, (float)d12.y);
+        const cplx<float> m21 = mk((float)d21.x, (float)d21.y), m22 = mk((float)d22.x, (float)d22.y);
+        const cplx<float> c = mk((float)dc.x, (float)dc.y);
+        cplx<float> w[4];
+        w[0] = cadd(m11, m22);
+        w[1] = mk(-(m21.y + m12.y), m21.x + m12.x);
+        w[2] = csub(m21, m12);
+        w[3] = mk(-(m11.y - m22.y), m11.x - m22.x);
+        if (l >= 4) {
+#pragma unroll
+            for (int k = 1; k < 4; ++k) w[k] = mk(-w[k].x, -w[k].y);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            b[k] = fmaf(c.x, w[k].x, fmaf(c.y, w[k].y, b[k]));
+#pragma unroll
+            for (int j = k; j < 4; ++j) A[k][j] = fmaf(w[k].x, w[j].x, fmaf(w[k].y, w[j].y, A[k][j]));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int j = 0; j < k; ++j) A[k][j] = A[j][k];
+    float af[4];
+    int fb = 0;
+    if (!kkt_newton_f32(A, b, af)) {
+        const float4 r = solve_f32_fallback(A[0][0], A[0][1], A[0][2], A[0][3], A[1][1], A[1][2], A[1][3], A[2][2],
+                                            A[2][3], A[3][3], b[0], b[1], b[2], b[3]);
+        af[0] = r.x;
+        af[1] = r.y;
+        af[2] = r.z;
+        af[3] = r.w;
+        fb = 1;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a[k] = (T)af[k];
+    const T inv = rsqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a[k] *= inv;
+    return fb;
+}
+
+template <typename T, typename L, bool S32 = false>
+__device__ __forceinline__ int subgroup_step(L& lk, const int P, const int Q, const int R, const T omega) {
+    T a[4];
+    int fb;
+    if constexpr (S32) {
+        fb = subgroup_step_s32<T, S32>(lk, P, Q, R, a);
+    } else {
+        T A[4][4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            b[i] = T(0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) A[i][j] = T(0);
+        }
+        const int ePP = 3 * P + P, ePQ = 3 * P + Q, eQP = 3 * Q + P, eQQ = 3 * Q + Q, eRR = 3 * R + R;
+#pragma unroll
+        for (int l = 0; l < 8; ++l) {
+            const cplx<T> m11 = lk(l, ePP), m12 = lk(l, ePQ), m21 = lk(l, eQP), m22 = lk(l, eQQ);
+            const cplx<T> c = lk(l, eRR);
+            cplx<T> w[4];
+            w[0] = cadd(m11, m22);
+            w[1] = mk(-(m21.y + m12.y), m21.x + m12.x);  // i (m21 + m12)
+            w[2] = csub(m21, m12);
+            w[3] = mk(-(m11.y - m22.y), m11.x - m22.x);  // i (m11 - m22)
+            if (l >= 4) {
+#pragma unroll
+                for (int k = 1; k < 4; ++k) w[k] = mk(-w[k].x, -w[k].y);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                b[k] = fma(c.x, w[k].x, fma(c.y, w[k].y, b[k]));
+#pragma unroll
+                for (int j = k; j < 4; ++j) A[k][j] = fma(w[k].x, w[j].x, fma(w[k].y, w[j].y, A[k][j]));
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int j = 0; j < k; ++j) A[k][j] = A[j][k];
+        asm volatile("" ::: "memory");
+        fb = Solver<T>::solve(A, b, a);
+    }
+    if (omega != T(1)) {
+        // over-relaxation: a -> normalise((1 - omega) e0 + omega a)
+        a[0] = (T(1) - omega) + omega * a[0];
+        a[1] *= omega;
+        a[2] *= omega;
+        a[3] *= omega;
+        const T inv = rsqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a[k] *= inv;
+    }
+    const cplx<T> g11 = mk(a[0], a[3]), g12 = mk(a[2], a[1]), g21 = mk(-a[2], a[1]), g22 = mk(a[0], -a[3]);
+#pragma unroll 1
+    for (int l = 0; l < 9; ++l) {
+        if (l < 4 || l == 8) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {  // rows P, Q of G U (and of G Omega)
+                const cplx<T> xp = lk(l, 3 * P + k), xq = lk(l, 3 * Q + k);
+                lk(l, 3 * P + k) = cfma(g12, xq, cmul(g11, xp));
+                lk(l, 3 * Q + k) = cfma(g22, xq, cmul(g21, xp));
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {  // columns P, Q of U G^dag
+                const cplx<T> xp = lk(l, 3 * k + P), xq = lk(l, 3 * k + Q);
+                lk(l, 3 * k + P) = cfmac(xq, g12, cmulc(xp, g11));
+                lk(l, 3 * k + Q) = cfmac(xq, g22, cmulc(xp, g21));
+            }
+        }
+    }
+    return fb;
+}
+
+__device__ __forceinline__ int field_of_block(const FieldDesc* __restrict__ d, int nf, int b) {
+    int lo = 0, hi = nf - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (d[mid].blk0 <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+// Shared memory per thread: 8 links + Omega (81 complex): 41.5 KB for 64 FP32
+// threads (5 blocks per SM), 83 KB for 128 FP32 or 64 FP64 threads (2 per SM).
+template <typename T, bool ACC, int NT, bool S32 = false>
+__global__ void __launch_bounds__(NT, 2) k_halfsweep(SweepBatch bt, int parity) {
+    const int f = field_of_block(bt.desc, bt.nf, blockIdx.x);
+    if (bt.state[f].done) return;  // block-uniform
+    const FieldDesc fd = bt.desc[f];
+    const Geom g = fd.geo;
+    cplx<T>* __restrict__ U = reinterpret_cast<cplx<T>*>(fd.U);
+    cplx<T>* __restrict__ G = reinterpret_cast<cplx<T>*>(fd.G);
+    const int s = (blockIdx.x - fd.blk0) * NT + threadIdx.x;
+    const bool active = s < g.vh;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemLinks<T, NT> lk;
+    lk.base = reinterpret_cast<cplx<T>*>(smem_raw);
+
+    double rsum = 0.0;
+    int fb = 0;
+    if (active) {
+        int c[4];
+        eo_coords(g, parity, s, c);
+        int sb[4];
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) sb[mu] = eo_neighbor(g, c, mu, -1);
+        // stage the 8 links and Omega in shared memory without passing
+        // through registers
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            const cplx<T>* src = U + lidx(g, mu, parity, 0, s);
+#pragma unroll 1
+            for (int e = 0; e < 9; ++e) cp_async<sizeof(cplx<T>)>(&lk(mu, e), src + (size_t)e * g.vh);
+        }
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            const cplx<T>* src = U + lidx(g, mu, parity ^ 1, 0, sb[mu]);
+#pragma unroll 1
+            for (int e = 0; e < 9; ++e) cp_async<sizeof(cplx<T>)>(&lk(4 + mu, e), src + (size_t)e * g.vh);
+        }
+#pragma unroll
+        for (int e = 0; e < 9; ++e) cp_async<sizeof(cplx<T>)>(&lk(8, e), &G[gidx(g, parity, e, s)]);
+        cp_async_wait_all();
+
+        // subgroups (0,1), (0,2), (1,2) in turn; compiler barriers keep the
+        // links in shared memory between the phases of the update
+        const T omega = (T)bt.omega;
+#pragma unroll 1
+        for (int sg = 0; sg < 3; ++sg) {
+            const int P = sg == 2 ? 1 : 0, Q = sg == 0 ? 1 : 2;
+            fb += subgroup_step<T, SmemLinks<T, NT>, S32>(lk, P, Q, 3 - P - Q, omega);
+            asm volatile("" ::: "memory");
+        }
+
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            cplx<T>* dst = U + lidx(g, mu, parity, 0, s);
+#pragma unroll 1
+            for (int e = 0; e < 9; ++e) dst[(size_t)e * g.vh] = lk(mu, e);
+        }
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            cplx<T>* dst = U + lidx(g, mu, parity ^ 1, 0, sb[mu]);
+#pragma unroll 1
+            for (int e = 0; e < 9; ++e) dst[(size_t)e * g.vh] = lk(4 + mu, e);
+        }
+#pragma unroll
+        for (int e = 0; e < 9; ++e) G[gidx(g, parity, e, s)] = lk(8, e);
+        if (ACC) {
+#pragma unroll
+            for (int l = 0; l < 8; ++l) {
+                const T tr = lk(l, 0).x + lk(l, 4).x + lk(l, 8).x;
+                const T ti = lk(l, 0).y + lk(l, 4).y + lk(l, 8).y;
+                rsum += (double)tr * (double)tr + (double)ti * (double)ti;
+            }
+        }
+    }
+    __shared__ double red[NT / 32];
+    if (ACC) {
+        const double tot = block_sum(rsum, red);
+        if (threadIdx.x == 0) bt.partial[blockIdx.x] = tot;
+    }
+    {
+        // count local solves that left the fast path (diagnostic)
+        const int w = __reduce_add_sync(0xffffffffu, fb);
+        if ((threadIdx.x & 31) == 0 && w) atomicAdd(&bt.state[f].fallbacks, w);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 half-sweep on the compact storage: one thread per site, the site's
+// nine matrices (forward links U_mu(x), backward links U_mu(x - mu), W(x)) in
+// registers as their rows 0 and 1 (108 floats), the three subgroup steps
+// unrolled with compile-time indices.  Row-2 entries are rebuilt where a step
+// needs them; G acting on rows (P, 2) of a forward link changes row P only in
+// the stored part (row 2 stays implied), and M G^dag acts on each row of a
+// backward link separately.  No shared memory: the loads of all nine matrices
+// are in flight at once, straight into registers.
+// ---------------------------------------------------------------------------
 
 // Makes the compiler treat the forward links as redefined here (no code
 // emitted): values derived from them before this point (row-2 entries built
@@ -1226,10 +1290,14 @@ static int prepare_halfsweep(int nt) {
         const size_t smem = halfsweep_smem_f64(nt);
         int rc = 0;
         if (nt == 128) {
-            if ((rc = raise_smem(k_halfsweep<T, false, 128>, smem)) || (rc = raise_smem(k_halfsweep<T, true, 128>, smem)))
+            if ((rc = raise_smem(k_halfsweep<T, false, 128>, smem)) || (rc = raise_smem(k_halfsweep<T, true, 128>, smem)) ||
+                (rc = raise_smem(k_halfsweep<T, false, 128, true>, smem)) ||
+                (rc = raise_smem(k_halfsweep<T, true, 128, true>, smem)))
                 return rc;
         } else {
-            if ((rc = raise_smem(k_halfsweep<T, false, 64>, smem)) || (rc = raise_smem(k_halfsweep<T, true, 64>, smem)))
+            if ((rc = raise_smem(k_halfsweep<T, false, 64>, smem)) || (rc = raise_smem(k_halfsweep<T, true, 64>, smem)) ||
+                (rc = raise_smem(k_halfsweep<T, false, 64, true>, smem)) ||
+                (rc = raise_smem(k_halfsweep<T, true, 64, true>, smem)))
                 return rc;
         }
         done[slot] = true;
@@ -1263,16 +1331,18 @@ template <typename T>
 static void launch_halfsweep(int nt, bool acc, const SweepBatch& bt, int parity, int nblocks, cudaStream_t st) {
     if constexpr (sizeof(T) == 8) {
         const size_t smem = halfsweep_smem_f64(nt);
+        const bool s32 = bt.solve32 != 0;
         if (nt == 128) {
             if (acc)
-                k_halfsweep<T, true, 128><<<nblocks, 128, smem, st>>>(bt, parity);
+                (s32 ? k_halfsweep<T, true, 128, true> : k_halfsweep<T, true, 128>)<<<nblocks, 128, smem, st>>>(bt, parity);
             else
-                k_halfsweep<T, false, 128><<<nblocks, 128, smem, st>>>(bt, parity);
+                (s32 ? k_halfsweep<T, false, 128, true> : k_halfsweep<T, false, 128>)<<<nblocks, 128, smem, st>>>(bt,
+                                                                                                                parity);
         } else {
             if (acc)
-                k_halfsweep<T, true, 64><<<nblocks, 64, smem, st>>>(bt, parity);
+                (s32 ? k_halfsweep<T, true, 64, true> : k_halfsweep<T, true, 64>)<<<nblocks, 64, smem, st>>>(bt, parity);
             else
-                k_halfsweep<T, false, 64><<<nblocks, 64, smem, st>>>(bt, parity);
+                (s32 ? k_halfsweep<T, false, 64, true> : k_halfsweep<T, false, 64>)<<<nblocks, 64, smem, st>>>(bt, parity);
         }
     } else {
         const size_t smem = halfsweep_smem_c12(nt);
@@ -1310,7 +1380,7 @@ static int enqueue_sweep(const SweepBatch& bt, int nt, int spb, cudaStream_t st)
 template <typename T>
 int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, FieldState* h_state, double* d_hist,
                   int hist_len, double tol, int window, double omega, int reunit_every, int abs_cap,
-                  int check_every, bool fresh, cudaStream_t stream) {
+                  int check_every, bool fresh, cudaStream_t stream, bool solve32) {
     const int prec = sizeof(T) == 8 ? MCG_F64 : MCG_F32;
     const int NT = sweep_block(prec);
     const int SPB = sweep_sites_per_block(prec);
@@ -1361,6 +1431,7 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
     bt.window = std::max(1, std::min(window, kRing - 1));
     bt.reunit_every = reunit_every;
     bt.omega = omega;
+    bt.solve32 = solve32 ? 1 : 0;
 
     if ((rc = prepare_halfsweep<T>(NT))) return rc;
 
@@ -1454,6 +1525,7 @@ int time_halfsweep(void* U, void* G, const Geom& g, int parity, int nreps, int f
     bt.window = 1;
     bt.reunit_every = 0;
     bt.omega = 1.0;
+    bt.solve32 = 0;
     if ((rc = prepare_halfsweep<T>(NT))) return rc;
     cudaEvent_t e0, e1;
     MCG_CK(cudaEventCreate(&e0));
@@ -1488,8 +1560,8 @@ template int time_halfsweep<float>(void*, void*, const Geom&, int, int, int, flo
 template int time_halfsweep<double>(void*, void*, const Geom&, int, int, int, float*, cudaStream_t);
 
 template int run_fix_phase<float>(const std::vector<FieldDesc>&, FieldState*, FieldState*, double*, int, double,
-                                  int, double, int, int, int, bool, cudaStream_t);
+                                  int, double, int, int, int, bool, cudaStream_t, bool);
 template int run_fix_phase<double>(const std::vector<FieldDesc>&, FieldState*, FieldState*, double*, int, double,
-                                   int, double, int, int, int, bool, cudaStream_t);
+                                   int, double, int, int, int, bool, cudaStream_t, bool);
 
 }  // namespace mcg

@@ -42,7 +42,8 @@ class mcg_lattice(ctypes.Structure):
 class mcg_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_sweeps", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("reunit_every", ctypes.c_int), ("fp32_sweeps", ctypes.c_int), ("fp32_tol", ctypes.c_double),
-                ("fp32_window", ctypes.c_int), ("fp32_overrelax", ctypes.c_double)]
+                ("fp32_window", ctypes.c_int), ("fp32_overrelax", ctypes.c_double),
+                ("fp64_solve32", ctypes.c_int)]
 
 
 class mcg_field(ctypes.Structure):
@@ -146,10 +147,12 @@ class Params:
     fp32_tol: float = 1e-10
     fp32_window: int = 25
     fp32_overrelax: float = 1.0
+    fp64_solve32: int = 0
 
     def c(self) -> mcg_params:
         return mcg_params(self.tol, self.max_sweeps, self.check_every, self.reunit_every, self.fp32_sweeps,
-                          self.fp32_tol, self.fp32_window, self.fp32_overrelax)
+                          self.fp32_tol, self.fp32_window, self.fp32_overrelax,
+                          int(self.fp64_solve32))
 
 
 def lattice(dims, nfields: int = 1, precision: int = F64) -> mcg_lattice:

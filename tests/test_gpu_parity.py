@@ -313,6 +313,38 @@ def test_mixed_overrelaxed_converges_on_orbit(mcg):
     assert (r["R_hist"][1] - r["R_hist"][0]) / (36 * 4096) < 1e-10
 
 
+def test_fp64_solve32_sweep_near_exact_and_on_orbit(mcg):
+    """FP64 sweeps with the local problem built and solved in FP32
+    (fp64_solve32): each site lands within FP32 solve precision of the
+    oracle's exact maximiser, and since G is normalised and applied in FP64
+    the field stays on its gauge orbit and in SU(3) to FP64 precision."""
+    dims = (6, 4, 4, 6)
+    U = synth.make_field(dims, 0.5, 17)
+    r = oracle.fix(dims, U, None, tol=NEVER, max_sweeps=1, reunit_every=0)
+    Ud, Gd = pack(mcg, U, dims), mcg.identity_gauge(dims)
+    mcg.mcg_fix(Ud, Gd, dims, mcg.Params(tol=NEVER, max_sweeps=1, reunit_every=0, fp64_solve32=1))
+    Uf, Gf = unpack(mcg, Ud, dims), unpack_g(mcg, Gd, dims)
+    err = np.abs(Uf - r["U"])
+    assert np.quantile(err, 0.99) < 2e-4 and err.max() < 2e-3
+    assert np.abs(oracle.apply_gauge(dims, U, Gf) - Uf).max() < 1e-13
+    M = Gf.reshape(-1, 3, 3)
+    assert np.abs(np.einsum("...ji,...jk->...ik", M.conj(), M) - np.eye(3)).max() < 1e-14
+
+
+def test_mixed_with_fp64_solve32_converges_by_the_fp64_criterion(mcg):
+    dims = (8, 8, 8, 8)
+    U = synth.make_field(dims, synth.W_PLAQ_06, 1)
+    Ud, Gd = pack(mcg, U, dims), mcg.identity_gauge(dims)
+    res = mcg.mcg_fix(Ud, Gd, dims, mcg.Params(tol=1e-10, max_sweeps=3000, fp32_sweeps=3000, fp32_tol=5e-11,
+                                               fp32_overrelax=1.85, fp64_solve32=1))
+    assert res["converged"]
+    Uf, Gf = unpack(mcg, Ud, dims), unpack_g(mcg, Gd, dims)
+    assert np.abs(oracle.apply_gauge(dims, U, Gf) - Uf).max() < 1e-12
+    # the oracle's exact FP64 relaxation raises V_U by less than 1e-10 in one more sweep
+    r = oracle.fix(dims, Uf, Gf, tol=NEVER, max_sweeps=1, reunit_every=0)
+    assert (r["R_hist"][1] - r["R_hist"][0]) / (36 * 4096) < 1e-10
+
+
 def test_batched_fields_match_single(mcg):
     dims = (4, 4, 4, 4)
     Us = [synth.make_field(dims, 0.5, s) for s in (20, 21, 22)]
