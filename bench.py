@@ -412,6 +412,27 @@ def main():
     roof["kernel_ms"] = {"fp32_odd": t32, "fp32_even": t32_even, "fp64_odd_exact_solve": t64}
     roof["step_share_estimate"] = {"fp32": share32 / max(share32 + share64, 1e-9),
                                    "fp64": share64 / max(share32 + share64, 1e-9)}
+    # the same kernel inside a fix (no flush: each half-sweep's 138 MB working
+    # set exceeds the 129 MB L2): FP32-phase time of N2 - N1 sweeps on a copy
+    # of the warm field, both half-sweeps and the end-of-sweep kernel per sweep
+    def fp32_phase_ms(n):
+        Ui, Gi = U_warm.clone(), mcg.identity_gauge(dims, 1, mcg.F64, dev)
+        pr_ = mcg.Params(tol=1e300, max_sweeps=n + 1, check_every=25, fp32_sweeps=n, fp32_tol=-1e300,
+                         fp32_window=25, fp32_overrelax=OMEGA)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        mcg.mcg_fix(Ui, Gi, dims, pr_)
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        return a0.elapsed_time(a1)
+    n1, n2 = 100, 500
+    fp32_phase_ms(n1)
+    sweep_ms = (fp32_phase_ms(n2) - fp32_phase_ms(n1)) / (n2 - n1)
+    roof["in_situ"] = {"ms_per_sweep": sweep_ms, "ms_per_launch": sweep_ms / 2,
+                       "achieved": 2 * bytes32 / (sweep_ms / 1e3) / 1e9, "unit": "GB/s",
+                       "frac": 2 * bytes32 / (sweep_ms / 1e3) / 1e9 / 6780.0,
+                       "method": "FP32 sweeps inside a fix, L2 not flushed (working set 138 MB > 129 MB L2); the "
+                                 "end-of-sweep kernel counted in the sweep"}
 
     # Sec. III.D on the level-0 result: center decomposition (vortex-removed
     # and vortex-only fields) and on-axis Wilson loops of the three fields
