@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 # DRAM traffic of the dominant kernel per launch, from one ncu capture of a
 # full 20^3 x 40 launch (the profile named below); reported only while the
 # kernel source is the one that was profiled
-TRAFFIC_FP32 = {"bytes_per_launch": 81.27e6, "source_sha256_prefix": "1678f2fc4b073ade",
+TRAFFIC_FP32 = {"bytes_per_launch": 81.20e6, "source_sha256_prefix": "149c31522852fe50",
                 "profile": "profiles/k_halfsweep_c12_f32_20x20x20x40.md"}
 
 METRIC = "MCG site-updates/s & time-to-ΔR<1e-10 at 20^3x40: batched/mixed vs plain FP64"
@@ -263,7 +263,7 @@ def main():
     if args.profile_slice:
         # FP32 : FP64 sweeps 100 : 1 per fix, close to the full step's ratio
         sl = mcg.Params(tol=-1e300, max_sweeps=101, check_every=25, reunit_every=50, fp32_sweeps=100,
-                        fp32_tol=-1e300, fp32_window=25, fp32_overrelax=OMEGA)
+                        fp32_tol=-1e300, fp32_window=25, fp32_overrelax=OMEGA, fp64_solve32=1)
         mcg.mcg_set_sweep_block(mcg.F32, 128)
         mcg.mcg_set_sweep_block(mcg.F64, 128)
         torch.cuda.synchronize(dev)
