@@ -124,12 +124,13 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # CPU oracle (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
-def oracle_sample(U, dims, seconds: float):
+def oracle_sample(U, dims, seconds: float, threads: int | None = None):
     """Oracle MCG sweeps on the workload field (identity start), bounded to
-    about `seconds` of CPU work; returns (site-updates/s, sweeps, threads)."""
+    about `seconds` of CPU work, on `threads` host threads (default: all the
+    process may use); returns (site-updates/s, sweeps, threads)."""
     import oracle
 
-    cores = len(os.sched_getaffinity(0))
+    cores = threads or len(os.sched_getaffinity(0))
     oracle.set_threads(cores)
     V = 1
     for d in dims:
@@ -487,8 +488,10 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, n, cores = oracle_sample(U_host, dims, args.cpu_seconds)
+        v1, n1, _ = oracle_sample(U_host, dims, max(2.0, args.cpu_seconds / 4), threads=1)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{n} oracle FP64 MCG sweeps of the {dims[0]}x{dims[1]}x{dims[2]}x{dims[3]} workload field"}
+               "sample": f"{n} oracle FP64 MCG sweeps of the {dims[0]}x{dims[1]}x{dims[2]}x{dims[3]} workload field",
+               "one_core": {"value": v1, "sample": f"{n1} sweeps on 1 thread"}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
