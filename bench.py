@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--profile-slice", action="store_true",
                     help="one bench step with sweeps capped (FP32 100 + FP64 1 per fix, levels 0 and 4, block sizes "
                          "128): the same kernels and launch shapes in ~1000 launches, for an ncu launch list")
+    ap.add_argument("--gribov", action="store_true",
+                    help="the batched Gribov-copy search at full size instead of the main step: 16 x 12^4, "
+                         "16 x 16^3 x 32 and 16 x 20^3 x 40 configurations with 8 random initial transforms "
+                         "each (384 fields, 60.4 M sites), fields generated on the GPU; one JSON line")
     ap.add_argument("--profile-kernel", choices=["f32", "f64"],
                     help="time the FP32 (or FP64) half-sweep on the field after 300 FP32 sweeps (the regime the FP32 "
                          "phase runs in), odd then even sites, 3 launches each, L2 flushed: the launches for an ncu "
@@ -202,6 +206,114 @@ def config_of(args, form):
 
 
 # ---------------------------------------------------------------------------
+# batched Gribov-copy search at full size (--gribov)
+# ---------------------------------------------------------------------------
+def _haar_su3(n, gen, dev):
+    """n Haar-random SU(3) matrices on the GPU (QR of a complex Ginibre matrix,
+    phases of diag R divided out, determinant's cube root removed)."""
+    import torch
+
+    re = torch.randn((n, 3, 3), generator=gen, dtype=torch.float64, device=dev)
+    im = torch.randn((n, 3, 3), generator=gen, dtype=torch.float64, device=dev)
+    Q, Rm = torch.linalg.qr(torch.complex(re, im))
+    d = torch.diagonal(Rm, dim1=-2, dim2=-1)
+    Q = Q * (d / d.abs()).unsqueeze(-2)
+    det = torch.linalg.det(Q)
+    return Q / (det ** (1.0 / 3.0)).reshape(n, 1, 1)
+
+
+def _gpu_field(dims, w, seed, dev):
+    """The synthetic field g(x) exp(i w theta.lambda/2) g(x+mu)^dag of the
+    workload, generated with torch on the GPU (canonical layout, (1, V, 4, 3, 3))."""
+    import torch
+
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(seed))
+    nx, ny, nz, nt = dims
+    V = nx * ny * nz * nt
+    g = _haar_su3(V, gen, dev).reshape(nt, nz, ny, nx, 3, 3)
+    lam = torch.zeros((8, 3, 3), dtype=torch.complex128, device=dev)
+    lam[0, 0, 1] = lam[0, 1, 0] = 1
+    lam[1, 0, 1], lam[1, 1, 0] = -1j, 1j
+    lam[2, 0, 0], lam[2, 1, 1] = 1, -1
+    lam[3, 0, 2] = lam[3, 2, 0] = 1
+    lam[4, 0, 2], lam[4, 2, 0] = -1j, 1j
+    lam[5, 1, 2] = lam[5, 2, 1] = 1
+    lam[6, 1, 2], lam[6, 2, 1] = -1j, 1j
+    lam[7, 0, 0] = lam[7, 1, 1] = 1 / 3 ** 0.5
+    lam[7, 2, 2] = -2 / 3 ** 0.5
+    links = []
+    for mu, ax in zip(range(4), (3, 2, 1, 0)):
+        th = torch.randn((nt, nz, ny, nx, 8), generator=gen, dtype=torch.float64, device=dev).to(torch.complex128)
+        H = torch.einsum("...a,aij->...ij", th, lam) * (0.5 * w)
+        E = torch.linalg.matrix_exp(1j * H)
+        gs = torch.roll(g, shifts=-1, dims=ax)
+        links.append(g @ E @ gs.conj().transpose(-1, -2))
+    return torch.stack(links, dim=4).reshape(1, V, 4, 3, 3).contiguous()
+
+
+def run_gribov(args, mcg, dev, rank):
+    import torch
+
+    sizes = [((12, 12, 12, 12), 16), ((16, 16, 16, 32), 16), ((20, 20, 20, 40), 16)]
+    ncopy = 8
+    t_gen = time.perf_counter()
+    Us, Gs, dims_list, cfg = [], [], [], []
+    c = 0
+    for dims, nconf in sizes:
+        V = dims[0] * dims[1] * dims[2] * dims[3]
+        for _ in range(nconf):
+            U = mcg.mcg_pack_links(_gpu_field(dims, synth_w(), c, dev), dims)
+            for k in range(ncopy):
+                gen = torch.Generator(device=dev)
+                gen.manual_seed(1000 + ncopy * c + k)
+                Gc = mcg.mcg_pack_gauge(_haar_su3(V, gen, dev).unsqueeze(0), dims)
+                Us.append(U.clone())
+                Gs.append(Gc)
+                dims_list.append(dims)
+                cfg.append(c)
+            del U
+            c += 1
+    torch.cuda.synchronize(dev)
+    t_gen = time.perf_counter() - t_gen
+    nconf_tot = c
+    p = mcg.Params(tol=1e-10, max_sweeps=20000, check_every=25, reunit_every=50, fp32_sweeps=20000, fp32_tol=5e-11,
+                   fp32_window=25, fp32_overrelax=OMEGA, fp64_solve32=1)
+    tune = mcg.autotune_schedule(Us, dims_list, p, trial_sweeps=20, chunks=(25, 50))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = mcg.mcg_kernel_launches()
+    e0.record()
+    res = mcg.mcg_gribov_search(Us, Gs, dims_list, cfg, nconf_tot, p)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    vols = [d[0] * d[1] * d[2] * d[3] for d in dims_list]
+    updates = sum(sw * v for sw, v in zip(res["sweeps"], vols))
+    Vs = [r / (36.0 * v) for r, v in zip(res["R"], vols)]
+    gain = []
+    for cc in range(nconf_tot):
+        ks = [k for k in range(len(cfg)) if cfg[k] == cc]
+        gain.append(res["best_V"][cc] - sum(Vs[k] for k in ks) / len(ks))
+    if rank == 0:
+        print(json.dumps({
+            "mode": "gribov_search", "metric": "batched Gribov-copy search site-updates/s", "unit": UNIT,
+            "value": updates / (ms / 1e3), "ms": ms, "configs": nconf_tot, "copies": len(Us),
+            "sites": sum(vols), "fp64_link_bytes": sum(vols) * 4 * 144, "site_updates": updates,
+            "converged": res["converged"], "sweeps_min": min(res["sweeps"]), "sweeps_max": max(res["sweeps"]),
+            "sweeps_mean": sum(res["sweeps"]) / len(res["sweeps"]),
+            "best_minus_mean_copy_V": {"mean": sum(gain) / len(gain), "max": max(gain)},
+            "autotune": {"block": tune["block"], "check_every": tune["check_every"]},
+            "generation_s": t_gen, "data": "synthetic fields and random transforms generated with torch on the GPU",
+            "gpu_launches": mcg.mcg_kernel_launches() - launches0}), flush=True)
+
+
+def synth_w():
+    from paper_0807_0264_gb300 import synth
+
+    return synth.W_PLAQ_06
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def main():
@@ -229,6 +341,11 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.gribov:
+        run_gribov(args, mcg, dev, rank)
+        if dist:
+            dist.destroy_process_group()
+        return
     dims = tuple(args.dims)
     V = 1
     for d in dims:
