@@ -219,7 +219,7 @@ def _haar_su3(n, gen, dev):
     d = torch.diagonal(Rm, dim1=-2, dim2=-1)
     Q = Q * (d / d.abs()).unsqueeze(-2)
     det = torch.linalg.det(Q)
-    return Q / (det ** (1.0 / 3.0)).reshape(n, 1, 1)
+    return (Q / (det ** (1.0 / 3.0)).reshape(n, 1, 1)).contiguous()
 
 
 def _gpu_field(dims, w, seed, dev):
