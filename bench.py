@@ -209,17 +209,18 @@ def config_of(args, form):
 # batched Gribov-copy search at full size (--gribov)
 # ---------------------------------------------------------------------------
 def _haar_su3(n, gen, dev):
-    """n Haar-random SU(3) matrices on the GPU (QR of a complex Ginibre matrix,
-    phases of diag R divided out, determinant's cube root removed)."""
+    """n Haar-random SU(3) matrices on the GPU, elementwise: Gram-Schmidt on two
+    complex Gaussian rows (a Haar U(3) pair of rows), row 2 = conj(row0 x row1)
+    (determinant 1)."""
     import torch
 
-    re = torch.randn((n, 3, 3), generator=gen, dtype=torch.float64, device=dev)
-    im = torch.randn((n, 3, 3), generator=gen, dtype=torch.float64, device=dev)
-    Q, Rm = torch.linalg.qr(torch.complex(re, im))
-    d = torch.diagonal(Rm, dim1=-2, dim2=-1)
-    Q = Q * (d / d.abs()).unsqueeze(-2)
-    det = torch.linalg.det(Q)
-    return (Q / (det ** (1.0 / 3.0)).reshape(n, 1, 1)).contiguous()
+    r = torch.complex(torch.randn((n, 2, 3), generator=gen, dtype=torch.float64, device=dev),
+                      torch.randn((n, 2, 3), generator=gen, dtype=torch.float64, device=dev))
+    r0 = r[:, 0] / torch.linalg.vector_norm(r[:, 0], dim=-1, keepdim=True)
+    r1 = r[:, 1] - (r0.conj() * r[:, 1]).sum(-1, keepdim=True) * r0
+    r1 = r1 / torch.linalg.vector_norm(r1, dim=-1, keepdim=True)
+    r2 = torch.linalg.cross(r0, r1, dim=-1).conj()
+    return torch.stack((r0, r1, r2), dim=1).contiguous()
 
 
 def _gpu_field(dims, w, seed, dev):
@@ -255,7 +256,8 @@ def _gpu_field(dims, w, seed, dev):
 def run_gribov(args, mcg, dev, rank):
     import torch
 
-    sizes = [((12, 12, 12, 12), 16), ((16, 16, 16, 32), 16), ((20, 20, 20, 40), 16)]
+    per = int(os.environ.get("MCG_GRIBOV_CONFIGS_PER_SIZE", "16"))
+    sizes = [((12, 12, 12, 12), per), ((16, 16, 16, 32), per), ((20, 20, 20, 40), per)]
     ncopy = 8
     t_gen = time.perf_counter()
     Us, Gs, dims_list, cfg = [], [], [], []
@@ -276,10 +278,12 @@ def run_gribov(args, mcg, dev, rank):
             c += 1
     torch.cuda.synchronize(dev)
     t_gen = time.perf_counter() - t_gen
+    print(f"gribov: generated {len(Us)} fields in {t_gen:.1f} s", file=sys.stderr, flush=True)
     nconf_tot = c
     p = mcg.Params(tol=1e-10, max_sweeps=20000, check_every=25, reunit_every=50, fp32_sweeps=20000, fp32_tol=5e-11,
                    fp32_window=25, fp32_overrelax=OMEGA, fp64_solve32=1)
     tune = mcg.autotune_schedule(Us, dims_list, p, trial_sweeps=20, chunks=(25, 50))
+    print(f"gribov: autotuned {tune['block']} x {tune['check_every']}", file=sys.stderr, flush=True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = mcg.mcg_kernel_launches()
     e0.record()
