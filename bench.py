@@ -265,7 +265,11 @@ def run_gribov(args, mcg, dev, rank):
     for dims, nconf in sizes:
         V = dims[0] * dims[1] * dims[2] * dims[3]
         for _ in range(nconf):
-            U = mcg.mcg_pack_links(_gpu_field(dims, synth_w(), c, dev), dims)
+            canon = _gpu_field(dims, synth_w(), c, dev)
+            if not bool(torch.isfinite(torch.view_as_real(canon)).all()):
+                print(f"gribov: config {c} {dims} generated non-finite links", file=sys.stderr, flush=True)
+            U = mcg.mcg_pack_links(canon, dims)
+            del canon
             for k in range(ncopy):
                 gen = torch.Generator(device=dev)
                 gen.manual_seed(1000 + ncopy * c + k)
@@ -294,10 +298,25 @@ def run_gribov(args, mcg, dev, rank):
     vols = [d[0] * d[1] * d[2] * d[3] for d in dims_list]
     updates = sum(sw * v for sw, v in zip(res["sweeps"], vols))
     Vs = [r / (36.0 * v) for r, v in zip(res["R"], vols)]
+    import math
+
     gain = []
     for cc in range(nconf_tot):
-        ks = [k for k in range(len(cfg)) if cfg[k] == cc]
-        gain.append(res["best_V"][cc] - sum(Vs[k] for k in ks) / len(ks))
+        ks = [k for k in range(len(cfg)) if cfg[k] == cc and math.isfinite(Vs[k])]
+        if ks:
+            gain.append(res["best_V"][cc] - sum(Vs[k] for k in ks) / len(ks))
+    per_size = {}
+    for dims, _ in sizes:
+        ks = [k for k in range(len(dims_list)) if dims_list[k] == dims]
+        fin = [Vs[k] for k in ks if math.isfinite(Vs[k])]
+        per_size["x".join(map(str, dims))] = {
+            "copies": len(ks), "non_finite_R": len(ks) - len(fin),
+            "at_sweep_cap": sum(1 for k in ks if res["sweeps"][k] >= p.max_sweeps),
+            "sweeps_mean": sum(res["sweeps"][k] for k in ks) / len(ks),
+            "V_mean": (sum(fin) / len(fin)) if fin else None}
+        if len(fin) < len(ks):
+            print(f"gribov: non-finite R for copies {[k for k in ks if not math.isfinite(Vs[k])]}",
+                  file=sys.stderr, flush=True)
     if rank == 0:
         print(json.dumps({
             "mode": "gribov_search", "metric": "batched Gribov-copy search site-updates/s", "unit": UNIT,
@@ -305,7 +324,8 @@ def run_gribov(args, mcg, dev, rank):
             "sites": sum(vols), "fp64_link_bytes": sum(vols) * 4 * 144, "site_updates": updates,
             "converged": res["converged"], "sweeps_min": min(res["sweeps"]), "sweeps_max": max(res["sweeps"]),
             "sweeps_mean": sum(res["sweeps"]) / len(res["sweeps"]),
-            "best_minus_mean_copy_V": {"mean": sum(gain) / len(gain), "max": max(gain)},
+            "best_minus_mean_copy_V": {"mean": sum(gain) / max(1, len(gain)), "max": max(gain) if gain else None},
+            "per_size": per_size,
             "autotune": {"block": tune["block"], "check_every": tune["check_every"]},
             "generation_s": t_gen, "data": "synthetic fields and random transforms generated with torch on the GPU",
             "gpu_launches": mcg.mcg_kernel_launches() - launches0}), flush=True)
