@@ -349,6 +349,7 @@ int orc_trs_solve(const double* A, const double* b, double* a) {
     for (int it = 0; it < 200; ++it) {
         double s2 = 0, s3 = 0;
         for (int i = 0; i < 4; ++i) {
+            if (beta[i] == 0.0) continue; /* a zero weight contributes nothing, also at mu = al[i] */
             double d = mu - al[i];
             double q = beta[i] * beta[i] / (d * d);
             s2 += q;
@@ -369,7 +370,8 @@ int orc_trs_solve(const double* A, const double* b, double* a) {
     double an2 = 0;
     for (int k = 0; k < 4; ++k) {
         double s = 0;
-        for (int i = 0; i < 4; ++i) s += V[4 * k + i] * beta[i] / (mu - al[i]);
+        for (int i = 0; i < 4; ++i)
+            if (beta[i] != 0.0) s += V[4 * k + i] * beta[i] / (mu - al[i]);
         a[k] = s;
         an2 += s * s;
     }

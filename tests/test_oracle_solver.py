@@ -125,3 +125,21 @@ def test_identity_links_keep_identity():
     a, hard = oracle.trs_solve(A, b)
     assert not hard
     np.testing.assert_allclose(a, [1, 0, 0, 0], atol=1e-15)
+
+
+def test_zero_weight_on_the_top_eigenvector():
+    """b orthogonal to the top eigenvector (its weight exactly 0) with the
+    remaining weights too large for the hard case: the multiplier lies strictly
+    above lambda_max and the maximiser follows from the other terms alone.
+    A = diag(3, 1, 0, 0), b = (0, 3, 0, 0): 9 / (mu - 1)^2 = 1 gives mu = 4 and
+    a = (0, 1, 0, 0) with F = 1 + 6 = 7 (F(e0) = 3)."""
+    A = np.diag([3.0, 1.0, 0.0, 0.0])
+    b = np.array([0.0, 3.0, 0.0, 0.0])
+    a, hard = oracle.trs_solve(A, b)
+    assert np.all(np.isfinite(a)) and not hard
+    assert np.abs(a - np.array([0.0, 1.0, 0.0, 0.0])).max() < 1e-12
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((100000, 4))
+    X /= np.linalg.norm(X, axis=1, keepdims=True)
+    F = np.einsum("ni,ij,nj->n", X, A, X) + 2 * X @ b
+    assert a @ A @ a + 2 * b @ a >= F.max() - 1e-12
