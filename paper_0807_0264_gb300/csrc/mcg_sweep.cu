@@ -188,6 +188,8 @@ __device__ __forceinline__ int trs_from_eigen(const T (&S)[4][4], const T (&V)[4
         T s2 = T(0), s3 = T(0);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
+            // a zero weight contributes nothing (also when mu sits on al[i])
+            if (beta[i] == T(0)) continue;
             const T r = frcp(mu - al[i]);
             const T q = beta[i] * beta[i] * r * r;
             s2 += q;
@@ -210,7 +212,7 @@ __device__ __forceinline__ int trs_from_eigen(const T (&S)[4][4], const T (&V)[4
     T n2 = T(0);
     T coef[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) coef[i] = fdiv(beta[i], mu - al[i]);
+    for (int i = 0; i < 4; ++i) coef[i] = beta[i] == T(0) ? T(0) : fdiv(beta[i], mu - al[i]);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         a[k] = V[k][0] * coef[0] + V[k][1] * coef[1] + V[k][2] * coef[2] + V[k][3] * coef[3];
@@ -496,6 +498,10 @@ __device__ __noinline__ Vec4d solve_f64_fallback(double a00, double a01, double 
 #pragma unroll
             for (int j = 0; j < 4; ++j) Aflat[4 * i + j] = A[i][j];
         solve_f64_full(Aflat, b, r.v);
+        if (!(isfinite(r.v[0]) && isfinite(r.v[1]) && isfinite(r.v[2]) && isfinite(r.v[3]))) {
+            r.v[0] = 1.0;  // backstop: the identity leaves the site unchanged
+            r.v[1] = r.v[2] = r.v[3] = 0.0;
+        }
         return r;
     }
     const double inv = rsqrt(r.v[0] * r.v[0] + r.v[1] * r.v[1] + r.v[2] * r.v[2] + r.v[3] * r.v[3]);
@@ -626,6 +632,10 @@ __device__ __noinline__ float4 solve_f32_fallback(float a00, float a01, float a0
     float V[4][4], a[4], mu;
     jacobi4<float>(S, V, 8, 5e-7f);
     trs_from_eigen<float>(S, V, b, a, mu);
+    // backstop: a degenerate local problem never feeds a non-finite update
+    // into the links (the identity leaves the site unchanged)
+    if (!(isfinite(a[0]) && isfinite(a[1]) && isfinite(a[2]) && isfinite(a[3])))
+        return make_float4(1.f, 0.f, 0.f, 0.f);
     return make_float4(a[0], a[1], a[2], a[3]);
 }
 
