@@ -180,38 +180,6 @@ __device__ __forceinline__ void m3_reunitarise(cplx<T>* a) {
     }
 }
 
-// Re-unitarise in place in the matrix's own precision (used for FP32 links
-// inside the FP32 sweep, where FP64 arithmetic would cost more than the sweep).
-template <typename T>
-__device__ __forceinline__ void m3_reunitarise_same(cplx<T>* a) {
-    T n0 = T(0);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) n0 += a[k].x * a[k].x + a[k].y * a[k].y;
-    n0 = rsqrt(n0);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) a[k] = cscale(a[k], n0);
-    T px = T(0), py = T(0);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        px += a[k].x * a[3 + k].x + a[k].y * a[3 + k].y;
-        py += a[k].x * a[3 + k].y - a[k].y * a[3 + k].x;
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) a[3 + k] = mk(a[3 + k].x - (px * a[k].x - py * a[k].y), a[3 + k].y - (px * a[k].y + py * a[k].x));
-    T n1 = T(0);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) n1 += a[3 + k].x * a[3 + k].x + a[3 + k].y * a[3 + k].y;
-    n1 = rsqrt(n1);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) a[3 + k] = cscale(a[3 + k], n1);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const int i = (k + 1) % 3, j = (k + 2) % 3;
-        const cplx<T> c = csub(cmul(a[i], a[3 + j]), cmul(a[j], a[3 + i]));
-        a[6 + k] = mk(c.x, -c.y);
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Field layout (the C-ABI contract, see include/mcg.h):
 //   site s of parity p (in-parity index s = lexicographic index / 2),
@@ -361,11 +329,6 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // reductions
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ long long warp_sum_ll(long long v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
