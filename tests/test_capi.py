@@ -62,3 +62,36 @@ def test_version_and_error_codes_without_gpu(mcg):
     assert lib.mcg_plaquette(ctypes.c_void_p(1), None, ctypes.byref(zero), None) == 2
     assert lib.mcg_smear(ctypes.c_void_p(1), ctypes.c_void_p(1), ctypes.byref(good), 0.1, 1.0, 1, None) == 3
     assert lib.mcg_convert(None, 0, ctypes.c_void_p(1), 1, 10, None) == 3
+
+
+def test_argument_validation_of_observables_and_params_without_gpu(mcg):
+    """Invalid calls to the Sec. III.D entries and bad parameters are refused
+    with MCG_BAD_ARG before any device work, each for its own reason."""
+    lib = mcg.library()
+    good = mcg.lattice((4, 4, 4, 6))
+    one, two = ctypes.c_void_p(1), ctypes.c_void_p(2)
+
+    def refused(rc, why):
+        assert rc == 3, rc
+        assert why.encode() in lib.mcg_last_error(), lib.mcg_last_error()
+
+    # center decomposition: null inputs, no output requested
+    refused(lib.mcg_vortex_remove(None, one, one, None, ctypes.byref(good), None), "null pointer")
+    refused(lib.mcg_vortex_remove(one, one, None, None, ctypes.byref(good), None), "no output requested")
+    # Wilson loops: R beyond the smallest spatial extent (4), T beyond N_t (6), empty ranges
+    W = (ctypes.c_double * 64)()
+    for R, T in ((0, 1), (5, 1), (1, 0), (1, 7)):
+        refused(lib.mcg_wilson_loops(one, ctypes.byref(good), R, T, W, None), "1 <= Rmax")
+    # off-axis: zero vector, a component as long as an extent, T out of range, no vectors
+    for vec, T, why in (((0, 0, 0), 1, "path length"), ((4, 0, 0), 1, "smallest spatial extent"),
+                        ((0, -4, 1), 1, "smallest spatial extent"), ((1, 1, 0), 7, "Tmax")):
+        v = (ctypes.c_int * 3)(*vec)
+        refused(lib.mcg_wilson_loops_offaxis(one, ctypes.byref(good), v, 1, T, W, None), why)
+    v = (ctypes.c_int * 3)(1, 1, 0)
+    refused(lib.mcg_wilson_loops_offaxis(one, ctypes.byref(good), v, 0, 1, W, None), "nvec")
+    # parameters: fp64_solve32 in {0, 1}; fp32_overrelax in (0, 2) when an FP32 phase runs
+    p = mcg.Params(fp64_solve32=2).c()
+    refused(lib.mcg_fix(one, two, ctypes.byref(good), ctypes.byref(p), None, None, None, None), "fp64_solve32")
+    for w in (0.0, 2.0, float("nan")):
+        p = mcg.Params(fp32_sweeps=10, fp32_overrelax=w).c()
+        refused(lib.mcg_fix(one, two, ctypes.byref(good), ctypes.byref(p), None, None, None, None), "overrelax")
