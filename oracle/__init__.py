@@ -58,6 +58,12 @@ def _load():
             lib.orc_halfsweep.argtypes = [P, P, P, I, D]
             lib.orc_halfsweep.restype = L
             lib.orc_fix.argtypes = [P, P, P, D, I, I, D, P, P, P]
+            U64 = ctypes.c_uint64
+            lib.orc_philox4x64.argtypes = [P, P, P]
+            lib.orc_anneal_halfsweep.argtypes = [P, P, P, I, D, L, I, D, U64, U64]
+            lib.orc_anneal_halfsweep.restype = L
+            lib.orc_anneal.argtypes = [P, P, P, P, I, L, I, D, U64, U64]
+            lib.orc_anneal.restype = L
             lib.orc_fix.restype = I
             lib.orc_expm.argtypes = [P, P]
             lib.orc_smear_step.argtypes = [P, P, P, D, D]
@@ -167,6 +173,36 @@ def fix(dims, U, G=None, tol: float = 1e-10, max_sweeps: int = 2000, reunit_ever
                          float(omega), _p(R_hist), ctypes.byref(sweeps), ctypes.byref(hard))
     n = sweeps.value
     return dict(U=U, G=G, R_hist=R_hist[: n + 1], sweeps=n, converged=(rc == 0), hard=int(hard.value))
+
+
+def philox4x64(counter, key) -> np.ndarray:
+    """Philox4x64-10 block for a 4-word counter and 2-word key (uint64)."""
+    c = np.ascontiguousarray(counter, dtype=np.uint64).reshape(4)
+    k = np.ascontiguousarray(key, dtype=np.uint64).reshape(2)
+    out = np.zeros(4, np.uint64)
+    _load().orc_philox4x64(_p(c), _p(k), _p(out))
+    return out
+
+
+def anneal_halfsweep(dims, U, G, parity: int, T: float, sweep: int, nhit: int, eps: float, seed: int,
+                     field: int = 0):
+    """One annealing half-sweep; returns (U', G', accepted hits)."""
+    U = _cfield(U).copy()
+    G = _cfield(G).copy()
+    acc = _load().orc_anneal_halfsweep(_p(_dims(dims)), _p(U), _p(G), int(parity), float(T), int(sweep), int(nhit),
+                                       float(eps), int(seed), int(field))
+    return U, G, int(acc)
+
+
+def anneal(dims, U, G, T, nhit: int, eps: float, seed: int, first_sweep: int = 0, field: int = 0):
+    """Simulated annealing with temperatures T[k] (one per sweep), then
+    re-unitarisation.  Returns (U', G', accepted hits)."""
+    U = _cfield(U).copy()
+    G = _cfield(G).copy()
+    T = np.ascontiguousarray(T, dtype=np.float64).reshape(-1)
+    acc = _load().orc_anneal(_p(_dims(dims)), _p(U), _p(G), _p(T), int(T.size), int(first_sweep), int(nhit),
+                             float(eps), int(seed), int(field))
+    return U, G, int(acc)
 
 
 def expm(X) -> np.ndarray:

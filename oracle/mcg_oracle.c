@@ -23,6 +23,10 @@
  *   - the stop rule is V_U(k) - V_U(k-1) < tol on the normalised functional;
  *   - links and Omega are re-unitarised every reunit_every sweeps;
  *   - stout smearing is isotropic in 4D and updates all links at once.
+ *   - simulated annealing (named in Sec. IV as a way to higher maxima, not
+ *     specified): Metropolis hits on the same subgroup moves, proposals and
+ *     acceptances drawn from Philox4x64-10 with a counter per (site, sweep,
+ *     subgroup and hit, field), temperatures given per sweep (orc_anneal).
  */
 #include <complex.h>
 #include <math.h>
@@ -508,6 +512,148 @@ int orc_fix(const int* dims, cplx* U, cplx* Om, double tol, int max_sweeps, int 
     *sweeps_out = max_sweeps;
     if (hard_out) *hard_out = hard;
     return 1;
+}
+
+/* ------------------------------------------------------------------ */
+/* Simulated annealing of the gauge transform (Sec. IV: the SU(2) route  */
+/* to higher maxima, here for the SU(3) functional as a Gribov-copy     */
+/* search variant ahead of the relaxation)                              */
+/* ------------------------------------------------------------------ */
+
+/* Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+ * easy as 1, 2, 3", SC'11): ten rounds on the counter (c0, c1, c2, c3) with
+ * key (k0, k1); each round maps
+ *   (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)),
+ * hi / lo the halves of the 128-bit product, and the key advances by the
+ * Weyl increments (W0, W1) between rounds. */
+void orc_philox4x64(const uint64_t* ctr, const uint64_t* key, uint64_t* out) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+    uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        unsigned __int128 p0 = (unsigned __int128)M0 * c0;
+        unsigned __int128 p1 = (unsigned __int128)M1 * c2;
+        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+/* 64 random bits -> a double in [0, 1): the top 53 bits times 2^-53 (exact). */
+static double unit_interval(uint64_t w) { return (double)(w >> 11) * 0x1p-53; }
+
+/* Sum over the 8 links at x of |tr|^2 (the site's share of R). */
+static double site_functional(cplx* const* F, cplx* const* B) {
+    double s = 0.0;
+    for (int mu = 0; mu < 4; ++mu) {
+        cplx tf = m_trace(F[mu]), tb = m_trace(B[mu]);
+        s += creal(tf) * creal(tf) + cimag(tf) * cimag(tf);
+        s += creal(tb) * creal(tb) + cimag(tb) * cimag(tb);
+    }
+    return s;
+}
+
+/*
+ * One annealing site update at x, temperature T.  For the subgroups (0,1),
+ * (0,2), (1,2) in turn, nhit Metropolis hits: the counter
+ * (x, sweep, subgroup * nhit + hit, field) under key (seed, 0) gives four
+ * words w0..w3; the proposal is the SU(2) element a = (a0, v) with
+ * v_k = eps (2 u(w_{k-1}) - 1), a0 = sqrt(1 - |v|^2) (its law is even under
+ * a -> a^dag, so the Metropolis rule keeps exp(F/T) times Haar measure
+ * invariant), embedded as G in rows/columns (p, q); the move
+ * U_mu(x) <- G U_mu(x), U_mu(x-mu) <- U_mu(x-mu) G^dag, Omega(x) <- G Omega(x)
+ * changes the site functional by dF, and is accepted when dF >= 0 or
+ * u(w3) < exp(dF / T).  Returns the number of accepted hits.
+ */
+static long anneal_site(const geom* g, cplx* U, cplx* Om, long x, double T, long sweep, int nhit, double eps,
+                        uint64_t seed, uint64_t field) {
+    static const int PQ[3][3] = {{0, 1, 2}, {0, 2, 1}, {1, 2, 0}};
+    cplx* F[4];
+    cplx* B[4];
+    for (int mu = 0; mu < 4; ++mu) {
+        F[mu] = link(U, x, mu);
+        B[mu] = link(U, shift(g, x, mu, -1), mu);
+    }
+    const uint64_t key[2] = {seed, 0};
+    long accepted = 0;
+    for (int s = 0; s < 3; ++s) {
+        int p = PQ[s][0], q = PQ[s][1], r = PQ[s][2];
+        for (int h = 0; h < nhit; ++h) {
+            uint64_t ctr[4] = {(uint64_t)x, (uint64_t)sweep, (uint64_t)(s * nhit + h), field}, w[4];
+            orc_philox4x64(ctr, key, w);
+            double v1 = eps * (2.0 * unit_interval(w[0]) - 1.0);
+            double v2 = eps * (2.0 * unit_interval(w[1]) - 1.0);
+            double v3 = eps * (2.0 * unit_interval(w[2]) - 1.0);
+            double a0 = sqrt(1.0 - (v1 * v1 + v2 * v2 + v3 * v3));
+            cplx G[9] = {0};
+            G[3 * r + r] = 1.0;
+            G[3 * p + p] = a0 + I * v3;
+            G[3 * p + q] = v2 + I * v1;
+            G[3 * q + p] = -v2 + I * v1;
+            G[3 * q + q] = a0 - I * v3;
+            cplx Fn[4][9], Bn[4][9];
+            for (int mu = 0; mu < 4; ++mu) {
+                m_mul(Fn[mu], G, F[mu]);
+                m_mul_nd(Bn[mu], B[mu], G);
+            }
+            cplx* Fp[4] = {Fn[0], Fn[1], Fn[2], Fn[3]};
+            cplx* Bp[4] = {Bn[0], Bn[1], Bn[2], Bn[3]};
+            double dF = site_functional(Fp, Bp) - site_functional(F, B);
+            if (dF >= 0.0 || unit_interval(w[3]) < exp(dF / T)) {
+                for (int mu = 0; mu < 4; ++mu) {
+                    memcpy(F[mu], Fn[mu], sizeof(Fn[mu]));
+                    memcpy(B[mu], Bn[mu], sizeof(Bn[mu]));
+                }
+                cplx o[9];
+                m_mul(o, G, Om + x * 9);
+                memcpy(Om + x * 9, o, sizeof(o));
+                ++accepted;
+            }
+        }
+    }
+    return accepted;
+}
+
+/* Annealing update of every site of one parity at temperature T (sweep
+ * number `sweep` in the random-number counter).  Returns accepted hits. */
+long orc_anneal_halfsweep(const int* dims, cplx* U, cplx* Om, int parity, double T, long sweep, int nhit, double eps,
+                          uint64_t seed, uint64_t field) {
+    geom g = make_geom(dims);
+    long acc = 0;
+#pragma omp parallel for schedule(static) reduction(+ : acc)
+    for (long x = 0; x < g.vol; ++x)
+        if (parity_of(&g, x) == parity) acc += anneal_site(&g, U, Om, x, T, sweep, nhit, eps, seed, field);
+    return acc;
+}
+
+/*
+ * Simulated annealing: for k = 0 .. nsweeps-1, an even then an odd annealing
+ * half-sweep at temperature T[k] with sweep number first_sweep + k; then
+ * links and Omega are re-unitarised once.  Returns the accepted hits.
+ */
+long orc_anneal(const int* dims, cplx* U, cplx* Om, const double* T, int nsweeps, long first_sweep, int nhit,
+                double eps, uint64_t seed, uint64_t field) {
+    geom g = make_geom(dims);
+    long acc = 0;
+    for (int k = 0; k < nsweeps; ++k) {
+        acc += orc_anneal_halfsweep(dims, U, Om, 0, T[k], first_sweep + k, nhit, eps, seed, field);
+        acc += orc_anneal_halfsweep(dims, U, Om, 1, T[k], first_sweep + k, nhit, eps, seed, field);
+    }
+    orc_reunitarise_field(g.vol * 4, U);
+    orc_reunitarise_field(g.vol, Om);
+    return acc;
 }
 
 /* ------------------------------------------------------------------ */
