@@ -204,6 +204,31 @@ int mcg_smear(const void* U_in, void* U_out, const mcg_lattice* lat, double rho,
 int mcg_fix(void* U, void* G, const mcg_lattice* lat, const mcg_params* params, double* R_out,
             int* sweeps_out, double* R_hist, cudaStream_t stream);
 
+/*
+ * Simulated annealing of the gauge transform: a Gribov-copy search variant
+ * run ahead of mcg_fix (Sec. IV names annealing as the route to higher maxima
+ * taken in SU(2); the paper does not specify it, so this is the library's
+ * reading).  For k = 0 .. nsweeps-1: an even then an odd checkerboard
+ * half-sweep at temperature T[k]; at each site and for the subgroups (0,1),
+ * (0,2), (1,2) in turn, nhit Metropolis hits on the move of mcg_fix
+ * (U_mu(x) <- G U_mu(x), U_mu(x-mu) <- U_mu(x-mu) G^dag, Omega(x) <- G Omega(x))
+ * with target density exp(F / T), F = sum over the 8 links at x of |tr|^2.
+ * Hit h of subgroup s at lexicographic site x in field f of sweep number
+ * first_sweep + k draws the four words of Philox4x64-10 at counter
+ * (x, first_sweep + k, s * nhit + h, f) under key (seed, 0); u_i = (w_i >> 11)
+ * 2^-53; the proposal is a = (sqrt(1 - |v|^2), v), v_i = eps (2 u_i - 1)
+ * (i = 0..2), the SU(2) element a0 + i v.sigma in rows/columns of the
+ * subgroup; it is accepted when dF >= 0 or u_3 < exp(dF / T).  After the last
+ * sweep links and Omega are re-unitarised.  In place on U and G (FP64 fields
+ * of lat, fields contiguous; lat->precision must be MCG_F64).
+ * T: host, nsweeps temperatures > 0.  nhit in 1..2^20, eps in (0, 0.5].
+ * accepted_out: host, nfields, may be NULL: accepted hits per field (out of
+ * nsweeps * V * 3 * nhit).  A call with first_sweep = the sweeps done so far
+ * continues the same random stream.  Synchronises.
+ */
+int mcg_anneal(void* U, void* G, const mcg_lattice* lat, const double* T, int nsweeps, long long first_sweep,
+               int nhit, double eps, unsigned long long seed, long long* accepted_out, cudaStream_t stream);
+
 /* Z3 center projection (Sec. II.A): m_mu(x) in {-1,0,1} is the sector of
  * phi = arg tr U_mu(x) nearest 2 pi m / 3 (equivalently the closest center
  * element on the group manifold); ties on |phi| = pi/3 go to 0, phi = pi to

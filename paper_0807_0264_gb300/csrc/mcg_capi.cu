@@ -469,6 +469,25 @@ int mcg_fix(void* U, void* G, const mcg_lattice* lat, const mcg_params* params, 
     return fix_impl(U, G, lat, g, params, R_out, sweeps_out, nullptr, R_hist, stream);
 }
 
+int mcg_anneal(void* U, void* G, const mcg_lattice* lat, const double* T, int nsweeps, long long first_sweep,
+               int nhit, double eps, unsigned long long seed, long long* accepted_out, cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if (lat->precision != MCG_F64) return fail(MCG_BAD_ARG, "annealing runs on FP64 fields");
+    if (lat->nfields > 65535) return fail(MCG_BAD_ARG, "at most 65535 fields per call");
+    if (!U || !G || (nsweeps > 0 && !T)) return fail(MCG_BAD_ARG, "null pointer");
+    if (nsweeps < 0 || first_sweep < 0) return fail(MCG_BAD_ARG, "nsweeps and first_sweep must be >= 0");
+    if (nhit < 1 || nhit > (1 << 20)) return fail(MCG_BAD_ARG, "nhit must be in 1..2^20");
+    if (!(eps > 0.0 && eps <= 0.5)) return fail(MCG_BAD_ARG, "eps must be in (0, 0.5]");
+    for (int k = 0; k < nsweeps; ++k)
+        if (!(T[k] > 0.0)) return fail(MCG_BAD_ARG, "every temperature must be > 0");
+    const size_t lb = elem_bytes(MCG_F64) * link_elems(g) * lat->nfields;
+    const size_t gb = elem_bytes(MCG_F64) * gauge_elems(g) * lat->nfields;
+    if (overlap(U, lb, G, gb)) return fail(MCG_BAD_ARG, "U and G overlap");
+    return run_anneal(U, G, g, lat->nfields, T, nsweeps, first_sweep, nhit, eps, seed, accepted_out, stream);
+}
+
 int mcg_center_project(const void* U, int8_t* Z, long long* counts, const mcg_lattice* lat, cudaStream_t stream) {
     Geom g;
     int rc = check_lat(lat, &g);

@@ -91,6 +91,14 @@ template <typename T>
 int time_halfsweep(void* U, void* G, const Geom& g, int parity, int nreps, int flush_l2, float* ms,
                    cudaStream_t stream);
 
+// Simulated annealing (FP64 fields of one lattice, fields contiguous): for
+// k < nsweeps an even then an odd Metropolis half-sweep at temperature T[k]
+// (host array) with sweep number first_sweep + k in the random counter; then
+// links and Omega are re-unitarised.  accepted_host (nfields, may be null):
+// accepted hits per field.  Synchronises.
+int run_anneal(void* U, void* G, const Geom& g, int nfields, const double* T, int nsweeps, long long first_sweep,
+               int nhit, double eps, unsigned long long seed, long long* accepted_host, cudaStream_t st);
+
 // threads per block of the half-sweep kernel for a precision, and the sites
 // each block covers (one thread per site in both precisions)
 int sweep_block(int prec);

@@ -712,58 +712,51 @@ __device__ __forceinline__ int subgroup_step_s32(L& lk, const int P, const int Q
     return fb;
 }
 
-template <typename T, typename L, bool S32 = false>
-__device__ __forceinline__ int subgroup_step(L& lk, const int P, const int Q, const int R, const T omega) {
-    T a[4];
-    int fb;
-    if constexpr (S32) {
-        fb = subgroup_step_s32<T, S32>(lk, P, Q, R, a);
-    } else {
-        T A[4][4], b[4];
+// Coefficients of the local problem of subgroup (P, Q) at a site: the site's
+// share of R after the move G(a) is a^T A a + 2 b^T a + const (Sec. II.A),
+// with tr(G M) = M_RR + sum_k w_k a_k per link and w_1..w_3 negated for the
+// backward links (which become M G^dag).
+template <typename T, typename L>
+__device__ __forceinline__ void local_problem(L& lk, const int P, const int Q, const int R, T (&A)[4][4],
+                                              T (&b)[4]) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            b[i] = T(0);
+    for (int i = 0; i < 4; ++i) {
+        b[i] = T(0);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) A[i][j] = T(0);
-        }
-        const int ePP = 3 * P + P, ePQ = 3 * P + Q, eQP = 3 * Q + P, eQQ = 3 * Q + Q, eRR = 3 * R + R;
+        for (int j = 0; j < 4; ++j) A[i][j] = T(0);
+    }
+    const int ePP = 3 * P + P, ePQ = 3 * P + Q, eQP = 3 * Q + P, eQQ = 3 * Q + Q, eRR = 3 * R + R;
 #pragma unroll
-        for (int l = 0; l < 8; ++l) {
-            const cplx<T> m11 = lk(l, ePP), m12 = lk(l, ePQ), m21 = lk(l, eQP), m22 = lk(l, eQQ);
-            const cplx<T> c = lk(l, eRR);
-            cplx<T> w[4];
-            w[0] = cadd(m11, m22);
-            w[1] = mk(-(m21.y + m12.y), m21.x + m12.x);  // i (m21 + m12)
-            w[2] = csub(m21, m12);
-            w[3] = mk(-(m11.y - m22.y), m11.x - m22.x);  // i (m11 - m22)
-            if (l >= 4) {
+    for (int l = 0; l < 8; ++l) {
+        const cplx<T> m11 = lk(l, ePP), m12 = lk(l, ePQ), m21 = lk(l, eQP), m22 = lk(l, eQQ);
+        const cplx<T> c = lk(l, eRR);
+        cplx<T> w[4];
+        w[0] = cadd(m11, m22);
+        w[1] = mk(-(m21.y + m12.y), m21.x + m12.x);  // i (m21 + m12)
+        w[2] = csub(m21, m12);
+        w[3] = mk(-(m11.y - m22.y), m11.x - m22.x);  // i (m11 - m22)
+        if (l >= 4) {
 #pragma unroll
-                for (int k = 1; k < 4; ++k) w[k] = mk(-w[k].x, -w[k].y);
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                b[k] = fma(c.x, w[k].x, fma(c.y, w[k].y, b[k]));
-#pragma unroll
-                for (int j = k; j < 4; ++j) A[k][j] = fma(w[k].x, w[j].x, fma(w[k].y, w[j].y, A[k][j]));
-            }
+            for (int k = 1; k < 4; ++k) w[k] = mk(-w[k].x, -w[k].y);
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < 4; ++k) {
+            b[k] = fma(c.x, w[k].x, fma(c.y, w[k].y, b[k]));
 #pragma unroll
-            for (int j = 0; j < k; ++j) A[k][j] = A[j][k];
-        asm volatile("" ::: "memory");
-        fb = Solver<T>::solve(A, b, a);
+            for (int j = k; j < 4; ++j) A[k][j] = fma(w[k].x, w[j].x, fma(w[k].y, w[j].y, A[k][j]));
+        }
     }
-    if (omega != T(1)) {
-        // over-relaxation: a -> normalise((1 - omega) e0 + omega a)
-        a[0] = (T(1) - omega) + omega * a[0];
-        a[1] *= omega;
-        a[2] *= omega;
-        a[3] *= omega;
-        const T inv = rsqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) a[k] *= inv;
-    }
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int j = 0; j < k; ++j) A[k][j] = A[j][k];
+}
+
+// The move itself: G = (a0 + i a3, a2 + i a1; -a2 + i a1, a0 - i a3) in rows
+// and columns (P, Q); U_mu(x) <- G U_mu(x) and Omega(x) <- G Omega(x) (slots
+// 0..3 and 8), U_mu(x - mu) <- U_mu(x - mu) G^dag (slots 4..7).
+template <typename T, typename L>
+__device__ __forceinline__ void apply_subgroup(L& lk, const int P, const int Q, const T (&a)[4]) {
     const cplx<T> g11 = mk(a[0], a[3]), g12 = mk(a[2], a[1]), g21 = mk(-a[2], a[1]), g22 = mk(a[0], -a[3]);
 #pragma unroll 1
     for (int l = 0; l < 9; ++l) {
@@ -783,6 +776,31 @@ __device__ __forceinline__ int subgroup_step(L& lk, const int P, const int Q, co
             }
         }
     }
+}
+
+template <typename T, typename L, bool S32 = false>
+__device__ __forceinline__ int subgroup_step(L& lk, const int P, const int Q, const int R, const T omega) {
+    T a[4];
+    int fb;
+    if constexpr (S32) {
+        fb = subgroup_step_s32<T, S32>(lk, P, Q, R, a);
+    } else {
+        T A[4][4], b[4];
+        local_problem<T>(lk, P, Q, R, A, b);
+        asm volatile("" ::: "memory");
+        fb = Solver<T>::solve(A, b, a);
+    }
+    if (omega != T(1)) {
+        // over-relaxation: a -> normalise((1 - omega) e0 + omega a)
+        a[0] = (T(1) - omega) + omega * a[0];
+        a[1] *= omega;
+        a[2] *= omega;
+        a[3] *= omega;
+        const T inv = rsqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a[k] *= inv;
+    }
+    apply_subgroup<T>(lk, P, Q, a);
     return fb;
 }
 
@@ -887,6 +905,165 @@ __global__ void __launch_bounds__(NT, 2) k_halfsweep(SweepBatch bt, int parity) 
         const int w = __reduce_add_sync(0xffffffffu, fb);
         if ((threadIdx.x & 31) == 0 && w) atomicAdd(&bt.state[f].fallbacks, w);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Simulated annealing of the gauge transform (Sec. IV names annealing as the
+// SU(2) route to higher maxima; here a Gribov-copy search variant run ahead
+// of the relaxation).  Each subgroup of a site gets nhit Metropolis hits on
+// the same move as the relaxation; the local problem (A, b) is built once per
+// subgroup, the hits are composed as SU(2) elements relative to it and scored
+// by the quadratic form, and the accepted product is applied once.
+// ---------------------------------------------------------------------------
+
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
+// (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1,
+// lo(M0 c0)), the key advancing by the Weyl increments between rounds.
+__device__ __forceinline__ void philox4x64_10(unsigned long long (&c)[4], unsigned long long k0,
+                                              unsigned long long k1) {
+    const unsigned long long M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const unsigned long long W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+        const unsigned long long hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+        c[0] = hi1 ^ c[1] ^ k0;
+        c[1] = lo1;
+        c[2] = hi0 ^ c[3] ^ k1;
+        c[3] = lo0;
+        k0 += W0;
+        k1 += W1;
+    }
+}
+
+// top 53 bits -> [0, 1), exact
+__device__ __forceinline__ double unit_interval(unsigned long long w) { return (double)(w >> 11) * 0x1p-53; }
+
+// a^T A a + 2 b^T a
+__device__ __forceinline__ double local_quadratic(const double (&A)[4][4], const double (&b)[4], const double (&a)[4]) {
+    double f = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        double r = 2.0 * b[i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) r = fma(A[i][j], a[j], r);
+        f = fma(r, a[i], f);
+    }
+    return f;
+}
+
+struct AnnealArgs {
+    cplx<double>* U;
+    cplx<double>* G;
+    Geom g;
+    double T;
+    long long sweep;
+    int nhit;
+    double eps;
+    unsigned long long seed;
+    unsigned long long* accepted;  // one per field
+};
+
+// One annealing half-sweep over the sites of `parity`, one thread per site,
+// field blockIdx.y.  The random words of hit h of subgroup s at
+// lexicographic site x come from the counter (x, sweep, s * nhit + h, field)
+// under key (seed, 0): v_k = eps (2 u_k - 1), a0 = sqrt(1 - |v|^2) (rounded
+// step by step, no contraction), accepted when dF >= 0 or u_3 < exp(dF / T).
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) k_anneal_halfsweep(AnnealArgs an, int parity) {
+    const int f = blockIdx.y;
+    const Geom g = an.g;
+    cplx<double>* __restrict__ U = an.U + (size_t)f * link_elems(g);
+    cplx<double>* __restrict__ G = an.G + (size_t)f * gauge_elems(g);
+    const int s = blockIdx.x * NT + threadIdx.x;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemLinks<double, NT> lk;
+    lk.base = reinterpret_cast<cplx<double>*>(smem_raw);
+
+    unsigned int acc = 0;
+    if (s < g.vh) {
+        int c[4];
+        eo_coords(g, parity, s, c);
+        int sb[4];
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) sb[mu] = eo_neighbor(g, c, mu, -1);
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            const cplx<double>* src = U + lidx(g, mu, parity, 0, s);
+#pragma unroll 1
+            for (int e = 0; e < 9; ++e) cp_async<sizeof(cplx<double>)>(&lk(mu, e), src + (size_t)e * g.vh);
+        }
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            const cplx<double>* src = U + lidx(g, mu, parity ^ 1, 0, sb[mu]);
+#pragma unroll 1
+            for (int e = 0; e < 9; ++e) cp_async<sizeof(cplx<double>)>(&lk(4 + mu, e), src + (size_t)e * g.vh);
+        }
+#pragma unroll
+        for (int e = 0; e < 9; ++e) cp_async<sizeof(cplx<double>)>(&lk(8, e), &G[gidx(g, parity, e, s)]);
+        cp_async_wait_all();
+
+        const unsigned long long x =
+            (unsigned long long)c[0] +
+            (unsigned long long)g.n[0] * (c[1] + (unsigned long long)g.n[1] * (c[2] + (unsigned long long)g.n[2] * c[3]));
+        const double T = an.T, eps = an.eps;
+#pragma unroll 1
+        for (int sg = 0; sg < 3; ++sg) {
+            const int P = sg == 2 ? 1 : 0, Q = sg == 0 ? 1 : 2;
+            double A[4][4], b[4];
+            local_problem<double>(lk, P, Q, 3 - P - Q, A, b);
+            double cur[4] = {1.0, 0.0, 0.0, 0.0};
+            double Fcur = local_quadratic(A, b, cur);
+#pragma unroll 1
+            for (int h = 0; h < an.nhit; ++h) {
+                unsigned long long w[4] = {x, (unsigned long long)an.sweep, (unsigned long long)(sg * an.nhit + h),
+                                           (unsigned long long)f};
+                philox4x64_10(w, an.seed, 0ull);
+                const double v1 = __dmul_rn(eps, __dsub_rn(__dmul_rn(2.0, unit_interval(w[0])), 1.0));
+                const double v2 = __dmul_rn(eps, __dsub_rn(__dmul_rn(2.0, unit_interval(w[1])), 1.0));
+                const double v3 = __dmul_rn(eps, __dsub_rn(__dmul_rn(2.0, unit_interval(w[2])), 1.0));
+                const double a0 =
+                    __dsqrt_rn(__dsub_rn(1.0, __dadd_rn(__dadd_rn(__dmul_rn(v1, v1), __dmul_rn(v2, v2)), __dmul_rn(v3, v3))));
+                // candidate = proposal * current (SU(2) product in (a0, a) form)
+                double cand[4];
+                cand[0] = a0 * cur[0] - (v1 * cur[1] + v2 * cur[2] + v3 * cur[3]);
+                cand[1] = a0 * cur[1] + cur[0] * v1 - (v2 * cur[3] - v3 * cur[2]);
+                cand[2] = a0 * cur[2] + cur[0] * v2 - (v3 * cur[1] - v1 * cur[3]);
+                cand[3] = a0 * cur[3] + cur[0] * v3 - (v1 * cur[2] - v2 * cur[1]);
+                const double Fc = local_quadratic(A, b, cand);
+                const double dF = Fc - Fcur;
+                if (dF >= 0.0 || unit_interval(w[3]) < exp(dF / T)) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) cur[k] = cand[k];
+                    Fcur = Fc;
+                    ++acc;
+                }
+            }
+            const double inv = rsqrt(cur[0] * cur[0] + cur[1] * cur[1] + cur[2] * cur[2] + cur[3] * cur[3]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) cur[k] *= inv;
+            apply_subgroup<double>(lk, P, Q, cur);
+            asm volatile("" ::: "memory");
+        }
+
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            cplx<double>* dst = U + lidx(g, mu, parity, 0, s);
+#pragma unroll 1
+            for (int e = 0; e < 9; ++e) dst[(size_t)e * g.vh] = lk(mu, e);
+        }
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            cplx<double>* dst = U + lidx(g, mu, parity ^ 1, 0, sb[mu]);
+#pragma unroll 1
+            for (int e = 0; e < 9; ++e) dst[(size_t)e * g.vh] = lk(4 + mu, e);
+        }
+#pragma unroll
+        for (int e = 0; e < 9; ++e) G[gidx(g, parity, e, s)] = lk(8, e);
+    }
+    const unsigned int w = __reduce_add_sync(0xffffffffu, acc);
+    if ((threadIdx.x & 31) == 0 && w) atomicAdd(&an.accepted[f], (unsigned long long)w);
 }
 
 // ---------------------------------------------------------------------------
@@ -1563,6 +1740,48 @@ int time_halfsweep(void* U, void* G, const Geom& g, int parity, int nreps, int f
     cudaEventDestroy(e1);
     MCG_CK(cudaGetLastError());
     *ms = (float)(total / std::max(1, nreps));
+    return 0;
+}
+
+int run_anneal(void* U, void* G, const Geom& g, int nfields, const double* T, int nsweeps, long long first_sweep,
+               int nhit, double eps, unsigned long long seed, long long* accepted_host, cudaStream_t st) {
+    constexpr int NT = 128;
+    const size_t smem = halfsweep_smem_f64(NT);
+    static bool prepared = false;
+    int rc = 0;
+    if (!prepared) {
+        if ((rc = raise_smem(k_anneal_halfsweep<NT>, smem))) return rc;
+        prepared = true;
+    }
+    unsigned long long* d_acc =
+        (unsigned long long*)scratch_device("anneal.acc", sizeof(unsigned long long) * nfields, &rc);
+    if (rc) return rc;
+    unsigned long long* h_acc =
+        (unsigned long long*)scratch_host("anneal.acc", sizeof(unsigned long long) * nfields, &rc);
+    if (rc) return rc;
+    MCG_CK(cudaMemsetAsync(d_acc, 0, sizeof(unsigned long long) * nfields, st));
+    AnnealArgs an;
+    an.U = (cplx<double>*)U;
+    an.G = (cplx<double>*)G;
+    an.g = g;
+    an.nhit = nhit;
+    an.eps = eps;
+    an.seed = seed;
+    an.accepted = d_acc;
+    const dim3 grid((g.vh + NT - 1) / NT, nfields);
+    for (int k = 0; k < nsweeps; ++k) {
+        an.T = T[k];
+        an.sweep = first_sweep + k;
+        for (int parity = 0; parity < 2; ++parity) k_anneal_halfsweep<NT><<<grid, NT, smem, st>>>(an, parity);
+        MCG_CK(cudaGetLastError());
+    }
+    note_launches(2LL * nsweeps);
+    if ((rc = launch_reunitarise(U, 0, MCG_F64, g, nfields, st))) return rc;
+    if ((rc = launch_reunitarise(G, 1, MCG_F64, g, nfields, st))) return rc;
+    MCG_CK(cudaMemcpyAsync(h_acc, d_acc, sizeof(unsigned long long) * nfields, cudaMemcpyDeviceToHost, st));
+    MCG_CK(cudaStreamSynchronize(st));
+    if (accepted_host)
+        for (int f = 0; f < nfields; ++f) accepted_host[f] = (long long)h_acc[f];
     return 0;
 }
 

@@ -85,6 +85,7 @@ def _load() -> ctypes.CDLL:
         "mcg_reunitarise": ([P, I, L, P], I),
         "mcg_smear": ([P, P, L, D, D, I, P], I),
         "mcg_fix": ([P, P, L, PR, P, P, P, P], I),
+        "mcg_anneal": ([P, P, L, P, I, ctypes.c_longlong, I, D, ctypes.c_ulonglong, P, P], I),
         "mcg_center_project": ([P, P, P, L, P], I),
         "mcg_vortex_remove": ([P, P, P, P, L, P], I),
         "mcg_wilson_loops": ([P, L, I, I, P, P], I),
@@ -122,7 +123,7 @@ EXPORTS = ("mcg_version", "mcg_last_error", "mcg_release", "mcg_pack_links", "mc
            "mcg_plaquette_static", "mcg_set_sweep_block", "mcg_get_sweep_block", "mcg_fix_batch",
            "mcg_gribov_search", "mcg_smear_backward_step", "mcg_functional_matrix_grad", "mcg_grad_R",
            "mcg_ascent_step", "mcg_vortex_remove", "mcg_wilson_loops",
-           "mcg_wilson_loops_offaxis")
+           "mcg_wilson_loops_offaxis", "mcg_anneal")
 
 
 def library() -> ctypes.CDLL:
@@ -358,6 +359,33 @@ def mcg_center_project(U: torch.Tensor, dims, Z: torch.Tensor | None = None, str
     _check("mcg_center_project",
            _lib.mcg_center_project(_ptr(U), _ptr(Z), counts, lattice(dims, nf, precision_of(U)), _stream(stream)))
     return Z, [list(counts[7 * f: 7 * f + 7]) for f in range(nf)]
+
+
+def anneal_schedule(T0: float, T1: float, nsweeps: int) -> list:
+    """Geometric temperatures from T0 (first sweep) to T1 (last sweep)."""
+    if nsweeps < 1:
+        return []
+    if nsweeps == 1:
+        return [float(T0)]
+    r = (float(T1) / float(T0)) ** (1.0 / (nsweeps - 1))
+    return [float(T0) * r**k for k in range(nsweeps)]
+
+
+def mcg_anneal(U: torch.Tensor, G: torch.Tensor, dims, T, nhit: int = 4, eps: float = 0.3, seed: int = 0,
+               first_sweep: int = 0, stream=None) -> dict:
+    """Simulated annealing of the gauge transform in place on U and G (FP64),
+    one sweep per temperature in T (see `anneal_schedule`); run mcg_fix
+    afterwards to reach the nearest maximum.  Returns dict(accepted,
+    acceptance) per field."""
+    _need_cuda(U, G)
+    nf = U.shape[0]
+    Ts = (ctypes.c_double * max(1, len(T)))(*[float(t) for t in T])
+    acc = (ctypes.c_longlong * nf)()
+    _check("mcg_anneal", _lib.mcg_anneal(_ptr(U), _ptr(G), lattice(dims, nf, precision_of(U)), Ts, len(T),
+                                         int(first_sweep), int(nhit), float(eps), int(seed) & ((1 << 64) - 1), acc,
+                                         _stream(stream)))
+    hits = len(T) * 3 * int(nhit) * 2 * vh_of(dims)
+    return dict(accepted=list(acc), acceptance=[a / hits if hits else 0.0 for a in acc])
 
 
 def mcg_vortex_remove(U: torch.Tensor, Z: torch.Tensor, dims, removed: bool = True, center: bool = True,

@@ -95,3 +95,30 @@ def test_argument_validation_of_observables_and_params_without_gpu(mcg):
     for w in (0.0, 2.0, float("nan")):
         p = mcg.Params(fp32_sweeps=10, fp32_overrelax=w).c()
         refused(lib.mcg_fix(one, two, ctypes.byref(good), ctypes.byref(p), None, None, None, None), "overrelax")
+
+
+def test_anneal_argument_validation_without_gpu(mcg):
+    """mcg_anneal refuses bad arguments with MCG_BAD_ARG before device work."""
+    lib = mcg.library()
+    one, two = ctypes.c_void_p(1), ctypes.c_void_p(1 << 40)
+    T = (ctypes.c_double * 3)(1.0, 0.5, 0.1)
+
+    def refused(lat, T_, n, first, nhit, eps, why, U=one, G=two):
+        rc = lib.mcg_anneal(U, G, ctypes.byref(lat), T_, n, first, nhit, eps, 7, None, None)
+        assert rc == 3, rc
+        assert why.encode() in lib.mcg_last_error(), lib.mcg_last_error()
+
+    f64 = mcg.lattice((4, 4, 4, 6))
+    refused(mcg.lattice((4, 4, 4, 6), 1, mcg.F32), T, 3, 0, 1, 0.3, "FP64")
+    refused(mcg.lattice((4, 4, 4, 6), 70000), T, 3, 0, 1, 0.3, "65535")
+    refused(f64, None, 3, 0, 1, 0.3, "null pointer")
+    refused(f64, T, 3, 0, 1, 0.3, "null pointer", G=None)
+    refused(f64, T, -1, 0, 1, 0.3, ">= 0")
+    refused(f64, T, 3, -2, 1, 0.3, ">= 0")
+    refused(f64, T, 3, 0, 0, 0.3, "nhit")
+    for eps in (0.0, 0.51, float("nan")):
+        refused(f64, T, 3, 0, 2, eps, "eps")
+    for bad in (0.0, -1.0, float("nan")):
+        Tb = (ctypes.c_double * 3)(1.0, bad, 0.1)
+        refused(f64, Tb, 3, 0, 2, 0.3, "temperature")
+    refused(f64, T, 3, 0, 2, 0.3, "overlap", U=one, G=ctypes.c_void_p(1 + 4096))

@@ -1,0 +1,112 @@
+"""GPU parity for simulated annealing of the gauge transform (the Gribov-copy
+search variant of Sec. IV) against the oracle, through the C ABI.  Both sides
+draw the same Philox4x64-10 words and build the same proposals (unfused FP64
+on both sides); the kernel scores hits by the local quadratic form, the oracle
+by traces over the eight links, so the acceptance counts must agree exactly
+and links and Omega to rounding (1e-11)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0807_0264_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+SEED = 0x123456789ABC
+
+
+@pytest.fixture(scope="module")
+def mcg():
+    from paper_0807_0264_gb300 import mcg as m
+
+    return m
+
+
+def pack_links(mcg, Us, dims):
+    return mcg.mcg_pack_links(torch.from_numpy(np.stack(Us)).to("cuda"), dims)
+
+
+def pack_gauge(mcg, Gs, dims):
+    return mcg.mcg_pack_gauge(torch.from_numpy(np.stack(Gs)).to("cuda"), dims)
+
+
+def run_both(mcg, dims, nf, T, nhit, eps, first_sweep=0, seed=SEED):
+    Us = [synth.make_field(dims, 0.6, 40 + f) for f in range(nf)]
+    Gs = [synth.random_gauge(dims, 50 + f) for f in range(nf)]
+    Ud, Gd = pack_links(mcg, Us, dims), pack_gauge(mcg, Gs, dims)
+    res = mcg.mcg_anneal(Ud, Gd, dims, T, nhit, eps, seed, first_sweep=first_sweep)
+    Ug = mcg.mcg_unpack_links(Ud, dims).cpu().numpy()
+    Gg = mcg.mcg_unpack_gauge(Gd, dims).cpu().numpy()
+    ref = [oracle.anneal(dims, Us[f], Gs[f], T, nhit, eps, seed, first_sweep=first_sweep, field=f) for f in range(nf)]
+    return Us, res, Ug, Gg, ref
+
+
+# vh = 192 (two blocks of 128, ragged), 576 with two fields, 3072 (24 full blocks)
+@pytest.mark.parametrize("dims,nf", [((4, 4, 4, 6), 1), ((6, 6, 4, 8), 2), ((8, 8, 8, 12), 1)])
+def test_anneal_matches_oracle(mcg, dims, nf):
+    T, nhit, eps = [5.0, 2.0, 0.8, 0.3], 3, 0.3
+    _, res, Ug, Gg, ref = run_both(mcg, dims, nf, T, nhit, eps, first_sweep=7)
+    V = int(np.prod(dims))
+    for f in range(nf):
+        Uo, Go, acc = ref[f]
+        assert res["accepted"][f] == acc
+        assert 0 < acc < len(T) * V * 3 * nhit
+        assert np.abs(Ug[f] - Uo).max() < 1e-11
+        assert np.abs(Gg[f] - Go).max() < 1e-11
+    if nf > 1:  # the field index is part of the counter
+        assert res["accepted"][0] != res["accepted"][1] or np.abs(Gg[0] - Gg[1]).max() > 0.1
+
+
+def test_anneal_full_workload_size_one_sweep(mcg):
+    dims = (20, 20, 20, 40)
+    _, res, Ug, Gg, ref = run_both(mcg, dims, 1, [1.0], 2, 0.3)
+    Uo, Go, acc = ref[0]
+    assert res["accepted"][0] == acc
+    assert np.abs(Ug[0] - Uo).max() < 1e-11
+    assert np.abs(Gg[0] - Go).max() < 1e-11
+
+
+def test_infinite_temperature_accepts_every_hit(mcg):
+    dims = (6, 4, 4, 6)
+    V = int(np.prod(dims))
+    _, res, Ug, Gg, ref = run_both(mcg, dims, 1, [1e300, 1e300], 2, 0.45)
+    assert res["accepted"][0] == 2 * V * 3 * 2 == ref[0][2]
+    assert np.abs(Gg[0] - ref[0][1]).max() < 1e-11
+
+
+def test_first_sweep_continues_the_stream(mcg):
+    dims = (4, 4, 4, 6)
+    U = synth.make_field(dims, 0.6, 3)
+    T = [3.0, 1.0, 0.2]
+    Ua, Ga = pack_links(mcg, [U], dims), mcg.identity_gauge(dims)
+    Ub, Gb = pack_links(mcg, [U], dims), mcg.identity_gauge(dims)
+    ra = mcg.mcg_anneal(Ua, Ga, dims, T, 2, 0.3, 5)
+    r1 = mcg.mcg_anneal(Ub, Gb, dims, T[:1], 2, 0.3, 5)
+    r2 = mcg.mcg_anneal(Ub, Gb, dims, T[1:], 2, 0.3, 5, first_sweep=1)
+    assert ra["accepted"][0] == r1["accepted"][0] + r2["accepted"][0]
+    assert (Ua - Ub).abs().max().item() < 1e-12 and (Ga - Gb).abs().max().item() < 1e-12
+
+
+def test_anneal_then_fix_stays_on_the_orbit_and_converges(mcg):
+    dims = (8, 8, 8, 8)
+    U0 = synth.make_field(dims, 0.6, 21)
+    Ud, Gd = pack_links(mcg, [U0], dims), mcg.identity_gauge(dims)
+    res = mcg.mcg_anneal(Ud, Gd, dims, mcg.anneal_schedule(2.0, 0.02, 30), 4, 0.3, 9)
+    assert 0.0 < res["acceptance"][0] < 1.0
+    out = mcg.mcg_fix(Ud, Gd, dims, mcg.Params(tol=1e-10, max_sweeps=6000, fp32_sweeps=6000, fp32_tol=1e-10,
+                                               fp32_overrelax=1.7))
+    assert out["converged"]
+    G = mcg.mcg_unpack_gauge(Gd, dims)[0].cpu().numpy()
+    U = mcg.mcg_unpack_links(Ud, dims)[0].cpu().numpy()
+    assert np.abs(oracle.apply_gauge(dims, U0, G) - U).max() < 1e-10
+    assert abs(mcg.mcg_plaquette(Ud, dims)[0] - oracle.plaquette(dims, U0)) < 1e-12
+
+
+def test_anneal_rejects_fp32_fields(mcg):
+    dims = (4, 4, 4, 6)
+    U32 = mcg.mcg_pack_links(torch.from_numpy(synth.make_field(dims, 0.6, 1)).to("cuda").unsqueeze(0), dims, mcg.F32)
+    G32 = mcg.identity_gauge(dims, precision=mcg.F32)
+    with pytest.raises(Exception, match="FP64"):
+        mcg.mcg_anneal(U32, G32, dims, [1.0], 1, 0.3, 0)
