@@ -63,6 +63,10 @@ def parse():
                     help="the batched Gribov-copy search at full size instead of the main step: 16 x 12^4, "
                          "16 x 16^3 x 32 and 16 x 20^3 x 40 configurations with 8 random initial transforms "
                          "each (384 fields, 60.4 M sites), fields generated on the GPU; one JSON line")
+    ap.add_argument("--anneal", action="store_true",
+                    help="simulated annealing as a Gribov-copy search variant instead of the main step: plain "
+                         "relaxation against annealing (200 sweeps, T 2 -> 0.02, 4 hits) + relaxation on 16 x 12^4 "
+                         "configurations, and the annealing sweep timed at 20^3 x 40; one JSON line")
     ap.add_argument("--profile-kernel", choices=["f32", "f64"],
                     help="time the FP32 (or FP64) half-sweep on the field after 300 FP32 sweeps (the regime the FP32 "
                          "phase runs in), odd then even sites, 3 launches each, L2 flushed: the launches for an ncu "
@@ -331,6 +335,82 @@ def run_gribov(args, mcg, dev, rank):
             "gpu_launches": mcg.mcg_kernel_launches() - launches0}), flush=True)
 
 
+ANNEAL_T = (2.0, 0.02, 200)  # first and last temperature, sweeps (geometric schedule)
+
+
+def anneal_flop_per_site(nhit: int) -> int:
+    """FP64 flops of one annealing site update: per subgroup the local problem
+    (8 links x 64), the move applied to 9 matrices (756), the start value of
+    the quadratic form and the normalisation (56), and per hit the proposal,
+    SU(2) product, quadratic form and acceptance (~110)."""
+    return 3 * (512 + 756 + 56 + 110 * nhit)
+
+
+def run_anneal(args, mcg, dev, rank):
+    import torch
+
+    from paper_0807_0264_gb300 import analysis
+
+    T0, T1, ns = ANNEAL_T
+    sched = mcg.anneal_schedule(T0, T1, ns)
+    # (1) the annealing sweep at the 20^3 x 40 workload size, per sweep, from
+    # the difference of a 12-sweep and a 2-sweep call (the fixed cost of a
+    # call -- re-unitarisation and the counter read -- cancels)
+    dims = (20, 20, 20, 40)
+    U0 = mcg.mcg_pack_links(_gpu_field(dims, synth_w(), 0, dev), dims)
+    sites = dims[0] * dims[1] * dims[2] * dims[3]
+    timing = {}
+    for nhit in (1, 4):
+        ms = {}
+        for nsw in (2, 12, 2, 12):
+            U = U0.clone()
+            G = mcg.identity_gauge(dims)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = mcg.mcg_anneal(U, G, dims, [1.0] * nsw, nhit, 0.3, 1)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms[nsw] = e0.elapsed_time(e1)  # the second (warm) call of each length is kept
+        per_sweep = (ms[12] - ms[2]) / 10.0
+        flop = anneal_flop_per_site(nhit) * sites
+        timing[f"nhit{nhit}"] = {"ms_per_sweep": per_sweep, "site_updates_per_s": sites / (per_sweep / 1e3),
+                                 "fp64_tflops_est": flop / (per_sweep / 1e3) / 1e12,
+                                 "acceptance_at_T_1": r["acceptance"][0]}
+    del U0
+    # (2) the study on 16 configurations of 12^4
+    dims = (12, 12, 12, 12)
+    nconf = int(os.environ.get("MCG_ANNEAL_CONFIGS", "16"))
+    Us = torch.cat([_gpu_field(dims, synth_w(), 100 + c, dev) for c in range(nconf)])
+    U = mcg.mcg_pack_links(Us, dims)
+    del Us
+    p = mcg.Params(tol=1e-10, max_sweeps=20000, check_every=25, reunit_every=50, fp32_sweeps=20000, fp32_tol=5e-11,
+                   fp32_window=25, fp32_overrelax=OMEGA, fp64_solve32=1)
+    t = time.perf_counter()
+    st = analysis.anneal_study(U, dims, p, sched, nhit=4, eps=0.3, seed=7)
+    t = time.perf_counter() - t
+    pl, an = st["plain"], st["annealed"]
+    tb = st["tables"]
+
+    def mean(x):
+        return sum(x) / len(x)
+
+    if rank == 0:
+        print(json.dumps({
+            "mode": "anneal_study", "schedule": {"T0": T0, "T1": T1, "sweeps": ns, "nhit": 4, "eps": 0.3},
+            "sweep_timing_20x20x20x40": timing,
+            "configs": nconf, "dims": list(dims), "seconds": t,
+            "V_mean": {"plain": mean(pl["V"]), "annealed": mean(an["V"])},
+            "V_gain_mean": mean([b - a for a, b in zip(pl["V"], an["V"])]),
+            "vortices_mean": {"plain": mean(pl["vortices"]), "annealed": mean(an["vortices"])},
+            "higher_max_pct": tb["higher_max_pct"][0][1], "fewer_vortices_pct": tb["fewer_vortices_pct"][0][1],
+            "fewer_given_higher_pct": tb["fewer_given_higher_pct"][1][0],
+            "sweeps_mean": {"plain": mean(pl["sweeps"]), "annealed": mean(an["sweeps"])},
+            "converged": {"plain": pl["converged"], "annealed": an["converged"]},
+            "acceptance_mean": mean(an["acceptance"]),
+            "data": "synthetic fields generated with torch on the GPU"}), flush=True)
+
+
 def synth_w():
     from paper_0807_0264_gb300 import synth
 
@@ -365,6 +445,11 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.anneal:
+        run_anneal(args, mcg, dev, rank)
+        if dist:
+            dist.destroy_process_group()
+        return
     if args.gribov:
         run_gribov(args, mcg, dev, rank)
         if dist:

@@ -63,3 +63,32 @@ def precondition_study(fields, dims, levels, params, rho: float = 0.1, eps: floa
         sw.append([r["sweeps_smeared"] + r["sweeps_fixed"] for r in res])
         conv.append([r["status"] == 0 for r in res])
     return {"V": V, "vortices": nv, "sweeps": sw, "converged": conv, "tables": transition_tables(V, nv)}
+
+
+def anneal_study(U, dims, params, T, nhit: int = 4, eps: float = 0.3, seed: int = 0) -> dict:
+    """Simulated annealing as a Gribov-copy search variant (Sec. IV): for each
+    configuration of U (an FP64 device tensor of nf fields of one lattice),
+    the relaxation `params` from Omega = 1 against annealing with the
+    temperatures T from Omega = 1 followed by the same relaxation.  Returns,
+    per variant ("plain", "annealed"), V_U, P-vortex counts, sweeps and
+    convergence (and the acceptance of the annealing), plus the Tables 2/3
+    statistics with level 0 = plain and level 1 = annealed."""
+    from . import mcg
+
+    nf = U.shape[0]
+    vol = 1
+    for d in dims:
+        vol *= d
+    out = {}
+    for name in ("plain", "annealed"):
+        Uw = U.clone()
+        G = mcg.identity_gauge(dims, nf)
+        acc = mcg.mcg_anneal(Uw, G, dims, T, nhit, eps, seed)["acceptance"] if name == "annealed" else None
+        r = mcg.mcg_fix(Uw, G, dims, params)
+        counts = mcg.mcg_center_project(Uw, dims)[1]
+        out[name] = {"V": [R / (36.0 * vol) for R in r["R"]], "vortices": [c[0] for c in counts],
+                     "sweeps": list(r["sweeps"]), "converged": bool(r["converged"]), "acceptance": acc}
+    V = [[p, a] for p, a in zip(out["plain"]["V"], out["annealed"]["V"])]
+    n = [[p, a] for p, a in zip(out["plain"]["vortices"], out["annealed"]["vortices"])]
+    out["tables"] = transition_tables(V, n)
+    return out

@@ -37,3 +37,33 @@ def test_precondition_study_matches_oracle():
     ref = transition_tables(Vo, no)
     for k in ("fewer_vortices_pct", "higher_max_pct", "fewer_given_higher_pct", "vortex_reduction_pct"):
         np.testing.assert_allclose(st["tables"][k], ref[k], equal_nan=True)
+
+
+def test_anneal_study_matches_oracle():
+    """Simulated annealing as a Gribov-copy search variant: the plain and the
+    annealed-then-relaxed maxima and P-vortex counts of anneal_study equal
+    the oracle's anneal and relaxation run per configuration."""
+    from paper_0807_0264_gb300 import mcg
+    from paper_0807_0264_gb300.analysis import anneal_study
+
+    dims = (4, 4, 4, 4)
+    fields = [synth.make_field(dims, 0.9, seed) for seed in (41, 42, 43)]
+    U = mcg.mcg_pack_links(torch.from_numpy(np.stack(fields)).cuda(), dims)
+    T = mcg.anneal_schedule(2.0, 0.05, 10)
+    p = mcg.Params(tol=1e-10, max_sweeps=1500)
+    st = anneal_study(U, dims, p, T, nhit=2, eps=0.3, seed=3)
+    V4 = 36.0 * 256
+    for f, Uc in enumerate(fields):
+        plain = oracle.fix(dims, Uc, None, tol=1e-10, max_sweeps=1500, reunit_every=50)
+        Ua, Ga, acc = oracle.anneal(dims, Uc, synth.identity_gauge(dims), T, 2, 0.3, 3, field=f)
+        ann = oracle.fix(dims, Ua, Ga, tol=1e-10, max_sweeps=1500, reunit_every=50)
+        for name, o in (("plain", plain), ("annealed", ann)):
+            assert st[name]["sweeps"][f] == o["sweeps"]
+            assert abs(st[name]["V"][f] - o["R_hist"][-1] / V4) < 1e-11
+            assert st[name]["vortices"][f] == oracle.vortex_count(dims, oracle.center_project(dims, o["U"]))[0]
+        assert st["annealed"]["acceptance"][f] == acc / (len(T) * 256 * 3 * 2)
+    V = [[a, b] for a, b in zip(st["plain"]["V"], st["annealed"]["V"])]
+    n = [[a, b] for a, b in zip(st["plain"]["vortices"], st["annealed"]["vortices"])]
+    ref = transition_tables(V, n)
+    assert np.array_equal(np.nan_to_num(st["tables"]["higher_max_pct"], nan=-1),
+                          np.nan_to_num(ref["higher_max_pct"], nan=-1))
