@@ -66,7 +66,8 @@ def parse():
     ap.add_argument("--anneal", action="store_true",
                     help="simulated annealing as a Gribov-copy search variant instead of the main step: plain "
                          "relaxation against annealing (200 sweeps, T 2 -> 0.02, 4 hits) + relaxation on 16 x 12^4 "
-                         "configurations, and the annealing sweep timed at 20^3 x 40; one JSON line")
+                         "configurations (MCG_ANNEAL_DIMS, MCG_ANNEAL_CONFIGS), and the annealing sweep timed at "
+                         "20^3 x 40; one JSON line")
     ap.add_argument("--profile-kernel", choices=["f32", "f64"],
                     help="time the FP32 (or FP64) half-sweep on the field after 300 FP32 sweeps (the regime the FP32 "
                          "phase runs in), odd then even sites, 3 launches each, L2 flushed: the launches for an ncu "
@@ -378,8 +379,9 @@ def run_anneal(args, mcg, dev, rank):
                                  "fp64_tflops_est": flop / (per_sweep / 1e3) / 1e12,
                                  "acceptance_at_T_1": r["acceptance"][0]}
     del U0
-    # (2) the study on 16 configurations of 12^4
-    dims = (12, 12, 12, 12)
+    # (2) the study: 16 configurations of 12^4 unless MCG_ANNEAL_DIMS ("nx,ny,nz,nt")
+    # and MCG_ANNEAL_CONFIGS say otherwise
+    dims = tuple(int(v) for v in os.environ.get("MCG_ANNEAL_DIMS", "12,12,12,12").split(","))
     nconf = int(os.environ.get("MCG_ANNEAL_CONFIGS", "16"))
     Us = torch.cat([_gpu_field(dims, synth_w(), 100 + c, dev) for c in range(nconf)])
     U = mcg.mcg_pack_links(Us, dims)
