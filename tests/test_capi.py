@@ -141,3 +141,12 @@ def test_anneal_argument_validation_without_gpu(mcg):
         Tb = (ctypes.c_double * 3)(1.0, bad, 0.1)
         refused(f64, Tb, 3, 0, 2, 0.3, "temperature")
     refused(f64, T, 3, 0, 2, 0.3, "overlap", U=one, G=ctypes.c_void_p(1 + 4096))
+
+
+def test_anneal_schedule_is_geometric(mcg):
+    T = mcg.anneal_schedule(2.0, 0.02, 5)
+    assert len(T) == 5 and T[0] == 2.0 and abs(T[-1] - 0.02) < 1e-15
+    r = [T[k + 1] / T[k] for k in range(4)]
+    assert max(r) - min(r) < 1e-14 and abs(r[0] - 0.1 ** 0.5) < 1e-14
+    assert mcg.anneal_schedule(3.0, 0.1, 1) == [3.0]
+    assert mcg.anneal_schedule(3.0, 0.1, 0) == []
