@@ -138,3 +138,12 @@ def test_first_sweep_continues_the_stream_and_the_field_stays_on_the_orbit():
     # gauge invariance: the annealed field is U0 transformed by the returned Omega
     assert np.abs(oracle.apply_gauge(DIMS, U0, G) - U).max() < 1e-12
     assert abs(oracle.plaquette(DIMS, U) - oracle.plaquette(DIMS, U0)) < 1e-13
+
+
+def test_zero_sweeps_only_reunitarise():
+    U0 = synth.make_field(DIMS, 0.6, 13)
+    G0 = synth.random_gauge(DIMS, 14)
+    U, G, acc = oracle.anneal(DIMS, U0, G0, [], 2, 0.3, 1)
+    assert acc == 0
+    assert np.abs(U - oracle.reunitarise(U0)).max() == 0 and np.abs(G - oracle.reunitarise(G0)).max() == 0
+    assert np.abs(U - U0).max() < 1e-14
