@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--levels", type=int, nargs="+", default=list(LEVELS))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-observables", action="store_true",
-                    help="skip the Sec. III.D measurement (vortex removal, Wilson loops) on the level-0 result")
+                    help="skip the Sec. III.A measurement (vortex removal, Wilson loops) on the level-0 result")
     ap.add_argument("--profile-slice", action="store_true",
                     help="one bench step with sweeps capped (FP32 100 + FP64 1 per fix, levels 0 and 4, block sizes "
                          "128): the same kernels and launch shapes in ~1000 launches, for an ncu launch list")
@@ -663,7 +663,7 @@ def main():
                        "method": "FP32 sweeps inside a fix, L2 not flushed (working set 138 MB > 129 MB L2); the "
                                  "end-of-sweep kernel counted in the sweep"}
 
-    # Sec. III.D on the level-0 result: center decomposition (vortex-removed
+    # Sec. III.A on the level-0 result: center decomposition (vortex-removed
     # and vortex-only fields) and on-axis Wilson loops of the three fields
     sec3d = None
     if not args.no_observables:

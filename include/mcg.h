@@ -206,7 +206,7 @@ int mcg_fix(void* U, void* G, const mcg_lattice* lat, const mcg_params* params, 
 
 /*
  * Simulated annealing of the gauge transform: a Gribov-copy search variant
- * run ahead of mcg_fix (Sec. IV names annealing as the route to higher maxima
+ * run ahead of mcg_fix (Sec. III.B names annealing as the route to higher maxima
  * taken in SU(2); the paper does not specify it, so this is the library's
  * reading).  For k = 0 .. nsweeps-1: an even then an odd checkerboard
  * half-sweep at temperature T[k]; at each site and for the subgroups (0,1),
@@ -240,7 +240,7 @@ int mcg_center_project(const void* U, int8_t* Z, long long* counts, const mcg_la
                        cudaStream_t stream);
 
 /*
- * Center decomposition of a fixed field (Sec. III.D): with Z the center
+ * Center decomposition of a fixed field (Sec. III.A): with Z the center
  * sectors of U (from mcg_center_project, same batch), U_removed <- Z^dag U
  * (the vortex-removed field U' of the paper) and U_center <- Z times the
  * identity (the vortex-only field), in the link layout and precision of U.
@@ -254,7 +254,7 @@ int mcg_vortex_remove(const void* U, const int8_t* Z, void* U_removed, void* U_c
                       cudaStream_t stream);
 
 /*
- * Planar Wilson loops (Sec. III.D): W(R, T) is the mean over all V
+ * Planar Wilson loops (Sec. III.A): W(R, T) is the mean over all V
  * translations and the three spatial axes i of
  *   (1/3) Re tr [ S_i^R(x) S_t^T(x + R i) S_i^R(x + T t)^dag S_t^T(x)^dag ],
  * S_mu^L(x) = U_mu(x) U_mu(x+mu) ... U_mu(x+(L-1)mu), t the fourth axis
@@ -267,7 +267,7 @@ int mcg_vortex_remove(const void* U, const int8_t* Z, void* U_removed, void* U_c
 int mcg_wilson_loops(const void* U, const mcg_lattice* lat, int Rmax, int Tmax, double* W_out, cudaStream_t stream);
 
 /*
- * Wilson loops with off-axis spatial sides (Sec. III.D, which uses off-axis
+ * Wilson loops with off-axis spatial sides (Sec. III.A, which uses off-axis
  * paths for non-integer separations without fixing them; this library's
  * reading): for each integer vector r of `vectors` (host, nvec x 3) and
  * 1 <= T <= Tmax (at most N_t), the mean over all translations x and all

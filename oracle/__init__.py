@@ -331,7 +331,7 @@ def smear_backward(dims, U, Gout, rho: float, eps: float, nsteps: int) -> np.nda
 
 
 def vortex_remove(dims, U, m) -> np.ndarray:
-    """Vortex-removed field U' = Z^dag U (Sec. III.D) for center sectors m (V, 4)."""
+    """Vortex-removed field U' = Z^dag U (Sec. III.A) for center sectors m (V, 4)."""
     U = _cfield(U)
     m = np.ascontiguousarray(m, dtype=np.int8)
     out = np.empty_like(U)
@@ -340,7 +340,7 @@ def vortex_remove(dims, U, m) -> np.ndarray:
 
 
 def center_links(dims, m) -> np.ndarray:
-    """The vortex-only field Z = exp(2 pi i m / 3) * 1 (Sec. III.D), shape (V, 4, 3, 3)."""
+    """The vortex-only field Z = exp(2 pi i m / 3) * 1 (Sec. III.A), shape (V, 4, 3, 3)."""
     m = np.ascontiguousarray(m, dtype=np.int8)
     out = np.empty((m.shape[0], 4, 3, 3), np.complex128)
     _load().orc_center_links(_p(_dims(dims)), _p(m), _p(out))
@@ -348,7 +348,7 @@ def center_links(dims, m) -> np.ndarray:
 
 
 def wilson_loops(dims, U, Rmax: int, Tmax: int) -> np.ndarray:
-    """Planar Wilson loops W(R, T) (Sec. III.D), R spatial (averaged over x, y, z),
+    """Planar Wilson loops W(R, T) (Sec. III.A), R spatial (averaged over x, y, z),
     T along t, averaged over all translations; shape (Rmax, Tmax)."""
     U = _cfield(U)
     out = np.zeros(Rmax * Tmax)
@@ -358,7 +358,7 @@ def wilson_loops(dims, U, Rmax: int, Tmax: int) -> np.ndarray:
 
 def wilson_loops_offaxis(dims, U, vectors, Tmax: int) -> np.ndarray:
     """Wilson loops with spatial side r (any integer 3-vector, off-axis
-    allowed) and temporal side T (Sec. III.D), averaged over all translations
+    allowed) and temporal side T (Sec. III.A), averaged over all translations
     and the distinct cubic images of r; shape (len(vectors), Tmax)."""
     U = _cfield(U)
     v = np.ascontiguousarray(np.asarray(vectors, dtype=np.int32).reshape(-1, 3))

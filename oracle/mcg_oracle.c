@@ -23,7 +23,7 @@
  *   - the stop rule is V_U(k) - V_U(k-1) < tol on the normalised functional;
  *   - links and Omega are re-unitarised every reunit_every sweeps;
  *   - stout smearing is isotropic in 4D and updates all links at once.
- *   - simulated annealing (named in Sec. IV as a way to higher maxima, not
+ *   - simulated annealing (named in Sec. III.B as a way to higher maxima, not
  *     specified): Metropolis hits on the same subgroup moves, proposals and
  *     acceptances drawn from Philox4x64-10 with a counter per (site, sweep,
  *     subgroup and hit, field), temperatures given per sweep (orc_anneal).
@@ -515,7 +515,7 @@ int orc_fix(const int* dims, cplx* U, cplx* Om, double tol, int max_sweeps, int 
 }
 
 /* ------------------------------------------------------------------ */
-/* Simulated annealing of the gauge transform (Sec. IV: the SU(2) route  */
+/* Simulated annealing of the gauge transform (Sec. III.B: the SU(2) route  */
 /* to higher maxima, here for the SU(3) functional as a Gribov-copy     */
 /* search variant ahead of the relaxation)                              */
 /* ------------------------------------------------------------------ */
@@ -864,7 +864,7 @@ long long orc_vortex_count(const int* dims, const int8_t* m, long long* per_plan
 }
 
 /* ------------------------------------------------------------------ */
-/* Vortex removal, the vortex-only field and Wilson loops (Sec. III.D)   */
+/* Vortex removal, the vortex-only field and Wilson loops (Sec. III.A)   */
 /* ------------------------------------------------------------------ */
 
 /* The center element exp(2 pi i m / 3) of sector m as (cos, sin); the
@@ -880,7 +880,7 @@ static void center_phase(int m, double* c, double* s) {
 }
 
 /* Vortex-removed field U'_mu(x) = Z_mu(x)^dag U_mu(x), Z the center element
- * of the link's sector m (Sec. III.D): every entry u becomes conj(Z) u, i.e.
+ * of the link's sector m (Sec. III.A): every entry u becomes conj(Z) u, i.e.
  * re' = c re + s im, im' = c im - s re (products and sums written out, never
  * fused). */
 void orc_vortex_remove(const int* dims, const cplx* U, const int8_t* m, cplx* Uout) {
@@ -919,7 +919,7 @@ static void line_product(const geom* g, const cplx* U, long x, int mu, int L, cp
     }
 }
 
-/* Planar Wilson loops W(R, T) (Sec. III.D): R links along a spatial axis i
+/* Planar Wilson loops W(R, T) (Sec. III.A): R links along a spatial axis i
  * in {x, y, z}, T links along t (mu = 3), averaged over all V translations
  * and the three spatial axes,
  *   W(R,T) = < (1/3) Re tr [ S_i^R(x) S_t^T(x + R i) S_i^R(x + T t)^dag S_t^T(x)^dag ] >,
@@ -960,7 +960,7 @@ void orc_wilson_loops(const int* dims, const cplx* U, int Rmax, int Tmax, double
     free(part);
 }
 
-/* Off-axis spatial paths (Sec. III.D mentions off-axis loops without
+/* Off-axis spatial paths (Sec. III.A mentions off-axis loops without
  * fixing the paths; reading): the path from x to x + r, r = (r0, r1, r2),
  * takes L = |r0| + |r1| + |r2| unit steps; step k (1-based) goes along the
  * axis j with the largest deficit k |r_j| / L - n_j (n_j: steps taken along j
@@ -1029,7 +1029,7 @@ static int cubic_images(const int* r, int img[48][3]) {
     return n;
 }
 
-/* Wilson loops with off-axis spatial sides (Sec. III.D): for each vector
+/* Wilson loops with off-axis spatial sides (Sec. III.A): for each vector
  * r of vecs (nvec x 3) and 1 <= T <= Tmax, the mean over all translations x
  * and all distinct cubic images r' of r of
  *   (1/3) Re tr [ P_r'(x) S_t^T(x + r') P_r'(x + T t)^dag S_t^T(x)^dag ],

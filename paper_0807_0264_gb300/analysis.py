@@ -66,7 +66,7 @@ def precondition_study(fields, dims, levels, params, rho: float = 0.1, eps: floa
 
 
 def anneal_study(U, dims, params, T, nhit: int = 4, eps: float = 0.3, seed: int = 0) -> dict:
-    """Simulated annealing as a Gribov-copy search variant (Sec. IV): for each
+    """Simulated annealing as a Gribov-copy search variant (Sec. III.B): for each
     configuration of U (an FP64 device tensor of nf fields of one lattice),
     the relaxation `params` from Omega = 1 against annealing with the
     temperatures T from Omega = 1 followed by the same relaxation.  Returns,

@@ -1,4 +1,4 @@
-// Observables on the center decomposition of a fixed field (Sec. III.D): the
+// Observables on the center decomposition of a fixed field (Sec. III.A): the
 // vortex-removed field U' = Z^dag U, the vortex-only field Z, and planar
 // Wilson loops W(R, T) averaged over all translations and spatial axes.
 #include <algorithm>

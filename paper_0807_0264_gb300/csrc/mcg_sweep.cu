@@ -908,7 +908,7 @@ __global__ void __launch_bounds__(NT, 2) k_halfsweep(SweepBatch bt, int parity) 
 }
 
 // ---------------------------------------------------------------------------
-// Simulated annealing of the gauge transform (Sec. IV names annealing as the
+// Simulated annealing of the gauge transform (Sec. III.B names annealing as the
 // SU(2) route to higher maxima; here a Gribov-copy search variant run ahead
 // of the relaxation).  Each subgroup of a site gets nhit Metropolis hits on
 // the same move as the relaxation; the local problem (A, b) is built once per

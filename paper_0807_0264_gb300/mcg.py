@@ -390,7 +390,7 @@ def mcg_anneal(U: torch.Tensor, G: torch.Tensor, dims, T, nhit: int = 4, eps: fl
 
 def mcg_vortex_remove(U: torch.Tensor, Z: torch.Tensor, dims, removed: bool = True, center: bool = True,
                       stream=None):
-    """Center decomposition of a fixed field (Sec. III.D) with its center
+    """Center decomposition of a fixed field (Sec. III.A) with its center
     sectors Z: returns (U_removed = Z^dag U, U_center = Z * 1), each None when
     not requested."""
     _need_cuda(U, Z)
@@ -406,7 +406,7 @@ def mcg_vortex_remove(U: torch.Tensor, Z: torch.Tensor, dims, removed: bool = Tr
 
 
 def mcg_wilson_loops(U: torch.Tensor, dims, Rmax: int, Tmax: int, stream=None):
-    """Planar on-axis Wilson loops W(R, T) (Sec. III.D), averaged over all
+    """Planar on-axis Wilson loops W(R, T) (Sec. III.A), averaged over all
     translations and the three spatial axes; numpy array (nfields, Rmax, Tmax)."""
     import numpy as np
 
@@ -421,7 +421,7 @@ def mcg_wilson_loops(U: torch.Tensor, dims, Rmax: int, Tmax: int, stream=None):
 def mcg_wilson_loops_offaxis(U: torch.Tensor, dims, vectors, Tmax: int, stream=None):
     """Wilson loops with (possibly off-axis) spatial side r for each integer
     3-vector of `vectors`, averaged over translations and cubic images
-    (Sec. III.D); numpy array (nfields, len(vectors), Tmax)."""
+    (Sec. III.A); numpy array (nfields, len(vectors), Tmax)."""
     import numpy as np
 
     _need_cuda(U)

@@ -84,7 +84,7 @@ def test_version_and_error_codes_without_gpu(mcg):
 
 
 def test_argument_validation_of_observables_and_params_without_gpu(mcg):
-    """Invalid calls to the Sec. III.D entries and bad parameters are refused
+    """Invalid calls to the Sec. III.A entries and bad parameters are refused
     with MCG_BAD_ARG before any device work, each for its own reason."""
     lib = mcg.library()
     good = mcg.lattice((4, 4, 4, 6))

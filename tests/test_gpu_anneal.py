@@ -1,5 +1,5 @@
 """GPU parity for simulated annealing of the gauge transform (the Gribov-copy
-search variant of Sec. IV) against the oracle, through the C ABI.  Both sides
+search variant of Sec. III.B) against the oracle, through the C ABI.  Both sides
 draw the same Philox4x64-10 words and build the same proposals (unfused FP64
 on both sides); the kernel scores hits by the local quadratic form, the oracle
 by traces over the eight links, so the acceptance counts must agree exactly

@@ -1,4 +1,4 @@
-"""GPU parity for the center decomposition and the Wilson loops (Sec. III.D)
+"""GPU parity for the center decomposition and the Wilson loops (Sec. III.A)
 against the oracle, through the C ABI: vortex removal and the vortex-only
 field bit-exact in FP64 (same literals, unfused products on both sides),
 Wilson loops within summation-order rounding (1e-12 relative in FP64), at

@@ -1,7 +1,7 @@
 """GPU parity: libmcg (CUDA, sm_103a, called through the C ABI) against the
 FP64 CPU oracle on identical seeded inputs.
 
-Bars (from the method's arithmetic, see DESIGN.md):
+Bars (from the method's arithmetic):
   - FP64 sweep: per link <= 1e-11 abs after each sweep from identical input;
     final R <= 1e-9 relative over a trajectory;
   - Z3 projection and vortex counts: bit-exact on identical links;

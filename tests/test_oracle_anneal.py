@@ -1,5 +1,5 @@
 """Pins for the oracle's simulated annealing of the gauge transform (the
-Gribov-copy search variant named in Sec. IV): its Philox4x64-10 generator
+Gribov-copy search variant named in Sec. III.B): its Philox4x64-10 generator
 against numpy's, the infinite-temperature limit (every proposal accepted, so
 Omega is the product of the drawn SU(2) elements, built here from Pauli
 matrices), the first half-sweep on the unit field (all eight links of a site

@@ -1,5 +1,5 @@
 """Pins for the oracle's vortex removal, vortex-only field and Wilson loops
-(Sec. III.D): Z U' = U, the removed field projects to the trivial sector, the
+(Sec. III.A): Z U' = U, the removed field projects to the trivial sector, the
 vortex-only field's plaquette is fixed by its P-vortex density, and the
 Wilson loops reduce to the space-time plaquette at R = T = 1, are gauge
 invariant, equal 1 on a pure gauge, match the closed form of a constant
