@@ -58,6 +58,8 @@ def _load():
             lib.orc_halfsweep.argtypes = [P, P, P, I, D]
             lib.orc_halfsweep.restype = L
             lib.orc_fix.argtypes = [P, P, P, D, I, I, D, P, P, P]
+            lib.orc_halfsweep_slab.argtypes = [P, P, P, I, D, I, I, I]
+            lib.orc_halfsweep_slab.restype = L
             U64 = ctypes.c_uint64
             lib.orc_philox4x64.argtypes = [P, P, P]
             lib.orc_anneal_halfsweep.argtypes = [P, P, P, I, D, L, I, D, U64, U64]
@@ -156,6 +158,17 @@ def halfsweep(dims, U, G, parity: int, omega: float = 1.0):
     G = _cfield(G).copy()
     hard = _load().orc_halfsweep(_p(_dims(dims)), _p(U), _p(G), int(parity), float(omega))
     return U, G, int(hard)
+
+
+def halfsweep_slab(dims, U, G, parity: int, t_lo: int, t_hi: int, t_offset: int = 0, omega: float = 1.0):
+    """Half-sweep of the sites with t_lo <= t < t_hi of the local array U
+    (a slab of a larger lattice plus ghost layers) whose whole-lattice parity
+    (x+y+z+t+t_offset) mod 2 is `parity`; in place.  Returns the number of
+    hard-case solves."""
+    assert U.flags["C_CONTIGUOUS"] and U.dtype == np.complex128
+    assert G.flags["C_CONTIGUOUS"] and G.dtype == np.complex128
+    return int(_load().orc_halfsweep_slab(_p(_dims(dims)), _p(U), _p(G), int(parity), float(omega), int(t_lo),
+                                          int(t_hi), int(t_offset)))
 
 
 def fix(dims, U, G=None, tol: float = 1e-10, max_sweeps: int = 2000, reunit_every: int = 50, omega: float = 1.0):

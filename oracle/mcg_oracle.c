@@ -485,6 +485,32 @@ long orc_halfsweep(const int* dims, cplx* U, cplx* Om, int parity, double omega)
  * R_hist[0..sweeps] receives R before the first sweep and after each sweep.
  * Returns 0 if converged, 1 if max_sweeps was reached.
  */
+/* The half-sweep of one t-slab of a larger lattice (the lattice split into
+ * slabs along t, one per process).  `dims` is the local array: the slab's
+ * layers at local t in [t_lo, t_hi) plus ghost layers outside that range,
+ * which hold the links owned by the neighbouring slabs that the slab's sites
+ * touch (the backward t-links of its first layer).  Updates the sites with
+ * t_lo <= t < t_hi whose parity on the whole lattice,
+ * (x + y + z + t + t_offset) mod 2, equals `parity`, with the site update of
+ * orc_halfsweep; ghost links are read and written like any other.  Same-parity
+ * sites share no link, so slabs updated one after another (or at once, each
+ * on its own copy with the ghosts exchanged around the call) give exactly the
+ * half-sweep of the whole lattice. */
+long orc_halfsweep_slab(const int* dims, cplx* U, cplx* Om, int parity, double omega, int t_lo, int t_hi,
+                        int t_offset) {
+    geom g = make_geom(dims);
+    long hard = 0;
+#pragma omp parallel for schedule(static) reduction(+ : hard)
+    for (long x = 0; x < g.vol; ++x) {
+        int c[4];
+        coords_of(&g, x, c);
+        if (c[3] < t_lo || c[3] >= t_hi) continue;
+        if (((c[0] + c[1] + c[2] + c[3] + t_offset) & 1) != parity) continue;
+        hard += site_update(&g, U, Om, x, omega);
+    }
+    return hard;
+}
+
 int orc_fix(const int* dims, cplx* U, cplx* Om, double tol, int max_sweeps, int reunit_every, double omega,
             double* R_hist, int* sweeps_out, long* hard_out) {
     geom g = make_geom(dims);
