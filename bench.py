@@ -43,6 +43,17 @@ RHO = 0.1
 OMEGA = float(os.environ.get("MCG_OMEGA", "1.85"))
 
 
+def hbm_peak():
+    """The HBM roofline denominator: the measured copy bandwidth of this GPU
+    pool (MEASURED_PEAKS.json, written by the driver), else the profiling
+    recipe's fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s (of fallback)"
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -623,21 +634,22 @@ def main():
 
     src = os.path.join(ROOT, "paper_0807_0264_gb300", "csrc", "mcg_sweep.cu")
     same_src = hashlib.sha256(open(src, "rb").read()).hexdigest().startswith(TRAFFIC_FP32["source_sha256_prefix"])
+    peak, peak_src = hbm_peak()
     if share32 >= share64:
         achieved = bytes32 / ((t32 + t32_even) / 2 / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": "k_halfsweep_c12", "achieved": achieved, "peak": 6780.0,
-                "unit": "GB/s", "frac": achieved / 6780.0,
+        roof = {"bound": "hbm", "kernel": "k_halfsweep_c12", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak,
                 "traffic": TRAFFIC_FP32["bytes_per_launch"] if same_src else None,
                 "traffic_source": TRAFFIC_FP32["profile"] if same_src else "kernel changed since the capture",
                 "algorithmic_bytes_per_launch": bytes32, "ms_per_launch": (t32 + t32_even) / 2,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+                "peak_source": peak_src}
     else:
         bytes64 = vh * (8 * 144 * 2 + 144 * 2)  # 8 links + Omega read and written, FP64
         achieved = bytes64 / (t64 / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": "k_halfsweep<double>", "achieved": achieved, "peak": 6780.0,
-                "unit": "GB/s", "frac": achieved / 6780.0, "traffic": None,
+        roof = {"bound": "hbm", "kernel": "k_halfsweep<double>", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                 "algorithmic_bytes_per_launch": bytes64, "ms_per_launch": t64,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+                "peak_source": peak_src}
     roof["kernel_ms"] = {"fp32_odd": t32, "fp32_even": t32_even, "fp64_odd_exact_solve": t64}
     roof["step_share_estimate"] = {"fp32": share32 / max(share32 + share64, 1e-9),
                                    "fp64": share64 / max(share32 + share64, 1e-9)}
@@ -659,7 +671,7 @@ def main():
     sweep_ms = (fp32_phase_ms(n2) - fp32_phase_ms(n1)) / (n2 - n1)
     roof["in_situ"] = {"ms_per_sweep": sweep_ms, "ms_per_launch": sweep_ms / 2,
                        "achieved": 2 * bytes32 / (sweep_ms / 1e3) / 1e9, "unit": "GB/s",
-                       "frac": 2 * bytes32 / (sweep_ms / 1e3) / 1e9 / 6780.0,
+                       "frac": 2 * bytes32 / (sweep_ms / 1e3) / 1e9 / peak,
                        "method": "FP32 sweeps inside a fix, L2 not flushed (working set 138 MB > 129 MB L2); the "
                                  "end-of-sweep kernel counted in the sweep"}
 

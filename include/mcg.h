@@ -124,8 +124,9 @@ int mcg_version(void);
 /* Message describing the last failure on this thread ("" if none). */
 const char* mcg_last_error(void);
 
-/* Free all cached scratch (device and pinned host).  Safe to call any time
- * no libmcg call is in flight; later calls re-create what they need. */
+/* Free all cached scratch (device and pinned host) and forget cached device
+ * addresses.  Safe to call any time no libmcg call is in flight; later calls
+ * re-create what they need. */
 int mcg_release(void);
 
 /* ---- layout conversion ---------------------------------------------------
@@ -400,7 +401,9 @@ int mcg_time_halfsweep(void* U, void* G, const mcg_lattice* lat, int parity, int
  * doubles, written asynchronously on `stream` (no synchronisation, no host
  * transfer).  The first call on each device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls share the one array and it keeps
+ * call before any stream capture.  The address stays cached for the process;
+ * after a cudaDeviceReset call mcg_release() (which drops the cache) before
+ * the next call.  All calls share the one array and it keeps
  * the previous call's partial sums: calls whose kernels overlap on the GPU
  * (other streams, other host threads) race and must be ordered by the caller.
  * Allocates nothing: no cudaMalloc, cudaFree or allocating library routine.

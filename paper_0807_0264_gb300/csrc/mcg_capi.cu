@@ -129,6 +129,7 @@ cudaStream_t capture_stream(int* rc) {
 }
 
 void release_all() {
+    static_release();
     std::lock_guard<std::mutex> lk(g_mu);
     int dev = 0;
     cudaGetDevice(&dev);
@@ -148,12 +149,16 @@ void release_all() {
 // ---------------------------------------------------------------------------
 // validation helpers
 // ---------------------------------------------------------------------------
-static int check_lat(const mcg_lattice* lat, Geom* g) {
+// Extents are bounded before they are multiplied (no overflow for any int
+// input): each in [2, 32768] and even, V / 2 <= 2^30, 1 <= nfields <= 2^20.
+int check_lattice(const mcg_lattice* lat, Geom* g) {
     if (!lat) return fail(MCG_BAD_ARG, "lattice descriptor is NULL");
     for (int d = 0; d < 4; ++d)
         if (lat->dims[d] < 2 || (lat->dims[d] & 1))
             return fail(MCG_BAD_DIMS, "every lattice extent must be even and >= 2");
-    if (lat->nfields < 1) return fail(MCG_BAD_DIMS, "nfields must be >= 1");
+    for (int d = 0; d < 4; ++d)
+        if (lat->dims[d] > (1 << 15)) return fail(MCG_BAD_DIMS, "lattice extent above 32768");
+    if (lat->nfields < 1 || lat->nfields > (1 << 20)) return fail(MCG_BAD_DIMS, "nfields must be in [1, 2^20]");
     if (lat->precision != MCG_F64 && lat->precision != MCG_F32)
         return fail(MCG_BAD_ARG, "precision must be MCG_F64 or MCG_F32");
     const long long V = (long long)lat->dims[0] * lat->dims[1] * lat->dims[2] * lat->dims[3];
@@ -162,6 +167,8 @@ static int check_lat(const mcg_lattice* lat, Geom* g) {
     g->vh = (int)(V / 2);
     return 0;
 }
+
+static int check_lat(const mcg_lattice* lat, Geom* g) { return check_lattice(lat, g); }
 
 static size_t elem_bytes(int prec) { return prec == MCG_F64 ? 16 : 8; }
 

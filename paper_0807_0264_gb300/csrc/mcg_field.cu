@@ -693,28 +693,26 @@ static int static_partials_address(double** out) {
     return 0;
 }
 
+void static_release() {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    for (auto& p : g_static_addr) p = nullptr;
+}
+
 }  // namespace mcg
 
 extern "C" int mcg_plaquette_static(const void* U, double* out, const mcg_lattice* lat, cudaStream_t stream) {
     using namespace mcg;
-    if (!lat) return fail(MCG_BAD_ARG, "lattice descriptor is NULL");
-    for (int d = 0; d < 4; ++d)
-        if (lat->dims[d] < 2 || (lat->dims[d] & 1)) return fail(MCG_BAD_DIMS, "every lattice extent must be even and >= 2");
-    if (lat->nfields < 1) return fail(MCG_BAD_DIMS, "nfields must be >= 1");
-    if (lat->precision != MCG_F64 && lat->precision != MCG_F32)
-        return fail(MCG_BAD_ARG, "precision must be MCG_F64 or MCG_F32");
+    Geom g;
+    int rc = check_lattice(lat, &g);
+    if (rc) return rc;
     if (!U || !out) return fail(MCG_BAD_ARG, "null pointer");
-    const long long V = (long long)lat->dims[0] * lat->dims[1] * lat->dims[2] * lat->dims[3];
+    const long long V = 2LL * g.vh;
     const long long bpf = (V + FT - 1) / FT;
     if (bpf * lat->nfields > kStaticPartials)
         return fail(MCG_BAD_ARG, "mcg_plaquette_static: nfields * ceil(V / 256) exceeds the 65536 static partial "
                                  "sums (at most 16 777 216 sites in total); use mcg_plaquette");
     double* partial = nullptr;
-    int rc = static_partials_address(&partial);
-    if (rc) return rc;
-    Geom g;
-    for (int d = 0; d < 4; ++d) g.n[d] = lat->dims[d];
-    g.vh = (int)(V / 2);
+    if ((rc = static_partials_address(&partial))) return rc;
     // every partial slot read below is written by its block first: nothing in
     // the shared array has to start at zero
     const int nb = (int)bpf * lat->nfields;

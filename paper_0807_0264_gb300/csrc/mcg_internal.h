@@ -22,6 +22,15 @@ int cuda_fail(cudaError_t e, const char* what);
         if (e_ != cudaSuccess) return ::mcg::cuda_fail(e_, #call); \
     } while (0)
 
+// ---- argument checks ----------------------------------------------------------
+// Validates a lattice descriptor (even extents in [2, 32768], at most 2^30
+// sites per parity, 1..2^20 fields, a known precision) and fills g.
+int check_lattice(const mcg_lattice* lat, Geom* g);
+
+// Drops the cached device addresses of the allocation-free entry point's
+// static array (mcg_release calls it).
+void static_release();
+
 // ---- launch accounting ------------------------------------------------------
 // Every kernel the library enqueues is counted (graph launches count their
 // kernel nodes); mcg_kernel_launches() reports the running total.

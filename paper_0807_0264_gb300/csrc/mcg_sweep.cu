@@ -1468,12 +1468,12 @@ static size_t halfsweep_smem_f64(int nt) { return sizeof(cplx<double>) * 81 * nt
 // (15 chunks per thread: 30 KB for 128 threads)
 static size_t halfsweep_smem_c12(int nt) { return sizeof(float4) * 15 * nt; }
 
+// Raises the dynamic shared-memory limit of the half-sweep kernels for the
+// current device.  Called on every fix phase (never inside a stream capture):
+// the attribute is per device, and the call costs microseconds.
 template <typename T>
 static int prepare_halfsweep(int nt) {
     if constexpr (sizeof(T) == 8) {
-        static bool done[2] = {false, false};
-        const int slot = nt == 64 ? 0 : 1;
-        if (done[slot]) return 0;
         const size_t smem = halfsweep_smem_f64(nt);
         int rc = 0;
         if (nt == 128) {
@@ -1487,11 +1487,7 @@ static int prepare_halfsweep(int nt) {
                 (rc = raise_smem(k_halfsweep<T, true, 64, true>, smem)))
                 return rc;
         }
-        done[slot] = true;
     } else {
-        static bool done[3] = {false, false, false};
-        const int slot = nt == 64 ? 0 : (nt == 128 ? 1 : 2);
-        if (done[slot]) return 0;
         const size_t smem = halfsweep_smem_c12(nt);
         int rc = 0;
         if (nt == 256) {
@@ -1507,7 +1503,6 @@ static int prepare_halfsweep(int nt) {
                 (rc = raise_smem(k_halfsweep_c12<true, 64, 6>, smem)))
                 return rc;
         }
-        done[slot] = true;
     }
     return 0;
 }
@@ -1747,12 +1742,9 @@ int run_anneal(void* U, void* G, const Geom& g, int nfields, const double* T, in
                int nhit, double eps, unsigned long long seed, long long* accepted_host, cudaStream_t st) {
     constexpr int NT = 128;
     const size_t smem = halfsweep_smem_f64(NT);
-    static bool prepared = false;
     int rc = 0;
-    if (!prepared) {
-        if ((rc = raise_smem(k_anneal_halfsweep<NT>, smem))) return rc;
-        prepared = true;
-    }
+    // per device and cheap: raised on every call
+    if ((rc = raise_smem(k_anneal_halfsweep<NT>, smem))) return rc;
     unsigned long long* d_acc =
         (unsigned long long*)scratch_device("anneal.acc", sizeof(unsigned long long) * nfields, &rc);
     if (rc) return rc;
