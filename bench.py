@@ -64,6 +64,16 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--dims", type=int, nargs=4, default=list(DIMS))
     ap.add_argument("--levels", type=int, nargs="+", default=list(LEVELS))
+    ap.add_argument("--rho", type=float, default=RHO)
+    ap.add_argument("--eps", type=float, default=1.0, help="1: stout; -0.25: over-improved stout (Sec. II.B)")
+    ap.add_argument("--config3", action="store_true",
+                    help="the over-improved stout workload: eps = -0.25, rho = 0.06, n in {10, 20, 40}")
+    ap.add_argument("--no-mixed-error", action="store_true",
+                    help="skip the mixed schedule's error against the oracle's FP64 relaxation from the same "
+                         "hand-off field")
+    ap.add_argument("--mixed-error-levels", type=int, nargs="+", default=None,
+                    help="levels for the mixed-error block (default: every level)")
+    ap.add_argument("--mixed-error-cap", type=int, default=1500, help="oracle sweeps cap per level")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-observables", action="store_true",
                     help="skip the Sec. III.A measurement (vortex removal, Wilson loops) on the level-0 result")
@@ -79,11 +89,19 @@ def parse():
                          "relaxation against annealing (200 sweeps, T 2 -> 0.02, 4 hits) + relaxation on 16 x 12^4 "
                          "configurations (MCG_ANNEAL_DIMS, MCG_ANNEAL_CONFIGS), and the annealing sweep timed at "
                          "20^3 x 40; one JSON line")
+    ap.add_argument("--profile-kernels", action="store_true",
+                    help="every kernel of the library once or twice on the 20^3 x 40 workload (smearing FP32/FP64/"
+                         "over-improved, fix phases FP32/FP64 exact/FP64 with FP32 solve, hand-off, gauge "
+                         "transforms, observables, center projection, vortex removal, Wilson loops, annealing, "
+                         "gradients, input check): the launches for a per-kernel ncu metrics capture")
     ap.add_argument("--profile-kernel", choices=["f32", "f64"],
                     help="time the FP32 (or FP64) half-sweep on the field after 300 FP32 sweeps (the regime the FP32 "
                          "phase runs in), odd then even sites, 3 launches each, L2 flushed: the launches for an ncu "
                          "capture of the dominant kernel (the warm-up runs 600 FP32 half-sweeps first)")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.config3:
+        a.eps, a.rho, a.levels = -0.25, 0.06, [10, 20, 40]
+    return a
 
 
 # ---------------------------------------------------------------------------
@@ -212,11 +230,16 @@ def reduce_over_ranks(dist, x: float, op: str, device) -> float:
     return float(t.item())
 
 
+def smearing_name(args):
+    return "stout" if args.eps == 1.0 else f"over-improved stout eps={args.eps:g}"
+
+
 def config_of(args, form):
     d = tuple(args.dims)
-    return {"workload": f"Sec. II.B preconditioned MCG, {d[0]}x{d[1]}x{d[2]}x{d[3]} SU(3), stout rho={RHO} "
-                        f"n in {list(args.levels)}, levels batched, dV_U<1e-10",
-            "lattice": list(d), "levels": list(args.levels), "rho": RHO, "tol": 1e-10, "form": form,
+    return {"workload": f"Sec. II.B preconditioned MCG, {d[0]}x{d[1]}x{d[2]}x{d[3]} SU(3), {smearing_name(args)} "
+                        f"rho={args.rho:g} n in {list(args.levels)}, levels batched, dV_U<1e-10",
+            "lattice": list(d), "levels": list(args.levels), "rho": args.rho, "eps": args.eps, "tol": 1e-10,
+            "form": form,
             "field": "synthetic g(x) exp(i w theta.lambda/2) g(x+mu)^dag, w=0.4326 (plaquette 0.60), seed 0",
             "l2": "inputs larger than L2 (184 MB FP64 field, 4 x 184 MB outputs)"}
 
@@ -433,6 +456,117 @@ def synth_w():
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def profile_kernels(mcg, U, dims, dev):
+    """Each library kernel on the 20^3 x 40 workload field, for a per-kernel
+    ncu capture (no timing here)."""
+    Gi = mcg.identity_gauge(dims, 1, mcg.F64, dev)
+    for eps, prec in ((1.0, mcg.F32), (1.0, mcg.F64), (-0.25, mcg.F64)):
+        Us = mcg.mcg_convert(U, prec) if prec == mcg.F32 else U
+        mcg.mcg_smear(Us, dims, 0.1, eps, 2)
+    # the mixed fix: FP32 phase (compact conversion, half-sweeps, reductions),
+    # hand-off, FP64 phase with the FP32 local solve; then the exact FP64 phase
+    Uf, Gf = U.clone(), Gi.clone()
+    mcg.mcg_fix(Uf, Gf, dims, mcg.Params(tol=-1e300, max_sweeps=4, check_every=2, reunit_every=2, fp32_sweeps=2,
+                                         fp32_tol=-1e300, fp32_window=1, fp32_overrelax=OMEGA, fp64_solve32=1))
+    mcg.mcg_fix(Uf, Gf, dims, mcg.Params(tol=-1e300, max_sweeps=2, check_every=2, reunit_every=2))
+    mcg.mcg_apply_gauge(Uf, Gf, dims)
+    mcg.mcg_reunitarise(Gf, 1, dims)
+    mcg.mcg_plaquette(Uf, dims)
+    mcg.mcg_functional(Uf, dims)
+    Z, _ = mcg.mcg_center_project(Uf, dims)
+    mcg.mcg_vortex_remove(Uf, Z, dims)
+    mcg.mcg_wilson_loops(Uf, dims, 2, 2)
+    mcg.mcg_anneal(Uf, Gf, dims, [1.0, 0.5], nhit=2, eps=0.3)
+    mcg.mcg_grad_R(Uf, dims)
+    Gout = torch_randn_like_links(U)
+    mcg.mcg_smear_backward_step(U, Gout, dims, 0.1, 1.0)
+    import torch
+
+    torch.cuda.synchronize(dev)
+    print(json.dumps({"profile_kernels": True, "dims": dims, "launches": mcg.mcg_kernel_launches()}), flush=True)
+
+
+def torch_randn_like_links(U):
+    import torch
+
+    g = torch.Generator(device=U.device)
+    g.manual_seed(0)
+    return torch.randn(U.shape, dtype=U.dtype, device=U.device, generator=g)
+
+
+def mixed_error_block(args, mcg, U, dims, levels, mixed, dev):
+    """Error of the mixed schedule against the oracle, per level, on the
+    preconditioned fix (the one that yields the level's fixed field): the
+    level's preconditioned field (the smeared field, FP64 smearing, fixed with
+    the mixed schedule; its transform applied to the input) runs the mixed
+    schedule up to its hand-off and first FP64 sweep; from that same field
+    H the GPU's FP64 finish (the bench's, local solve in FP32) and the GPU's
+    exact FP64 finish run to dV_U < 1e-10, and so does the oracle's plain FP64
+    relaxation on the host cores.  Reported: sweeps, V_U, |V_gpu - V_oracle|,
+    max per-link |U_gpu - U_oracle|, P-vortex counts."""
+    import numpy as np
+
+    import oracle
+
+    V = int(np.prod(dims))
+    oracle.set_threads(len(os.sched_getaffinity(0)))
+    handoff = mcg.Params(tol=1e300, max_sweeps=mixed.max_sweeps, check_every=mixed.check_every,
+                         reunit_every=mixed.reunit_every, fp32_sweeps=mixed.fp32_sweeps, fp32_tol=mixed.fp32_tol,
+                         fp32_window=mixed.fp32_window, fp32_overrelax=mixed.fp32_overrelax,
+                         fp64_solve32=mixed.fp64_solve32)
+
+    def compare(F):
+        """F (device, FP64) -> hand-off H in place; finishes from H compared."""
+        Gh = mcg.identity_gauge(dims, 1, mcg.F64, dev)
+        h = mcg.mcg_fix(F, Gh, dims, handoff)
+        H = mcg.mcg_unpack_links(F, dims)[0].cpu().numpy()
+        row = {"handoff_sweeps": h["sweeps"][0]}
+        for name, s32 in (("gpu_bench_finish", 1), ("gpu_exact_finish", 0)):
+            Ug, Gg = F.clone(), mcg.identity_gauge(dims, 1, mcg.F64, dev)
+            rg = mcg.mcg_fix(Ug, Gg, dims, mcg.Params(tol=1e-10, max_sweeps=20000, check_every=25, reunit_every=50,
+                                                      fp64_solve32=s32))
+            _, cnt = mcg.mcg_center_project(Ug, dims)
+            row[name] = {"sweeps": rg["sweeps"][0], "converged": rg["converged"], "V": rg["R"][0] / (36.0 * V),
+                         "vortices": int(cnt[0][0]), "U": mcg.mcg_unpack_links(Ug, dims)[0].cpu().numpy()}
+            del Ug, Gg
+        ro = oracle.fix(dims, H, None, tol=1e-10, max_sweeps=args.mixed_error_cap, reunit_every=50)
+        Vo = ro["R_hist"][-1] / (36.0 * V)
+        no = int(oracle.vortex_count(dims, oracle.center_project(dims, ro["U"]))[0])
+        row["oracle_finish"] = {"sweeps": ro["sweeps"], "converged": ro["converged"], "V": Vo, "vortices": no}
+        for name in ("gpu_bench_finish", "gpu_exact_finish"):
+            r = row[name]
+            Ug = r.pop("U")
+            r["V_rel_err"] = abs(r["V"] - Vo) / Vo
+            r["max_link_err"] = float(np.abs(Ug - ro["U"]).max())
+            r["vortices_equal"] = r["vortices"] == no
+        return row, Gh
+
+    out = []
+    for n in levels:
+        t0 = time.perf_counter()
+        row = {"level": n}
+        Up = U.clone()
+        if n > 0:
+            S = mcg.mcg_smear(U, dims, args.rho, args.eps, n)
+            row["smeared_fix"], _ = compare(S)
+            # the preconditioning transform: the mixed fix of the smeared field
+            S = mcg.mcg_smear(U, dims, args.rho, args.eps, n)
+            G1 = mcg.identity_gauge(dims, 1, mcg.F64, dev)
+            mcg.mcg_fix(S, G1, dims, mixed)
+            mcg.mcg_reunitarise(G1, 1, dims)
+            mcg.mcg_apply_gauge(Up, G1, dims)
+            del S, G1
+        row["preconditioned_fix"], _ = compare(Up)
+        row["seconds"] = time.perf_counter() - t0
+        out.append(row)
+        del Up
+    return {"method": "per level and per fix (the smeared field's, then the preconditioned field's): the mixed "
+                      "schedule runs to its hand-off and first FP64 sweep (field H); from H the GPU's FP64 finish "
+                      "(the bench's: local solve in FP32) and the GPU's exact FP64 finish run to dV_U<1e-10, and "
+                      "so does the oracle's plain FP64 relaxation on the host cores; FP64 smearing",
+            "levels": out}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -500,6 +634,10 @@ def main():
         print(json.dumps({"profile_kernel": args.profile_kernel, "dims": dims, "ms_per_launch": ms}), flush=True)
         return
 
+    if args.profile_kernels:
+        profile_kernels(mcg, U, dims, dev)
+        return
+
     if args.profile_slice:
         # FP32 : FP64 sweeps 100 : 1 per fix, close to the full step's ratio
         sl = mcg.Params(tol=-1e300, max_sweeps=101, check_every=25, reunit_every=50, fp32_sweeps=100,
@@ -523,8 +661,8 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     def step(params, smear_prec):
-        return mcg.mcg_precondition_levels(U, dims, levels, params, rho=RHO, eps=1.0, smear_precision=smear_prec,
-                                           U_out=U_out, G_out=G_out, Z_out=Z_out)[3]
+        return mcg.mcg_precondition_levels(U, dims, levels, params, rho=args.rho, eps=args.eps,
+                                           smear_precision=smear_prec, U_out=U_out, G_out=G_out, Z_out=Z_out)[3]
 
     def barrier():
         if dist:
@@ -543,6 +681,7 @@ def main():
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     launches0 = mcg.mcg_kernel_launches()
+    mcg.mcg_phase_stats(reset=True)
     with Clocks(local) as clk:
         barrier()
         e0.record(stream)
@@ -553,6 +692,7 @@ def main():
         e1.record(stream)
         barrier()
     launches = mcg.mcg_kernel_launches() - launches0
+    phases = mcg.mcg_phase_stats(reset=True)
     ms_total = max_over_ranks(e0.elapsed_time(e1))
     ms = ms_total / args.steps
     total_updates = sum_over_ranks(site_updates)
@@ -625,9 +765,6 @@ def main():
     t32_even = mcg.mcg_time_halfsweep(U32, G32, dims, parity=0, nreps=20, flush_l2=True)
     t64 = mcg.mcg_time_halfsweep(Uc, Gc, dims, parity=1, nreps=5, flush_l2=True)
     del Uc, Gc, U32, G32
-    sw64 = sw_all - sw32
-    share32 = sw32 * (t32 + t32_even)
-    share64 = sw64 * 2 * t64
     vh = V // 2
     bytes32 = vh * (8 * 48 * 2 + 48 * 2)  # 8 links + W read and written, FP32 rows 0 and 1
     import hashlib
@@ -635,24 +772,31 @@ def main():
     src = os.path.join(ROOT, "paper_0807_0264_gb300", "csrc", "mcg_sweep.cu")
     same_src = hashlib.sha256(open(src, "rb").read()).hexdigest().startswith(TRAFFIC_FP32["source_sha256_prefix"])
     peak, peak_src = hbm_peak()
-    if share32 >= share64:
-        achieved = bytes32 / ((t32 + t32_even) / 2 / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": "k_halfsweep_c12", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak,
-                "traffic": TRAFFIC_FP32["bytes_per_launch"] if same_src else None,
-                "traffic_source": TRAFFIC_FP32["profile"] if same_src else "kernel changed since the capture",
-                "algorithmic_bytes_per_launch": bytes32, "ms_per_launch": (t32 + t32_even) / 2,
-                "peak_source": peak_src}
-    else:
-        bytes64 = vh * (8 * 144 * 2 + 144 * 2)  # 8 links + Omega read and written, FP64
-        achieved = bytes64 / (t64 / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": "k_halfsweep<double>", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                "algorithmic_bytes_per_launch": bytes64, "ms_per_launch": t64,
-                "peak_source": peak_src}
+    # the dominant kernel inside the timed region: the FP32 sweep graphs
+    # (half-sweeps + end-of-sweep reduction), CUDA events around each graph
+    # launch in the library, site-updates from the fields' sweep counts
+    p32, p64 = phases["f32"], phases["f64"]
+    achieved = p32["site_updates"] * 864 / (p32["ms"] / 1e3) / 1e9 if p32["ms"] > 0 else 0.0
+    roof = {"bound": "hbm", "kernel": "k_halfsweep_c12", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak,
+            "traffic": TRAFFIC_FP32["bytes_per_launch"] if same_src else None,
+            "traffic_source": TRAFFIC_FP32["profile"] if same_src else "kernel changed since the capture",
+            "traffic_launch": "one 20^3 x 40 half-sweep (160 000 site-updates, 138.24 MB algorithmic)",
+            "algorithmic_bytes_per_site_update": 864, "peak_source": peak_src,
+            "method": "live in the timed region: FP32 sweep-graph GPU time (CUDA events in the library around "
+                      "each graph launch; the end-of-sweep reduction kernel included) over the FP32 site-updates "
+                      "x 864 B",
+            "timed_region": {"fp32_ms": p32["ms"], "fp32_site_updates": p32["site_updates"],
+                             "fp64_ms": p64["ms"], "fp64_site_updates": p64["site_updates"],
+                             "fp64_ms_per_field_sweep": p64["ms"] / max(1e-9, p64["site_updates"] / V),
+                             "fp32_ms_per_field_sweep": p32["ms"] / max(1e-9, p32["site_updates"] / V),
+                             "share_of_step": {"fp32": p32["ms"] / ms_total, "fp64": p64["ms"] / ms_total}},
+            "isolated": {"ms_per_launch": (t32 + t32_even) / 2,
+                         "achieved": bytes32 / ((t32 + t32_even) / 2 / 1e3) / 1e9,
+                         "frac": bytes32 / ((t32 + t32_even) / 2 / 1e3) / 1e9 / peak,
+                         "method": "one 20^3 x 40 field, mean of the odd and even half-sweep, L2 flushed by a "
+                                   "256 MB memset before each launch"}}
     roof["kernel_ms"] = {"fp32_odd": t32, "fp32_even": t32_even, "fp64_odd_exact_solve": t64}
-    roof["step_share_estimate"] = {"fp32": share32 / max(share32 + share64, 1e-9),
-                                   "fp64": share64 / max(share32 + share64, 1e-9)}
     # the same kernel inside a fix (no flush: each half-sweep's 138 MB working
     # set exceeds the 129 MB L2): FP32-phase time of N2 - N1 sweeps on a copy
     # of the warm field, both half-sweeps and the end-of-sweep kernel per sweep
@@ -716,8 +860,8 @@ def main():
     for _ in range(args.steps):
         canon_dev.copy_(canon_pinned, non_blocking=True)
         Ue = mcg.mcg_pack_links(canon_dev, dims, mcg.F64)
-        r2 = mcg.mcg_precondition_levels(Ue, dims, levels, mixed, rho=RHO, eps=1.0, smear_precision=mcg.F32,
-                                         U_out=U_out, G_out=G_out, Z_out=Z_out)[3]
+        r2 = mcg.mcg_precondition_levels(Ue, dims, levels, mixed, rho=args.rho, eps=args.eps,
+                                         smear_precision=mcg.F32, U_out=U_out, G_out=G_out, Z_out=Z_out)[3]
         z_host.copy_(mcg.mcg_unpack_center(Z_out, dims), non_blocking=True)
         e2e_updates += sum(r["sweeps_smeared"] + r["sweeps_fixed"] for r in r2) * V
     h1.record(stream)
@@ -732,6 +876,10 @@ def main():
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{n} oracle FP64 MCG sweeps of the {dims[0]}x{dims[1]}x{dims[2]}x{dims[3]} workload field",
                "one_core": {"value": v1, "sample": f"{n1} sweeps on 1 thread"}}
+
+    mixed_err = None
+    if rank == 0 and world == 1 and not args.no_mixed_error:
+        mixed_err = mixed_error_block(args, mcg, U, dims, args.mixed_error_levels or levels, mixed, dev)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -755,7 +903,7 @@ def main():
                 "roofline": roof, "cpu_baseline": cpu, "autotune": tuned,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": canon_pinned.numel() * 16,
                         "d2h_bytes_per_step": z_host.numel(), "ms_per_step": e2e_ms / args.steps},
-                "clocks": clk.summary(), "gpu_launches": launches, "sec3d": sec3d}
+                "clocks": clk.summary(), "gpu_launches": launches, "sec3d": sec3d, "mixed_error": mixed_err}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -52,9 +52,9 @@ typedef enum {
     MCG_NOT_CONVERGED = 1, /* max_sweeps reached; results are valid          */
     MCG_BAD_DIMS = 2,      /* an extent is odd or < 2, or nfields < 1        */
     MCG_BAD_ARG = 3,       /* null pointer, aliasing, out-of-range parameter */
-    MCG_BAD_INPUT = 4,     /* non-finite or non-unitary input field          */
-    MCG_CUDA_ERROR = 5,    /* a CUDA runtime call failed                     */
-    MCG_WAIT_TIMEOUT = 6   /* a bounded device-side wait gave up             */
+    MCG_BAD_INPUT = 4,     /* an input link or transform is not finite or   */
+                           /* not in SU(3) (see "Input validation" below)   */
+    MCG_CUDA_ERROR = 5     /* a CUDA runtime call failed                     */
 } mcg_status;
 
 typedef enum { MCG_F64 = 0, MCG_F32 = 1 } mcg_precision;
@@ -118,6 +118,21 @@ typedef struct {
     int status;            /* MCG_OK or MCG_NOT_CONVERGED                       */
 } mcg_precond_result;
 
+/*
+ * Input validation.  mcg_smear, mcg_fix, mcg_anneal, mcg_precondition_fix,
+ * mcg_precondition_levels, mcg_fix_batch and mcg_gribov_search first check,
+ * in one pass over the caller's links (and transforms G where the call reads
+ * them), that every matrix M is finite and in SU(3):
+ * max_ij |(M M^dag - 1)_ij| <= tol and |det M - 1| <= tol, with tol = 1e-6 for
+ * MCG_F64 fields and 1e-4 for MCG_F32 fields (far above rounding, far below a
+ * real defect).  mcg_center_project checks finiteness only: the sector is a
+ * function of tr U and is defined for any finite matrix.  On failure they
+ * return MCG_BAD_INPUT before any other GPU work; mcg_last_error() names the
+ * array and the first failing matrix (field, direction, parity, in-parity
+ * site).  The check synchronises the stream.  (The paper works with SU(3)
+ * fields, Sec. II.A; the check only refuses inputs outside that domain.)
+ */
+
 /* Library version (major*10000 + minor*100 + patch). */
 int mcg_version(void);
 
@@ -177,6 +192,8 @@ int mcg_reunitarise(void* M, int which, const mcg_lattice* lat, cudaStream_t str
  *             1x2 rectangle staples) ],  Omega = C U^dag,
  *   Q = (i/2)(Omega^dag - Omega) - (i/6) tr(Omega^dag - Omega),  U' = exp(iQ) U.
  * U_in and U_out are fields of lat (U_out must not overlap U_in); n = 0 copies.
+ * U_in is validated first (see "Input validation"; synchronises), then the
+ * steps run asynchronously on `stream`.
  */
 int mcg_smear(const void* U_in, void* U_out, const mcg_lattice* lat, double rho, double eps, int n,
               cudaStream_t stream);
@@ -420,6 +437,15 @@ int mcg_get_sweep_block(int precision);
 /* Running total of CUDA kernels this library has enqueued in this process
  * (kernels inside a CUDA graph count once per graph launch). */
 long long mcg_kernel_launches(void);
+
+/* Sweep-phase accounting since the last reset (instrumentation; not part of
+ * the paper's method): ms_out[p] = GPU milliseconds of the relaxation's sweep
+ * graphs (half-sweeps, end-of-sweep reductions, FP64 re-unitarisation), timed
+ * with CUDA events on the calling stream, and site_updates_out[p] = sites x
+ * half-sweeps they performed (a full sweep of a field is V site-updates),
+ * for p = 0: FP64 sweeps, p = 1: FP32 sweeps.  ms_out: host, 2 doubles;
+ * site_updates_out: host, 2 long long.  reset != 0 zeroes the counters. */
+int mcg_phase_stats(double* ms_out, long long* site_updates_out, int reset);
 
 #ifdef __cplusplus
 }

@@ -49,6 +49,16 @@ int cuda_fail(cudaError_t e, const char* what) {
 static std::atomic<long long> g_launches{0};
 void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+static std::mutex g_phase_mu;
+static double g_phase_ms[2] = {0.0, 0.0};
+static long long g_phase_su[2] = {0, 0};
+void note_phase(int prec, double ms, long long site_updates) {
+    std::lock_guard<std::mutex> lk(g_phase_mu);
+    const int i = prec == MCG_F64 ? 0 : 1;
+    g_phase_ms[i] += ms;
+    g_phase_su[i] += site_updates;
+}
+
 // ---------------------------------------------------------------------------
 // scratch: grow-only named buffers per device
 // ---------------------------------------------------------------------------
@@ -460,6 +470,7 @@ int mcg_smear(const void* U_in, void* U_out, const mcg_lattice* lat, double rho,
     if (!(std::isfinite(rho) && std::isfinite(eps))) return fail(MCG_BAD_ARG, "rho/eps not finite");
     const size_t bytes = elem_bytes(lat->precision) * link_elems(g) * lat->nfields;
     if (overlap(U_in, bytes, U_out, bytes)) return fail(MCG_BAD_ARG, "U_in and U_out overlap");
+    if ((rc = validate_su3(U_in, lat->precision, g, 8, lat->nfields, "mcg_smear: U_in", stream))) return rc;
     return run_smear(U_in, U_out, lat->precision, g, lat->nfields, rho, eps, n, stream);
 }
 
@@ -473,6 +484,8 @@ int mcg_fix(void* U, void* G, const mcg_lattice* lat, const mcg_params* params, 
     const size_t eb = elem_bytes(lat->precision);
     if (overlap(U, eb * link_elems(g) * lat->nfields, G, eb * gauge_elems(g) * lat->nfields))
         return fail(MCG_BAD_ARG, "U and G overlap");
+    if ((rc = validate_su3(U, lat->precision, g, 8, lat->nfields, "mcg_fix: U", stream))) return rc;
+    if ((rc = validate_su3(G, lat->precision, g, 2, lat->nfields, "mcg_fix: G", stream))) return rc;
     return fix_impl(U, G, lat, g, params, R_out, sweeps_out, nullptr, R_hist, stream);
 }
 
@@ -492,6 +505,8 @@ int mcg_anneal(void* U, void* G, const mcg_lattice* lat, const double* T, int ns
     const size_t lb = elem_bytes(MCG_F64) * link_elems(g) * lat->nfields;
     const size_t gb = elem_bytes(MCG_F64) * gauge_elems(g) * lat->nfields;
     if (overlap(U, lb, G, gb)) return fail(MCG_BAD_ARG, "U and G overlap");
+    if ((rc = validate_su3(U, MCG_F64, g, 8, lat->nfields, "mcg_anneal: U", stream))) return rc;
+    if ((rc = validate_su3(G, MCG_F64, g, 2, lat->nfields, "mcg_anneal: G", stream))) return rc;
     return run_anneal(U, G, g, lat->nfields, T, nsweeps, first_sweep, nhit, eps, seed, accepted_out, stream);
 }
 
@@ -500,6 +515,8 @@ int mcg_center_project(const void* U, int8_t* Z, long long* counts, const mcg_la
     int rc = check_lat(lat, &g);
     if (rc) return rc;
     if (!U || !Z) return fail(MCG_BAD_ARG, "null pointer");
+    // the sector is a function of tr U alone, defined for any finite matrix
+    if ((rc = validate_su3(U, lat->precision, g, 8, lat->nfields, "mcg_center_project: U", stream, true))) return rc;
     return compute_center(U, lat->precision, Z, g, lat->nfields, counts, stream);
 }
 
@@ -560,6 +577,7 @@ int mcg_precondition_fix(void* U, void* G, int8_t* Z, const mcg_lattice* lat, co
     if (!U || !G || !results) return fail(MCG_BAD_ARG, "null pointer");
     if (nsmear < 0) return fail(MCG_BAD_ARG, "nsmear must be >= 0");
     if (smear_precision != MCG_F64 && smear_precision != MCG_F32) return fail(MCG_BAD_ARG, "bad smear precision");
+    if ((rc = validate_su3(U, lat->precision, g, 8, lat->nfields, "mcg_precondition_fix: U", stream))) return rc;
     const int nf = lat->nfields, prec = lat->precision;
     const size_t le = link_elems(g), ge = gauge_elems(g), eb = elem_bytes(prec);
     std::vector<double> plaq_in(nf), plaq_out(nf), Rs(nf, 0.0), Rf(nf);
@@ -627,6 +645,20 @@ int mcg_precondition_fix(void* U, void* G, int8_t* Z, const mcg_lattice* lat, co
 
 long long mcg_kernel_launches(void) { return g_launches.load(); }
 
+int mcg_phase_stats(double* ms_out, long long* site_updates_out, int reset) {
+    if (!ms_out || !site_updates_out) return fail(MCG_BAD_ARG, "null pointer");
+    std::lock_guard<std::mutex> lk(g_phase_mu);
+    for (int i = 0; i < 2; ++i) {
+        ms_out[i] = g_phase_ms[i];
+        site_updates_out[i] = g_phase_su[i];
+        if (reset) {
+            g_phase_ms[i] = 0.0;
+            g_phase_su[i] = 0;
+        }
+    }
+    return MCG_OK;
+}
+
 int mcg_set_sweep_block(int precision, int threads) {
     if (precision != MCG_F64 && precision != MCG_F32) return fail(MCG_BAD_ARG, "bad precision");
     if (threads != 64 && threads != 128 && !(threads == 256 && precision == MCG_F32))
@@ -671,6 +703,7 @@ int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_o
     for (int l = 0; l < nlevels; ++l)
         if (nsmear[l] < 0 || (l > 0 && nsmear[l] < nsmear[l - 1]))
             return fail(MCG_BAD_ARG, "nsmear must be non-negative and non-decreasing");
+    if ((rc = validate_su3(U, lat->precision, g, 8, 1, "mcg_precondition_levels: U", stream))) return rc;
     const int prec = lat->precision;
     const size_t le = link_elems(g), ge = gauge_elems(g), eb = elem_bytes(prec), seb = elem_bytes(smear_precision);
     if (overlap(U, eb * le, U_out, eb * le * nlevels)) return fail(MCG_BAD_ARG, "U and U_out overlap");
@@ -764,6 +797,10 @@ int mcg_fix_batch(const mcg_field* fields, int nfields, int precision, const mcg
     std::vector<FieldSpec> fs(nfields);
     for (int f = 0; f < nfields; ++f)
         if ((rc = field_spec(fields[f], precision, &fs[f]))) return rc;
+    for (int f = 0; f < nfields; ++f)
+        if ((rc = validate_su3(fs[f].U, precision, fs[f].g, 8, 1, "mcg_fix_batch: U", stream)) ||
+            (rc = validate_su3(fs[f].G, precision, fs[f].g, 2, 1, "mcg_fix_batch: G", stream)))
+            return rc;
     return fix_fields(fs, precision, params, R_out, sweeps_out, nullptr, nullptr, stream);
 }
 
@@ -779,6 +816,10 @@ int mcg_gribov_search(const mcg_field* copies, int ncopies, const int* config_of
         if ((rc = field_spec(copies[f], precision, &fs[f]))) return rc;
         if (config_of_copy[f] < 0 || config_of_copy[f] >= nconfigs) return fail(MCG_BAD_ARG, "config index out of range");
     }
+    for (int f = 0; f < ncopies; ++f)
+        if ((rc = validate_su3(fs[f].U, precision, fs[f].g, 8, 1, "mcg_gribov_search: U", stream)) ||
+            (rc = validate_su3(fs[f].G, precision, fs[f].g, 2, 1, "mcg_gribov_search: G", stream)))
+            return rc;
     // each copy starts as U^Omega0 with its own random Omega0; the fix then
     // accumulates onto Omega0, so G ends as the total transform of the copy
     for (int f = 0; f < ncopies; ++f)

@@ -3,6 +3,7 @@
 // All are HBM-bound streaming kernels (one thread per site of one parity).
 #include <cuda_runtime.h>
 
+#include <cstdio>
 #include <mutex>
 #include <vector>
 
@@ -501,6 +502,98 @@ int launch_unpack_center(const int8_t* Z, int8_t* canon, const Geom& g, int nfie
     MCG_CK(cudaGetLastError());
     note_launches(1);
     return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Input validation: every matrix finite and in SU(3) to within tol
+// ---------------------------------------------------------------------------
+// Matrix m of a field (nslots x Vh matrices: 8 = 4 directions x 2 parities
+// for links, 2 parities for a gauge transform) has entry e at
+// ((m / Vh) * 9 + e) * Vh + m % Vh.  A matrix fails if an entry is not finite,
+// if max_ij |(M M^dag - 1)_ij| > tol or if |det M - 1| > tol (FP32 arithmetic:
+// its rounding, ~1e-7, is far below the tolerances used).  bad[0]: number of
+// failing matrices; bad[1]: smallest failing global matrix index.
+template <typename T>
+__global__ void k_check_su3(const cplx<T>* __restrict__ M, int nslots, size_t vh, size_t nmat, float tol,
+                            bool finite_only, unsigned long long* __restrict__ bad) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nmat) return;
+    const size_t per_field = (size_t)nslots * vh;
+    const size_t f = i / per_field, m = i % per_field;
+    const cplx<T>* base = M + f * per_field * 9 + (m / vh) * 9 * vh + m % vh;
+    cplx<float> a[9];
+    bool finite = true;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+        const cplx<T> v = base[(size_t)e * vh];
+        finite = finite && isfinite(v.x) && isfinite(v.y);
+        a[e] = mk((float)v.x, (float)v.y);
+    }
+    bool ok = finite;
+    if (ok && !finite_only) {
+        float dev = 0.f;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = r; c < 3; ++c) {
+                cplx<float> d = mk(r == c ? -1.f : 0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) d = cfmac(a[3 * r + k], a[3 * c + k], d);
+                dev = fmaxf(dev, fmaxf(fabsf(d.x), fabsf(d.y)));
+            }
+        // det by the first row's cofactors
+        const cplx<float> c0 = csub(cmul(a[4], a[8]), cmul(a[5], a[7]));
+        const cplx<float> c1 = csub(cmul(a[5], a[6]), cmul(a[3], a[8]));
+        const cplx<float> c2 = csub(cmul(a[3], a[7]), cmul(a[4], a[6]));
+        const cplx<float> det = cadd(cadd(cmul(a[0], c0), cmul(a[1], c1)), cmul(a[2], c2));
+        dev = fmaxf(dev, fmaxf(fabsf(det.x - 1.f), fabsf(det.y)));
+        ok = dev <= tol;  // false for NaN too
+    }
+    if (!ok) {
+        atomicAdd(&bad[0], 1ull);
+        atomicMin(&bad[1], (unsigned long long)i);
+    }
+}
+
+int validate_su3(const void* M, int prec, const Geom& g, int nslots, int nfields, const char* what,
+                 cudaStream_t st, bool finite_only) {
+    int rc = 0;
+    unsigned long long* d_bad = (unsigned long long*)scratch_device("check.bad", 2 * sizeof(unsigned long long), &rc);
+    if (rc) return rc;
+    unsigned long long* h_bad = (unsigned long long*)scratch_host("check.bad", 2 * sizeof(unsigned long long), &rc);
+    if (rc) return rc;
+    MCG_CK(cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), st));
+    MCG_CK(cudaMemsetAsync(d_bad + 1, 0xff, sizeof(unsigned long long), st));
+    const size_t vh = (size_t)g.vh, nmat = (size_t)nslots * vh * nfields;
+    const unsigned nb = (unsigned)((nmat + FT - 1) / FT);
+    if (prec == MCG_F64)
+        k_check_su3<double><<<nb, FT, 0, st>>>((const cplx<double>*)M, nslots, vh, nmat, kSU3TolF64, finite_only,
+                                               d_bad);
+    else
+        k_check_su3<float><<<nb, FT, 0, st>>>((const cplx<float>*)M, nslots, vh, nmat, kSU3TolF32, finite_only,
+                                              d_bad);
+    MCG_CK(cudaGetLastError());
+    note_launches(1);
+    MCG_CK(cudaMemcpyAsync(h_bad, d_bad, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    MCG_CK(cudaStreamSynchronize(st));
+    if (h_bad[0] == 0) return 0;
+    const size_t i = (size_t)h_bad[1], per_field = (size_t)nslots * vh;
+    const size_t f = i / per_field, slot = (i % per_field) / vh, s = i % vh;
+    char buf[320];
+    if (finite_only)
+        snprintf(buf, sizeof buf, "%s: %llu matrices have non-finite entries (first: field %zu, mu %zu, parity %zu, "
+                 "in-parity site %zu)", what, h_bad[0], f, slot / 2, slot % 2, s);
+    else if (nslots == 8)
+        snprintf(buf, sizeof buf,
+                 "%s: %llu matrices are not finite or not in SU(3) to %g (first: field %zu, mu %zu, parity %zu, "
+                 "in-parity site %zu)",
+                 what, h_bad[0], prec == MCG_F64 ? kSU3TolF64 : kSU3TolF32, f, slot / 2, slot % 2, s);
+    else
+        snprintf(buf, sizeof buf,
+                 "%s: %llu matrices are not finite or not in SU(3) to %g (first: field %zu, parity %zu, "
+                 "in-parity site %zu)",
+                 what, h_bad[0], prec == MCG_F64 ? kSU3TolF64 : kSU3TolF32, f, slot, s);
+    return fail(MCG_BAD_INPUT, buf);
 }
 
 int launch_identity_gauge(void* G, int prec, const Geom& g, int nfields, cudaStream_t st) {

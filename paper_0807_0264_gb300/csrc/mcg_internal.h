@@ -35,6 +35,9 @@ void static_release();
 // Every kernel the library enqueues is counted (graph launches count their
 // kernel nodes); mcg_kernel_launches() reports the running total.
 void note_launches(long long n);
+// Sweep-phase accounting: GPU milliseconds of the sweep graphs and the
+// site-updates they performed, per precision (mcg_phase_stats reports them).
+void note_phase(int prec, double ms, long long site_updates);
 
 // ---- scratch ----------------------------------------------------------------
 // Named, grow-only device and pinned-host buffers cached per device; freed by
@@ -73,7 +76,8 @@ struct SweepBatch {
     int nf;
     int total_blocks;
     FieldState* state;
-    double* partial;  // one per block
+    double* partial;  // one per warp: ppb per block
+    int ppb;          // partials per block (threads per block / 32)
     double* R_hist;   // nf x hist_len (may be null)
     int hist_len;
     double tol;
@@ -113,6 +117,19 @@ int run_anneal(void* U, void* G, const Geom& g, int nfields, const double* T, in
 int sweep_block(int prec);
 void set_sweep_block(int prec, int nt);
 int sweep_sites_per_block(int prec);
+
+// ---- input validation (mcg_field.cu) -----------------------------------------
+// Tolerances of the SU(3) check on caller-supplied fields: max |M M^dag - 1|
+// and |det M - 1|.  Far above rounding (FP64 fields ~1e-15, FP32 ~1e-7), far
+// below any real defect (a link scaled by 1.01 is off by 2e-2).
+constexpr float kSU3TolF64 = 1e-6f;
+constexpr float kSU3TolF32 = 1e-4f;
+// Checks every matrix of nfields fields (nslots = 8 for links, 2 for gauge
+// transforms); returns 0, or MCG_BAD_INPUT with a message naming `what` and
+// the first failing matrix.  finite_only: only finiteness is required.
+// Synchronises the stream.
+int validate_su3(const void* M, int prec, const Geom& g, int nslots, int nfields, const char* what,
+                 cudaStream_t st, bool finite_only = false);
 
 // ---- field kernels (mcg_field.cu) -------------------------------------------
 int launch_convert(const void* src, int src_prec, void* dst, int dst_prec, size_t n, cudaStream_t st);

@@ -804,6 +804,14 @@ __device__ __forceinline__ int subgroup_step(L& lk, const int P, const int Q, co
     return fb;
 }
 
+// R partial sums: one per warp, partial[blockIdx.x * (NT / 32) + warp], summed
+// by k_finalize in a fixed order (deterministic, and no block barrier in the
+// sweep kernels).
+__device__ __forceinline__ void warp_partial(double v, double* __restrict__ partial) {
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) partial[blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)] = v;
+}
+
 __device__ __forceinline__ int field_of_block(const FieldDesc* __restrict__ d, int nf, int b) {
     int lo = 0, hi = nf - 1;
     while (lo < hi) {
@@ -895,11 +903,7 @@ __global__ void __launch_bounds__(NT, 2) k_halfsweep(SweepBatch bt, int parity) 
             }
         }
     }
-    __shared__ double red[NT / 32];
-    if (ACC) {
-        const double tot = block_sum(rsum, red);
-        if (threadIdx.x == 0) bt.partial[blockIdx.x] = tot;
-    }
+    if (ACC) warp_partial(rsum, bt.partial);
     {
         // count local solves that left the fast path (diagnostic)
         const int w = __reduce_add_sync(0xffffffffu, fb);
@@ -1137,6 +1141,63 @@ __device__ __forceinline__ void bwd_store(float4* bst, int l, const cplx<float>*
         bst[(l * 3 + q) * NT + threadIdx.x] = make_float4(m[2 * q].x, m[2 * q].y, m[2 * q + 1].x, m[2 * q + 1].y);
 }
 
+// Packed FP32 arithmetic: on sm_100 and later one instruction performs two
+// independent FP32 FMAs on a register pair (__ffma2_rn), which halves the
+// instruction count of the (A, b) build and of the SU(2) moves.  A complex
+// number is such a pair.  The moves use g x = g.x (x.x, x.y) + g.y (-x.y, x.x),
+// with the coefficients of the subgroup element broadcast to pairs once per
+// step: x[i] = (g_i.x, g_i.x), y[i] = (-g_i.y, g_i.y), yc[i] = (g_i.y, -g_i.y)
+// for g_i = g11, g12, g21, g22.
+struct PackedSU2 {
+    float2 x[4], y[4], yc[4];
+};
+__device__ __forceinline__ void packed_su2(const float (&a)[4], PackedSU2& G) {
+    const float gx[4] = {a[0], a[2], -a[2], a[0]};
+    const float gy[4] = {a[3], a[1], a[1], -a[3]};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        G.x[i] = make_float2(gx[i], gx[i]);
+        G.y[i] = make_float2(-gy[i], gy[i]);
+        G.yc[i] = make_float2(gy[i], -gy[i]);
+    }
+}
+__device__ __forceinline__ float2 pk(cplx<float> c) { return make_float2(c.x, c.y); }
+__device__ __forceinline__ float2 pk_swap(cplx<float> c) { return make_float2(c.y, c.x); }
+// g_i0 u + g_i1 v  (a row of G M)
+__device__ __forceinline__ cplx<float> su2_row(const PackedSU2& G, int i0, int i1, cplx<float> u, cplx<float> v) {
+    float2 r = __fmul2_rn(G.x[i0], pk(u));
+    r = __ffma2_rn(G.y[i0], pk_swap(u), r);
+    r = __ffma2_rn(G.x[i1], pk(v), r);
+    r = __ffma2_rn(G.y[i1], pk_swap(v), r);
+    return mk(r.x, r.y);
+}
+// u conj(g_i0) + v conj(g_i1)  (an entry of M G^dag)
+__device__ __forceinline__ cplx<float> su2_col(const PackedSU2& G, int i0, int i1, cplx<float> u, cplx<float> v) {
+    float2 r = __fmul2_rn(G.x[i0], pk(u));
+    r = __ffma2_rn(G.yc[i0], pk_swap(u), r);
+    r = __ffma2_rn(G.x[i1], pk(v), r);
+    r = __ffma2_rn(G.yc[i1], pk_swap(v), r);
+    return mk(r.x, r.y);
+}
+// M <- G M on a compact matrix (rows 0 and 1), as c12_left_update.
+template <int P, int Q>
+__device__ __forceinline__ void c12_left_update_pk(cplx<float>* m, const PackedSU2& G) {
+    if constexpr (Q < 2) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const cplx<float> xp = m[3 * P + k], xq = m[3 * Q + k];
+            m[3 * P + k] = su2_row(G, 0, 1, xp, xq);
+            m[3 * Q + k] = su2_row(G, 2, 3, xp, xq);
+        }
+    } else {
+        cplx<float> r2[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) r2[k] = row2_entry(m, k);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) m[3 * P + k] = su2_row(G, 0, 1, m[3 * P + k], r2[k]);
+    }
+}
+
 // One SU(2)-subgroup step (rows/columns P < Q, R the third index) on the
 // compact forward links m[0..3] (registers) and the compact backward links
 // in shared memory.  Writes the (over-relaxed) subgroup element to `a` for the
@@ -1144,13 +1205,14 @@ __device__ __forceinline__ void bwd_store(float4* bst, int l, const cplx<float>*
 template <int P, int Q, int R, int NT>
 __device__ __forceinline__ int c12_subgroup_step(cplx<float> (&m)[4][6], float4* bst, const float omega,
                                                  float (&a)[4]) {
-    float A[4][4], b[4];
+    // A = sum Re(conj(w) w^T), b = sum Re(conj(c) w): each entry accumulated as
+    // a pair (sum of x-products, sum of y-products), added at the end.  For a
+    // backward link w_1..w_3 change sign, which flips b_1..b_3 and A_0j (j > 0).
+    float2 Ap[10], bp[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        b[i] = 0.f;
+    for (int i = 0; i < 10; ++i) Ap[i] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) A[i][j] = 0.f;
-    }
+    for (int i = 0; i < 4; ++i) bp[i] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int l = 0; l < 8; ++l) {
         cplx<float> mb[6];
@@ -1159,28 +1221,41 @@ __device__ __forceinline__ int c12_subgroup_step(cplx<float> (&m)[4][6], float4*
         const cplx<float> m11 = c12_entry<P, P>(M), m12 = c12_entry<P, Q>(M);
         const cplx<float> m21 = c12_entry<Q, P>(M), m22 = c12_entry<Q, Q>(M);
         const cplx<float> cc = c12_entry<R, R>(M);
-        // tr(G M) = cc + w.a for a forward link; tr(M G^dag) = cc + w'.a for
-        // a backward link, w' = w with the signs of w1..w3 flipped
-        cplx<float> w[4];
-        w[0] = cadd(m11, m22);
-        w[1] = mk(-(m21.y + m12.y), m21.x + m12.x);
-        w[2] = csub(m21, m12);
-        w[3] = mk(-(m11.y - m22.y), m11.x - m22.x);
+        // tr(G M) = cc + w.a, w = (m11 + m22, i(m21 + m12), m21 - m12, i(m11 - m22))
+        float2 w[4];
+        w[0] = make_float2(m11.x + m22.x, m11.y + m22.y);
+        w[1] = make_float2(-(m21.y + m12.y), m21.x + m12.x);
+        w[2] = make_float2(m21.x - m12.x, m21.y - m12.y);
+        w[3] = make_float2(-(m11.y - m22.y), m11.x - m22.x);
+        float2 c0 = make_float2(cc.x, cc.y), c1 = c0, w0 = w[0];
         if (l >= 4) {
-#pragma unroll
-            for (int k = 1; k < 4; ++k) w[k] = mk(-w[k].x, -w[k].y);
+            c1 = make_float2(-cc.x, -cc.y);
+            w0 = make_float2(-w[0].x, -w[0].y);
         }
+        bp[0] = __ffma2_rn(c0, w[0], bp[0]);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            b[k] = fmaf(cc.x, w[k].x, fmaf(cc.y, w[k].y, b[k]));
-#pragma unroll
-            for (int j = k; j < 4; ++j) A[k][j] = fmaf(w[k].x, w[j].x, fmaf(w[k].y, w[j].y, A[k][j]));
-        }
+        for (int k = 1; k < 4; ++k) bp[k] = __ffma2_rn(c1, w[k], bp[k]);
+        Ap[0] = __ffma2_rn(w[0], w[0], Ap[0]);
+        Ap[1] = __ffma2_rn(w0, w[1], Ap[1]);
+        Ap[2] = __ffma2_rn(w0, w[2], Ap[2]);
+        Ap[3] = __ffma2_rn(w0, w[3], Ap[3]);
+        Ap[4] = __ffma2_rn(w[1], w[1], Ap[4]);
+        Ap[5] = __ffma2_rn(w[1], w[2], Ap[5]);
+        Ap[6] = __ffma2_rn(w[1], w[3], Ap[6]);
+        Ap[7] = __ffma2_rn(w[2], w[2], Ap[7]);
+        Ap[8] = __ffma2_rn(w[2], w[3], Ap[8]);
+        Ap[9] = __ffma2_rn(w[3], w[3], Ap[9]);
     }
+    float A[4][4], b[4];
+    {
+        int i = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < 4; ++k)
 #pragma unroll
-        for (int j = 0; j < k; ++j) A[k][j] = A[j][k];
+            for (int j = k; j < 4; ++j, ++i) A[k][j] = A[j][k] = Ap[i].x + Ap[i].y;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) b[k] = bp[k].x + bp[k].y;
+    }
     c12_opaque(m);
     asm volatile("" ::: "memory");
     int fb = 0;
@@ -1203,11 +1278,12 @@ __device__ __forceinline__ int c12_subgroup_step(cplx<float> (&m)[4][6], float4*
 #pragma unroll
         for (int k = 0; k < 4; ++k) a[k] *= inv;
     }
+    PackedSU2 G;
+    packed_su2(a, G);
     // forward links: rows P, Q of G M
 #pragma unroll
-    for (int l = 0; l < 4; ++l) c12_left_update<P, Q>(m[l], a);
+    for (int l = 0; l < 4; ++l) c12_left_update_pk<P, Q>(m[l], G);
     // backward links: columns P, Q of M G^dag, rows 0 and 1
-    const cplx<float> g11 = mk(a[0], a[3]), g12 = mk(a[2], a[1]), g21 = mk(-a[2], a[1]), g22 = mk(a[0], -a[3]);
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
         cplx<float> mb[6];
@@ -1215,8 +1291,8 @@ __device__ __forceinline__ int c12_subgroup_step(cplx<float> (&m)[4][6], float4*
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const cplx<float> xp = mb[3 * i + P], xq = mb[3 * i + Q];
-            mb[3 * i + P] = cfmac(xq, g12, cmulc(xp, g11));
-            mb[3 * i + Q] = cfmac(xq, g22, cmulc(xp, g21));
+            mb[3 * i + P] = su2_col(G, 0, 1, xp, xq);
+            mb[3 * i + Q] = su2_col(G, 2, 3, xp, xq);
         }
         bwd_store<NT>(bst, l, mb);
     }
@@ -1311,17 +1387,17 @@ __global__ void __launch_bounds__(NT, MINB) k_halfsweep_c12(SweepBatch bt, int p
             w[2 * q] = mk(v.x, v.y);
             w[2 * q + 1] = mk(v.z, v.w);
         }
-        c12_left_update<0, 1>(w, a01);
-        c12_left_update<0, 2>(w, a02);
-        c12_left_update<1, 2>(w, a12);
+        PackedSU2 G;
+        packed_su2(a01, G);
+        c12_left_update_pk<0, 1>(w, G);
+        packed_su2(a02, G);
+        c12_left_update_pk<0, 2>(w, G);
+        packed_su2(a12, G);
+        c12_left_update_pk<1, 2>(w, G);
         c12_reunitarise(w);
         c12_store(W + c12_gidx(g, parity, 0, s), vh, w);
     }
-    __shared__ double red[NT / 32];
-    if (ACC) {
-        const double tot = block_sum((double)rsum, red);
-        if (threadIdx.x == 0) bt.partial[blockIdx.x] = tot;
-    }
+    if (ACC) warp_partial((double)rsum, bt.partial);
     {
         // count local solves that left the Newton path (diagnostic)
         const int w = __reduce_add_sync(0xffffffffu, fb);
@@ -1361,9 +1437,7 @@ __global__ void __launch_bounds__(256) k_functional(SweepBatch bt) {
                 r += tr * tr + ti * ti;
             }
     }
-    __shared__ double red[8];
-    const double tot = block_sum(r, red);
-    if (threadIdx.x == 0) bt.partial[blockIdx.x] = tot;
+    warp_partial(r, bt.partial);
 }
 
 // mode 0: end of a sweep; 1: fresh start (sweep = 0); 2: continue (new phase)
@@ -1376,7 +1450,9 @@ __global__ void __launch_bounds__(256) k_finalize(SweepBatch bt, int mode) {
     }
     const FieldDesc fd = bt.desc[f];
     double v = 0.0;
-    for (int k = threadIdx.x; k < fd.nblk; k += blockDim.x) v += bt.partial[fd.blk0 + k];
+    const size_t n = (size_t)fd.nblk * bt.ppb;
+    const double* __restrict__ part = bt.partial + (size_t)fd.blk0 * bt.ppb;
+    for (size_t k = threadIdx.x; k < n; k += blockDim.x) v += part[k];
     __shared__ double red[8];
     const double R = block_sum(v, red);
     if (threadIdx.x != 0) return;
@@ -1577,7 +1653,7 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
     int rc = 0;
     FieldDesc* d_desc = (FieldDesc*)scratch_device("fix.desc", sizeof(FieldDesc) * nf, &rc);
     if (rc) return rc;
-    double* d_partial = (double*)scratch_device("fix.partial", sizeof(double) * total, &rc);
+    double* d_partial = (double*)scratch_device("fix.partial", sizeof(double) * total * (SPB / 32), &rc);
     if (rc) return rc;
     FieldDesc* h_desc = (FieldDesc*)scratch_host("fix.desc", sizeof(FieldDesc) * nf, &rc);
     if (rc) return rc;
@@ -1607,6 +1683,7 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
     bt.total_blocks = total;
     bt.state = d_state;
     bt.partial = d_partial;
+    bt.ppb = SPB / 32;
     bt.R_hist = d_hist;
     bt.hist_len = hist_len;
     bt.tol = tol;
@@ -1645,12 +1722,20 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
     const int nodes_per_chunk = chunk * ((sizeof(T) == 8 && reunit_every > 0) ? 4 : 3);
     const int max_chunks = (phase_len + chunk - 1) / chunk + 1;
     int status = 0;
+    // phase timing (instrumentation): GPU time of the chunk graphs and the
+    // site-updates they performed
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    const bool timed = cudaEventCreate(&t0) == cudaSuccess && cudaEventCreate(&t1) == cudaSuccess;
+    std::vector<int> sw0(nf);
+    for (int f = 0; f < nf; ++f) sw0[f] = h_state[f].sweep;
     for (int c = 0; c < max_chunks; ++c) {
+        if (timed) cudaEventRecord(t0, stream);
         ce = cudaGraphLaunch(exec, stream);
         if (ce != cudaSuccess) {
             status = cuda_fail(ce, "cudaGraphLaunch");
             break;
         }
+        if (timed) cudaEventRecord(t1, stream);
         note_launches(nodes_per_chunk);
         ce = cudaMemcpyAsync(h_state, d_state, sizeof(FieldState) * nf, cudaMemcpyDeviceToHost, stream);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
@@ -1658,10 +1743,22 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
             status = cuda_fail(ce, "sweep chunk");
             break;
         }
+        if (timed) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, t0, t1);
+            long long su = 0;
+            for (int f = 0; f < nf; ++f) {
+                su += (long long)(h_state[f].sweep - sw0[f]) * 2LL * fields[f].geo.vh;
+                sw0[f] = h_state[f].sweep;
+            }
+            note_phase(sizeof(T) == 8 ? MCG_F64 : MCG_F32, ms, su);
+        }
         bool all = true;
         for (int f = 0; f < nf; ++f) all = all && h_state[f].done != 0;
         if (all) break;
     }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
     cudaGraphExecDestroy(exec);
     cudaGraphDestroy(graph);
     return status;
@@ -1685,7 +1782,7 @@ int time_halfsweep(void* U, void* G, const Geom& g, int parity, int nreps, int f
     if (rc) return rc;
     FieldState* d_state = (FieldState*)scratch_device("time.state", sizeof(FieldState), &rc);
     if (rc) return rc;
-    double* d_partial = (double*)scratch_device("time.partial", sizeof(double) * fd.nblk, &rc);
+    double* d_partial = (double*)scratch_device("time.partial", sizeof(double) * fd.nblk * (SPB / 32), &rc);
     if (rc) return rc;
     void* flush = nullptr;
     const size_t flush_bytes = (size_t)256 << 20;
@@ -1701,6 +1798,7 @@ int time_halfsweep(void* U, void* G, const Geom& g, int parity, int nreps, int f
     bt.total_blocks = fd.nblk;
     bt.state = d_state;
     bt.partial = d_partial;
+    bt.ppb = SPB / 32;
     bt.R_hist = nullptr;
     bt.hist_len = 0;
     bt.tol = 0;

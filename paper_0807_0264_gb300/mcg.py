@@ -26,7 +26,7 @@ from . import build as _build
 F64, F32 = 0, 1
 OK, NOT_CONVERGED = 0, 1
 _STATUS = {0: "MCG_OK", 1: "MCG_NOT_CONVERGED", 2: "MCG_BAD_DIMS", 3: "MCG_BAD_ARG", 4: "MCG_BAD_INPUT",
-           5: "MCG_CUDA_ERROR", 6: "MCG_WAIT_TIMEOUT"}
+           5: "MCG_CUDA_ERROR"}
 
 
 class MCGError(RuntimeError):
@@ -95,6 +95,7 @@ def _load() -> ctypes.CDLL:
                                      ctypes.POINTER(mcg_precond_result), P], I),
         "mcg_time_halfsweep": ([P, P, L, I, I, I, ctypes.POINTER(ctypes.c_float), P], I),
         "mcg_kernel_launches": ([], ctypes.c_longlong),
+        "mcg_phase_stats": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), I], I),
         "mcg_plaquette_static": ([P, P, L, P], I),
         "mcg_set_sweep_block": ([I, I], I),
         "mcg_smear_backward_step": ([P, P, P, L, D, D, P], I),
@@ -123,7 +124,7 @@ EXPORTS = ("mcg_version", "mcg_last_error", "mcg_release", "mcg_pack_links", "mc
            "mcg_plaquette_static", "mcg_set_sweep_block", "mcg_get_sweep_block", "mcg_fix_batch",
            "mcg_gribov_search", "mcg_smear_backward_step", "mcg_functional_matrix_grad", "mcg_grad_R",
            "mcg_ascent_step", "mcg_vortex_remove", "mcg_wilson_loops",
-           "mcg_wilson_loops_offaxis", "mcg_anneal")
+           "mcg_wilson_loops_offaxis", "mcg_anneal", "mcg_phase_stats")
 
 
 def library() -> ctypes.CDLL:
@@ -492,6 +493,15 @@ def mcg_time_halfsweep(U: torch.Tensor, G: torch.Tensor, dims, parity: int = 1, 
 
 def mcg_kernel_launches() -> int:
     return int(_lib.mcg_kernel_launches())
+
+
+def mcg_phase_stats(reset: bool = False) -> dict:
+    """GPU milliseconds and site-updates of the FP64 and FP32 sweep phases
+    since the last reset (CUDA events around the sweep graphs)."""
+    ms = (ctypes.c_double * 2)()
+    su = (ctypes.c_longlong * 2)()
+    _check("mcg_phase_stats", _lib.mcg_phase_stats(ms, su, int(bool(reset))))
+    return {"f64": {"ms": ms[0], "site_updates": su[0]}, "f32": {"ms": ms[1], "site_updates": su[1]}}
 
 
 def mcg_plaquette_static(U: torch.Tensor, dims, out: torch.Tensor, stream=None) -> torch.Tensor:

@@ -380,22 +380,54 @@ def test_precondition_pipeline_parity(mcg, nsmear, eps, rho):
     np.testing.assert_array_equal(mcg.mcg_unpack_center(Z, dims)[0].cpu().numpy(), o["m"])
 
 
+def oracle_response(dims, U, G, delta, seeds=(1, 2), **kw):
+    """Per link (site, mu): the largest change of the oracle's one-sweep result
+    (the link or Omega at its site) when every entry of every input link is
+    perturbed by a relative delta (complex Gaussian noise, seeded): the
+    conditioning of the local problems that decide the link, propagation
+    through the sweep included."""
+    base = oracle.fix(dims, U, G, tol=NEVER, max_sweeps=1, reunit_every=0, **kw)
+    resp = np.zeros(U.shape[:2])
+    for sd in seeds:
+        rng = np.random.default_rng(sd)
+        noise = rng.standard_normal(U.shape) + 1j * rng.standard_normal(U.shape)
+        r = oracle.fix(dims, U * (1 + delta * noise), G, tol=NEVER, max_sweeps=1, reunit_every=0, **kw)
+        dU = np.abs(r["U"] - base["U"]).max(axis=(2, 3))
+        dG = np.abs(r["G"] - base["G"]).max(axis=(1, 2))
+        resp = np.maximum(resp, np.maximum(dU, dG[:, None]))
+    return base, resp
+
+
 def test_full_size_20x40_one_sweep_parity(mcg):
     """20^3 x 40 (the bench workload's lattice): one FP64 sweep against the
-    oracle over every link, the FP32 sweep close, plaquette of the input."""
+    oracle over every link, R, and the vortex count of the result.
+
+    Per-link bar: |GPU - oracle| <= max(1e-11, 32 r) with r the link's
+    oracle response to a 1e-15 relative perturbation of the input links.  The
+    oracle itself moves by up to ~4e-11 under that perturbation on this field
+    (a few of the 960 000 local problems of a sweep have gaps of mu - A near
+    1e-6 of their scale), so no FP64 evaluation in another rounding order can
+    meet a flat 1e-11 there.  The factor 32: an entry of A or b is a sum of 16
+    products of sums of link entries (~20 operations); with terms of size s
+    the two sides' roundings differ by at most 2 x 20 x 16 eps s (coherent
+    worst case), while the probe moves the entry by ~8 delta s (random signs
+    over 16 terms): 80 eps / delta ~ 9.  A random probe meets the one most
+    sensitive direction of a local problem with ~1/sqrt(14) of its size (A and
+    b have 14 independent entries): 9 x 3.7 ~ 33, taken as 32.  Measured on
+    this field: worst err/r = 13."""
     dims = (20, 20, 20, 40)
     U = synth.make_field(dims, synth.W_PLAQ_06, 0)
     G = synth.identity_gauge(dims)
-    r = oracle.fix(dims, U, G, tol=NEVER, max_sweeps=1, reunit_every=0)
+    r, resp = oracle_response(dims, U, G, 1e-15)
     Ug, Gg, res = gpu_sweeps(mcg, U, G, dims, 1, reunit_every=0)
-    # Two correct FP64 solvers of the local 4x4 problem agree to ~1e-16 times
-    # its condition number 1/gap(mu - A).  Among the 960 000 local solves of a
-    # 20^3 x 40 sweep a handful are conditioned ~1e5..1e6, so the 1e-11 bar
-    # holds for all but a few links, whose deviation stays below 1e-9.
     err = np.maximum(np.abs(Ug - r["U"]).max(axis=(2, 3)), np.abs(Gg - r["G"]).max(axis=(1, 2))[:, None])
-    print("links beyond 1e-11:", int((err > 1e-11).sum()), "of", err.size, "max", float(err.max()))
-    assert (err > 1e-11).sum() <= 1e-3 * err.size, (err > 1e-11).sum()
-    assert err.max() <= 1e-8
+    bound = np.maximum(1e-11, 32.0 * resp)
+    widened = bound > 1e-11
+    print(f"links beyond 1e-11: {int((err > 1e-11).sum())}; bar widened by conditioning on "
+          f"{int(widened.sum())} of {err.size}; max err {float(err.max()):.3g}; "
+          f"max err/bar {float((err / bound).max()):.3g}")
+    assert (err <= bound).all(), np.argwhere(err > bound)[:10]
+    assert widened.sum() <= 1e-2 * err.size  # measured: 0.3 % of the links
     assert abs(res["R"][0] - r["R_hist"][-1]) <= 1e-12 * r["R_hist"][-1]
     Ud = pack(mcg, r["U"], dims)
     _, counts = mcg.mcg_center_project(Ud, dims)
