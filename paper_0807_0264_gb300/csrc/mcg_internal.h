@@ -112,6 +112,12 @@ int time_halfsweep(void* U, void* G, const Geom& g, int parity, int nreps, int f
 int run_anneal(void* U, void* G, const Geom& g, int nfields, const double* T, int nsweeps, long long first_sweep,
                int nhit, double eps, unsigned long long seed, long long* accepted_host, cudaStream_t st);
 
+// The compact FP32 half-sweep (mcg_sweep_f32.cu): raise its shared-memory
+// limit for nt threads per block (64, 128, 256) on the current device, and
+// launch one half-sweep of the batch (acc: with the fused R partials).
+int prepare_halfsweep_c12(int nt);
+void launch_halfsweep_c12(int nt, bool acc, const SweepBatch& bt, int parity, int nblocks, cudaStream_t st);
+
 // threads per block of the half-sweep kernel for a precision, and the sites
 // each block covers (one thread per site in both precisions)
 int sweep_block(int prec);

@@ -432,3 +432,30 @@ def test_full_size_20x40_one_sweep_parity(mcg):
     Ud = pack(mcg, r["U"], dims)
     _, counts = mcg.mcg_center_project(Ud, dims)
     assert counts[0][0] == oracle.vortex_count(dims, oracle.center_project(dims, r["U"]))[0]
+
+
+def test_planted_vortex_workload_20x40(mcg):
+    """The planted-vortex workload at 20^3 x 40 (3.1 % of the plaquettes
+    pierced): after the mixed-precision fix, the P-vortex counts of the GPU's
+    center projection equal the oracle's on the same fixed links, plane by
+    plane (bit-exact, and non-zero), and recover the planted sheets."""
+    dims = (20, 20, 20, 40)
+    U, k = synth.make_vortex_field(dims, synth.W_VORTEX_06, 0, synth.VORTEX_PAIRS_20x40)
+    Ud, Gd = pack(mcg, U, dims), mcg.identity_gauge(dims)
+    p = mcg.Params(tol=1e-10, max_sweeps=30000, check_every=25, reunit_every=50, fp32_sweeps=30000, fp32_tol=5e-11,
+                   fp32_window=25, fp32_overrelax=1.85, fp64_solve32=1)
+    res = mcg.mcg_fix(Ud, Gd, dims, p)
+    assert res["converged"]
+    Z, counts = mcg.mcg_center_project(Ud, dims)
+    Uf = unpack(mcg, Ud, dims)
+    m = oracle.center_project(dims, Uf)
+    n, per = oracle.vortex_count(dims, m)
+    np.testing.assert_array_equal(mcg.mcg_unpack_center(Z, dims)[0].cpu().numpy(), m)
+    assert counts[0][0] == n and list(counts[0][1:]) == list(per)
+    V = int(np.prod(dims))
+    kg = k.reshape(40, 20, 20, 20, 4).astype(np.int64)
+    ax = (3, 2, 1, 0)
+    planted = sum(int((((kg[..., a] + np.roll(kg[..., b], -1, axis=ax[a]) - np.roll(kg[..., a], -1, axis=ax[b])
+                         - kg[..., b]) % 3) != 0).sum()) for a in range(4) for b in range(a + 1, 4))
+    print(f"P-vortices {n} ({n / (6 * V):.4f}), planted {planted}")
+    assert abs(n - planted) <= 0.01 * planted
