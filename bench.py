@@ -488,6 +488,7 @@ def profile_kernels(mcg, U, dims, dev):
     mcg.mcg_fix(Uf, Gf, dims, mcg.Params(tol=-1e300, max_sweeps=4, check_every=2, reunit_every=2, fp32_sweeps=2,
                                          fp32_tol=-1e300, fp32_window=1, fp32_overrelax=OMEGA, fp64_solve32=1))
     mcg.mcg_fix(Uf, Gf, dims, mcg.Params(tol=-1e300, max_sweeps=2, check_every=2, reunit_every=2))
+    mcg.mcg_fix(Uf, Gf, dims, mcg.Params(tol=-1e300, max_sweeps=2, check_every=2, fp64_df=1))
     mcg.mcg_apply_gauge(Uf, Gf, dims)
     mcg.mcg_reunitarise(Gf, 1, dims)
     mcg.mcg_plaquette(Uf, dims)
@@ -532,7 +533,7 @@ def mixed_error_block(args, mcg, U, dims, levels, mixed, dev):
     handoff = mcg.Params(tol=1e300, max_sweeps=mixed.max_sweeps, check_every=mixed.check_every,
                          reunit_every=mixed.reunit_every, fp32_sweeps=mixed.fp32_sweeps, fp32_tol=mixed.fp32_tol,
                          fp32_window=mixed.fp32_window, fp32_overrelax=mixed.fp32_overrelax,
-                         fp64_solve32=mixed.fp64_solve32)
+                         fp64_solve32=mixed.fp64_solve32, fp64_df=mixed.fp64_df)
 
     def compare(F):
         """F (device, FP64) -> hand-off H in place; finishes from H compared."""
@@ -540,10 +541,12 @@ def mixed_error_block(args, mcg, U, dims, levels, mixed, dev):
         h = mcg.mcg_fix(F, Gh, dims, handoff)
         H = mcg.mcg_unpack_links(F, dims)[0].cpu().numpy()
         row = {"handoff_sweeps": h["sweeps"][0]}
-        for name, s32 in (("gpu_bench_finish", 1), ("gpu_exact_finish", 0)):
+        finishes = (("gpu_bench_finish", dict(fp64_solve32=mixed.fp64_solve32, fp64_df=mixed.fp64_df)),
+                    ("gpu_exact_finish", dict(fp64_solve32=0, fp64_df=0)))
+        for name, kw in finishes:
             Ug, Gg = F.clone(), mcg.identity_gauge(dims, 1, mcg.F64, dev)
             rg = mcg.mcg_fix(Ug, Gg, dims, mcg.Params(tol=1e-10, max_sweeps=20000, check_every=25, reunit_every=50,
-                                                      fp64_solve32=s32))
+                                                      **kw))
             _, cnt = mcg.mcg_center_project(Ug, dims)
             row[name] = {"sweeps": rg["sweeps"][0], "converged": rg["converged"], "V": rg["R"][0] / (36.0 * V),
                          "vortices": int(cnt[0][0]), "U": mcg.mcg_unpack_links(Ug, dims)[0].cpu().numpy()}
@@ -581,7 +584,7 @@ def mixed_error_block(args, mcg, U, dims, levels, mixed, dev):
         del Up
     return {"method": "per level and per fix (the smeared field's, then the preconditioned field's): the mixed "
                       "schedule runs to its hand-off and first FP64 sweep (field H); from H the GPU's FP64 finish "
-                      "(the bench's: local solve in FP32) and the GPU's exact FP64 finish run to dV_U<1e-10, and "
+                      "(the bench's: double-float moves, local solve in FP32) and the GPU's exact FP64 finish run to dV_U<1e-10, and "
                       "so does the oracle's plain FP64 relaxation on the host cores; FP64 smearing",
             "levels": out}
 
@@ -679,7 +682,7 @@ def main():
              "f64": mcg.autotune_sweep_block(U_warm.clone(), dims, reps=3)}
     mixed = mcg.Params(tol=1e-10, max_sweeps=30000, check_every=25, reunit_every=50, fp32_sweeps=30000,
                        fp32_tol=float(os.environ.get("MCG_FP32_TOL", "5e-11")), fp32_window=25,
-                       fp32_overrelax=OMEGA, fp64_solve32=1)
+                       fp32_overrelax=OMEGA, fp64_solve32=1, fp64_df=int(os.environ.get("MCG_FP64_DF", "1")))
     stream = torch.cuda.current_stream(dev)
 
     def step(params, smear_prec):
@@ -906,8 +909,11 @@ def main():
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": config_of(args, f"batched levels, FP32 smearing, FP32 sweeps (over-relaxed, omega="
                                           f"{mixed.fp32_overrelax}, until the 25-sweep mean dV_U < "
-                                          f"{mixed.fp32_tol:g}) then FP64 plain relaxation (local 4x4 solve in "
-                                          f"FP32, G normalised and applied in FP64) to dV_U<1e-10"),
+                                          f"{mixed.fp32_tol:g}) then FP64-class plain relaxation ("
+                                          + ("double-float moves, local 4x4 solve in FP32, transform applied in "
+                                             "FP64" if mixed.fp64_df else
+                                             "local 4x4 solve in FP32, G normalised and applied in FP64")
+                                          + ") to dV_U<1e-10 in FP64"),
                 "ttc": {"mixed_ms_to_converged": ms, "plain_fp64": plain_info,
                         "sweeps": sw_all, "sweeps_fp32": sw32,
                         "V_fixed": [r["V_fixed"] for r in mixed_res],

@@ -94,6 +94,15 @@ typedef struct {
                        /* applied in FP64 (G stays unitary, the field stays on  */
                        /* its gauge orbit, R and the stop rule stay FP64; each  */
                        /* site lands within ~1e-7 of its exact local maximum).  */
+    int fp64_df;       /* FP64 sweeps: 1 = run them in double-float arithmetic */
+                       /* (each real an FP32 pair hi + lo, ~48-bit significand, */
+                       /* in the compact rows-0-and-1 storage; local problem  */
+                       /* built and solved in FP32 as with fp64_solve32, its   */
+                       /* solution normalised in FP64); R and the stop rule    */
+                       /* stay FP64; the phase's transform is re-unitarised   */
+                       /* in FP64 and applied to the FP64 links at the end, so */
+                       /* the result is exactly on its gauge orbit.  GB300     */
+                       /* runs FP64 at ~1/60 of its FP32 rate.  0 = FP64.      */
 } mcg_params;
 
 /* One field of a heterogeneous batch: device pointers to its links and its
@@ -336,6 +345,22 @@ int mcg_precondition_fix(void* U, void* G, int8_t* Z, const mcg_lattice* lat, co
 int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_out, const mcg_lattice* lat,
                             const mcg_params* params, double rho, double eps, const int* nsmear, int nlevels,
                             int smear_precision, mcg_precond_result* results, cudaStream_t stream);
+
+/*
+ * One FP64 half-sweep (exact local maximisation, as mcg_fix's FP64 sweeps) of
+ * the sites of `parity` whose t lies in [t_lo, t_hi): the compute step of a
+ * lattice split into t-slabs, one per process (domain decomposition; the
+ * caller's array is a slab plus ghost layers of the neighbouring slabs'
+ * links, which the sites read and update like any other link).  One field,
+ * MCG_F64, in place on U and G.  R_out (host, may be NULL): the sum of
+ * |tr U|^2 over the 8 links of every updated site, after the update
+ * (synchronises); summed over the slabs' odd half-sweeps it is the lattice's
+ * R, since every link has exactly one odd end.  Same-parity sites share no
+ * link (Sec. II.A checkerboard), so the slabs' half-sweeps together equal the
+ * lattice's.
+ */
+int mcg_halfsweep_slab(void* U, void* G, const mcg_lattice* lat, int parity, int t_lo, int t_hi, double* R_out,
+                       cudaStream_t stream);
 
 /*
  * MCG relaxation (as mcg_fix) of a batch of fields of any sizes, all of one

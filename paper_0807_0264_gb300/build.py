@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libmcg.so")
-SOURCES = ["mcg_capi.cu", "mcg_field.cu", "mcg_observables.cu", "mcg_smear.cu", "mcg_sweep.cu", "mcg_sweep_f32.cu"]
+SOURCES = ["mcg_capi.cu", "mcg_field.cu", "mcg_observables.cu", "mcg_smear.cu", "mcg_sweep.cu", "mcg_sweep_f32.cu", "mcg_sweep_df.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -190,6 +190,7 @@ static bool overlap(const void* a, size_t na, const void* b, size_t nb) {
 
 static int check_params(const mcg_params* p) {
     if (!p) return fail(MCG_BAD_ARG, "params is NULL");
+    if (p->fp64_df != 0 && p->fp64_df != 1) return fail(MCG_BAD_ARG, "fp64_df must be 0 or 1");
     if (p->max_sweeps < 0) return fail(MCG_BAD_ARG, "max_sweeps must be >= 0");
     if (p->check_every < 1) return fail(MCG_BAD_ARG, "check_every must be >= 1");
     if (p->reunit_every < 0 || p->fp32_sweeps < 0) return fail(MCG_BAD_ARG, "negative schedule parameter");
@@ -273,10 +274,49 @@ static int fix_fields(const std::vector<FieldSpec>& fs, int prec, const mcg_para
         for (int f = 0; f < nf; ++f) s32[f] = h_state[f].sweep;
         // hand-off: FP64 re-unitarised transform applied to the FP64 links
         for (int f = 0; f < nf; ++f)
-            if ((rc = launch_handoff(fds[f].G, (double*)fs[f].U, (double*)fs[f].G, fs[f].g, 1, st))) return rc;
+            if ((rc = launch_handoff(fds[f].G, nullptr, (double*)fs[f].U, (double*)fs[f].G, fs[f].g, 1, st)))
+                return rc;
         fresh = false;
     }
-    if (prec == MCG_F64) {
+    if (prec == MCG_F64 && prm->fp64_df) {
+        // FP64-class sweeps in double-float on compact copies of the links and
+        // a transform W of the phase (from the identity); at the end W is
+        // re-unitarised in FP64 and applied to the FP64 links and transform
+        size_t lo_tot = 0, go_tot = 0;
+        for (const auto& f : fs) {
+            lo_tot += c12_link_chunks(f.g);
+            go_tot += c12_gauge_chunks(f.g);
+        }
+        char* Uh = (char*)scratch_device("fix.df.Uh", 16 * lo_tot, &rc);
+        if (rc) return rc;
+        char* Ul = (char*)scratch_device("fix.df.Ul", 16 * lo_tot, &rc);
+        if (rc) return rc;
+        char* Wh = (char*)scratch_device("fix.df.Wh", 16 * go_tot, &rc);
+        if (rc) return rc;
+        char* Wl = (char*)scratch_device("fix.df.Wl", 16 * go_tot, &rc);
+        if (rc) return rc;
+        std::vector<FieldDesc> fds(nf);
+        size_t lo = 0, go = 0;
+        for (int f = 0; f < nf; ++f) {
+            const Geom& g = fs[f].g;
+            fds[f].U = Uh + 16 * lo;
+            fds[f].Ulo = Ul + 16 * lo;
+            fds[f].G = Wh + 16 * go;
+            fds[f].Glo = Wl + 16 * go;
+            fds[f].geo = g;
+            fds[f].norm = 1.0 / (9.0 * 8.0 * g.vh);
+            lo += c12_link_chunks(g);
+            go += c12_gauge_chunks(g);
+            if ((rc = launch_to_df((const double*)fs[f].U, fds[f].U, fds[f].Ulo, g, 4, 1, st))) return rc;
+            if ((rc = launch_identity_df(fds[f].G, fds[f].Glo, g, 1, st))) return rc;
+        }
+        rc = run_fix_phase<DoubleFloat>(fds, d_state, h_state, d_hist, hist_len, prm->tol, 1, 1.0, 0,
+                                        prm->max_sweeps, prm->check_every, fresh, st);
+        if (rc) return rc;
+        for (int f = 0; f < nf; ++f)
+            if ((rc = launch_handoff(fds[f].G, fds[f].Glo, (double*)fs[f].U, (double*)fs[f].G, fs[f].g, 1, st)))
+                return rc;
+    } else if (prec == MCG_F64) {
         std::vector<FieldDesc> fds(nf);
         for (int f = 0; f < nf; ++f) {
             fds[f].U = fs[f].U;
@@ -687,6 +727,19 @@ int mcg_time_halfsweep(void* U, void* G, const mcg_lattice* lat, int parity, int
     if ((rc = launch_to_c12(U, MCG_F32, U12, g, 4, 1, stream))) return rc;
     if ((rc = launch_to_c12(G, MCG_F32, W12, g, 1, 1, stream))) return rc;
     return time_halfsweep<float>(U12, W12, g, parity, nreps, flush_l2, ms_out, stream);
+}
+
+int mcg_halfsweep_slab(void* U, void* G, const mcg_lattice* lat, int parity, int t_lo, int t_hi, double* R_out,
+                      cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if (!U || !G) return fail(MCG_BAD_ARG, "null pointer");
+    if (lat->precision != MCG_F64 || lat->nfields != 1) return fail(MCG_BAD_ARG, "one FP64 field");
+    if (parity != 0 && parity != 1) return fail(MCG_BAD_ARG, "parity must be 0 or 1");
+    if (t_lo < 0 || t_hi > g.n[3] || t_lo >= t_hi) return fail(MCG_BAD_ARG, "need 0 <= t_lo < t_hi <= N_t");
+    if (overlap(U, 16 * link_elems(g), G, 16 * gauge_elems(g))) return fail(MCG_BAD_ARG, "U and G overlap");
+    return run_halfsweep_slab(U, G, g, parity, t_lo, t_hi, R_out != nullptr, R_out, stream);
 }
 
 int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_out, const mcg_lattice* lat,

@@ -209,8 +209,9 @@ __global__ void __launch_bounds__(FT) k_reunit_all(cplx<T>* __restrict__ M, int 
 // Mixed-precision hand-off, pass 1: W64 = reunit(W) written to scratch (W in
 // the compact FP32 form: rows 0 and 1; the FP64 re-unitarisation rebuilds row
 // 2 from them), G64 <- reunit(W64 G64).
-__global__ void __launch_bounds__(FT) k_handoff_gauge(const float4* __restrict__ W, cplx<double>* __restrict__ W64,
-                                                      cplx<double>* __restrict__ G, Geom g, int nfields) {
+__global__ void __launch_bounds__(FT) k_handoff_gauge(const float4* __restrict__ W, const float4* __restrict__ Wlo,
+                                                      cplx<double>* __restrict__ W64, cplx<double>* __restrict__ G,
+                                                      Geom g, int nfields) {
     const long long n = 2LL * g.vh * nfields;
     const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= n) return;
@@ -225,6 +226,11 @@ __global__ void __launch_bounds__(FT) k_handoff_gauge(const float4* __restrict__
         const float4 v = Wf[c12_gidx(g, p, q, s)];
         w[2 * q] = mk((double)v.x, (double)v.y);
         w[2 * q + 1] = mk((double)v.z, (double)v.w);
+        if (Wlo) {
+            const float4 l = Wlo[(size_t)f * c12_gauge_chunks(g) + c12_gidx(g, p, q, s)];
+            w[2 * q] = mk(w[2 * q].x + (double)l.x, w[2 * q].y + (double)l.y);
+            w[2 * q + 1] = mk(w[2 * q + 1].x + (double)l.z, w[2 * q + 1].y + (double)l.w);
+        }
     }
 #pragma unroll
     for (int e = 6; e < 9; ++e) w[e] = mk(0.0, 0.0);
@@ -695,13 +701,15 @@ int compute_center(const void* U, int prec, int8_t* Z, const Geom& g, int nfield
     return 0;
 }
 
-int launch_handoff(const void* W32, double* U64, double* G64, const Geom& g, int nfields, cudaStream_t st) {
+int launch_handoff(const void* W32, const void* W32lo, double* U64, double* G64, const Geom& g, int nfields,
+                   cudaStream_t st) {
     int rc = 0;
     cplx<double>* W64 =
         (cplx<double>*)scratch_device("handoff.W64", sizeof(cplx<double>) * gauge_elems(g) * nfields, &rc);
     if (rc) return rc;
     const long long n = 2LL * g.vh * nfields;
-    k_handoff_gauge<<<blocks_for(n, FT), FT, 0, st>>>((const float4*)W32, W64, (cplx<double>*)G64, g, nfields);
+    k_handoff_gauge<<<blocks_for(n, FT), FT, 0, st>>>((const float4*)W32, (const float4*)W32lo, W64,
+                                                      (cplx<double>*)G64, g, nfields);
     k_apply_gauge<double><<<blocks_for(n, FT), FT, 0, st>>>((cplx<double>*)U64, W64, g, nfields);
     MCG_CK(cudaGetLastError());
     note_launches(2);

@@ -55,7 +55,15 @@ struct FieldDesc {
     int blk0;     // first block of this field in the flattened grid
     int nblk;     // blocks of this field
     double norm;  // 1 / (9 * 4V)
+    void* Ulo = nullptr;  // double-float storage: the lo parts of U and G (U, G
+    void* Glo = nullptr;  // then hold the hi parts), compact layout
+    int t_lo = 0;         // FP64 half-sweep: only sites with t_lo <= t < t_hi
+    int t_hi = 1 << 30;   // (a t-slab of a decomposed lattice)
 };
+
+// Tag of the double-float sweep phase in run_fix_phase<T> (T = float: compact
+// FP32, double: FP64 full layout, DoubleFloat: compact hi + lo FP32 pairs).
+struct DoubleFloat {};
 
 constexpr int kRing = 32;  // R history kept per field for windowed stop tests
 
@@ -104,6 +112,12 @@ template <typename T>
 int time_halfsweep(void* U, void* G, const Geom& g, int parity, int nreps, int flush_l2, float* ms,
                    cudaStream_t stream);
 
+// One FP64 half-sweep (exact local solve) of the sites of `parity` with
+// t_lo <= t < t_hi on one field; want_R: the odd-parity R partial of those
+// sites' 8 links to *R_host (synchronises).
+int run_halfsweep_slab(void* U, void* G, const Geom& g, int parity, int t_lo, int t_hi, bool want_R, double* R_host,
+                       cudaStream_t stream);
+
 // Simulated annealing (FP64 fields of one lattice, fields contiguous): for
 // k < nsweeps an even then an odd Metropolis half-sweep at temperature T[k]
 // (host array) with sweep number first_sweep + k in the random counter; then
@@ -111,6 +125,16 @@ int time_halfsweep(void* U, void* G, const Geom& g, int parity, int nreps, int f
 // accepted hits per field.  Synchronises.
 int run_anneal(void* U, void* G, const Geom& g, int nfields, const double* T, int nsweeps, long long first_sweep,
                int nhit, double eps, unsigned long long seed, long long* accepted_host, cudaStream_t st);
+
+// The double-float half-sweep (mcg_sweep_df.cu): threads (= sites) per block,
+// shared-memory set-up, launches of the half-sweep and of the R reduction,
+// FP64 full layout -> double-float compact links, identity transform.
+int df_threads();
+int prepare_halfsweep_df();
+void launch_halfsweep_df(bool acc, const SweepBatch& bt, int parity, int nblocks, cudaStream_t st);
+void launch_functional_df(const SweepBatch& bt, int nblocks, cudaStream_t st);
+int launch_to_df(const double* src, void* hi, void* lo, const Geom& g, int nmat, int nfields, cudaStream_t st);
+int launch_identity_df(void* hi, void* lo, const Geom& g, int nfields, cudaStream_t st);
 
 // The compact FP32 half-sweep (mcg_sweep_f32.cu): raise its shared-memory
 // limit for nt threads per block (64, 128, 256) on the current device, and
@@ -147,8 +171,10 @@ int compute_functional(const void* U, int prec, const Geom& g, int nfields, doub
 int compute_center(const void* U, int prec, int8_t* Z, const Geom& g, int nfields, long long* counts_host,
                    cudaStream_t st);
 // FP32 transform W of this call (compact form) -> FP64: W64 = reunit(W);
-// U64 <- W64 U64 W64(x+mu)^dag; G64 <- reunit(W64 G64).
-int launch_handoff(const void* W32, double* U64, double* G64, const Geom& g, int nfields, cudaStream_t st);
+// U64 <- W64 U64 W64(x+mu)^dag; G64 <- reunit(W64 G64).  W32lo (may be null):
+// lo parts of a double-float W (W = hi + lo).
+int launch_handoff(const void* W32, const void* W32lo, double* U64, double* G64, const Geom& g, int nfields,
+                   cudaStream_t st);
 // compact FP32 working storage (rows 0 and 1 of each matrix) of the FP32
 // sweep phase: from / to the full layout; nmat = 4 for links, 1 for a gauge
 // transform

@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "mcg_common.cuh"
@@ -210,7 +211,12 @@ __global__ void __launch_bounds__(NT, 2) k_halfsweep(SweepBatch bt, int parity) 
     cplx<T>* __restrict__ U = reinterpret_cast<cplx<T>*>(fd.U);
     cplx<T>* __restrict__ G = reinterpret_cast<cplx<T>*>(fd.G);
     const int s = (blockIdx.x - fd.blk0) * NT + threadIdx.x;
-    const bool active = s < g.vh;
+    bool active = s < g.vh;
+    int c[4];
+    if (active) {
+        eo_coords(g, parity, s, c);
+        active = c[3] >= fd.t_lo && c[3] < fd.t_hi;  // the sites of a t-slab (whole lattice by default)
+    }
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmemLinks<T, NT> lk;
@@ -219,8 +225,6 @@ __global__ void __launch_bounds__(NT, 2) k_halfsweep(SweepBatch bt, int parity) 
     double rsum = 0.0;
     int fb = 0;
     if (active) {
-        int c[4];
-        eo_coords(g, parity, s, c);
         int sb[4];
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) sb[mu] = eo_neighbor(g, c, mu, -1);
@@ -555,6 +559,16 @@ __global__ void __launch_bounds__(128) k_reunit_pending(SweepBatch bt) {
     }
 }
 
+// sum of n partials in a fixed order (one block)
+__global__ void __launch_bounds__(256) k_sum_slab_partials(const double* __restrict__ partial, int n,
+                                                           double* __restrict__ out) {
+    double v = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) v += partial[k];
+    __shared__ double red[8];
+    const double tot = block_sum(v, red);
+    if (threadIdx.x == 0) *out = tot;
+}
+
 // ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
@@ -627,12 +641,21 @@ static void launch_halfsweep(int nt, bool acc, const SweepBatch& bt, int parity,
 
 template <typename T>
 static int enqueue_sweep(const SweepBatch& bt, int nt, int spb, cudaStream_t st) {
-    launch_halfsweep<T>(nt, false, bt, 0, bt.total_blocks, st);
-    launch_halfsweep<T>(nt, true, bt, 1, bt.total_blocks, st);
-    k_finalize<<<bt.nf, 256, 0, st>>>(bt, 0);
-    // FP32 sweeps re-unitarise inside the half-sweep kernel
-    if constexpr (sizeof(T) == 8)
-        if (bt.reunit_every > 0) k_reunit_pending<T><<<bt.total_blocks, spb, 0, st>>>(bt);
+    if constexpr (std::is_same<T, DoubleFloat>::value) {
+        // no re-unitarisation inside the phase: the double-float links drift
+        // from unitarity by ~1e-14 per sweep; the output is the FP64 field
+        // transformed by the re-unitarised W of the phase
+        launch_halfsweep_df(false, bt, 0, bt.total_blocks, st);
+        launch_halfsweep_df(true, bt, 1, bt.total_blocks, st);
+        k_finalize<<<bt.nf, 256, 0, st>>>(bt, 0);
+    } else {
+        launch_halfsweep<T>(nt, false, bt, 0, bt.total_blocks, st);
+        launch_halfsweep<T>(nt, true, bt, 1, bt.total_blocks, st);
+        k_finalize<<<bt.nf, 256, 0, st>>>(bt, 0);
+        // FP32 sweeps re-unitarise inside the half-sweep kernel
+        if constexpr (sizeof(T) == 8)
+            if (bt.reunit_every > 0) k_reunit_pending<T><<<bt.total_blocks, spb, 0, st>>>(bt);
+    }
     return 0;
 }
 
@@ -640,9 +663,10 @@ template <typename T>
 int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, FieldState* h_state, double* d_hist,
                   int hist_len, double tol, int window, double omega, int reunit_every, int abs_cap,
                   int check_every, bool fresh, cudaStream_t stream, bool solve32) {
-    const int prec = sizeof(T) == 8 ? MCG_F64 : MCG_F32;
-    const int NT = sweep_block(prec);
-    const int SPB = sweep_sites_per_block(prec);
+    constexpr bool DF = std::is_same<T, DoubleFloat>::value;
+    const int prec = (DF || sizeof(T) == 8) ? MCG_F64 : MCG_F32;
+    const int NT = DF ? df_threads() : sweep_block(prec);
+    const int SPB = DF ? NT : sweep_sites_per_block(prec);
     const int nf = (int)fields_in.size();
     std::vector<FieldDesc> fields = fields_in;
     int total = 0;
@@ -693,9 +717,13 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
     bt.omega = omega;
     bt.solve32 = solve32 ? 1 : 0;
 
-    if ((rc = prepare_halfsweep<T>(NT))) return rc;
-
-    k_functional<T><<<total, SPB, 0, stream>>>(bt);
+    if constexpr (DF) {
+        if ((rc = prepare_halfsweep_df())) return rc;
+        launch_functional_df(bt, total, stream);
+    } else {
+        if ((rc = prepare_halfsweep<T>(NT))) return rc;
+        k_functional<T><<<total, SPB, 0, stream>>>(bt);
+    }
     k_finalize<<<nf, 256, 0, stream>>>(bt, fresh ? 1 : 2);
     MCG_CK(cudaGetLastError());
     note_launches(2);
@@ -720,7 +748,7 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
         cudaGraphDestroy(graph);
         return cuda_fail(ce, "cudaGraphInstantiate");
     }
-    const int nodes_per_chunk = chunk * ((sizeof(T) == 8 && reunit_every > 0) ? 4 : 3);
+    const int nodes_per_chunk = chunk * ((!DF && sizeof(T) == 8 && reunit_every > 0) ? 4 : 3);
     const int max_chunks = (phase_len + chunk - 1) / chunk + 1;
     int status = 0;
     // phase timing (instrumentation): GPU time of the chunk graphs and the
@@ -752,7 +780,7 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
                 su += (long long)(h_state[f].sweep - sw0[f]) * 2LL * fields[f].geo.vh;
                 sw0[f] = h_state[f].sweep;
             }
-            note_phase(sizeof(T) == 8 ? MCG_F64 : MCG_F32, ms, su);
+            note_phase(prec, ms, su);
         }
         bool all = true;
         for (int f = 0; f < nf; ++f) all = all && h_state[f].done != 0;
@@ -876,11 +904,68 @@ int run_anneal(void* U, void* G, const Geom& g, int nfields, const double* T, in
     return 0;
 }
 
+int run_halfsweep_slab(void* U, void* G, const Geom& g, int parity, int t_lo, int t_hi, bool want_R, double* R_host,
+                       cudaStream_t stream) {
+    const int NT = sweep_block(MCG_F64);
+    int rc = 0;
+    FieldDesc fd;
+    fd.U = U;
+    fd.G = G;
+    fd.geo = g;
+    fd.blk0 = 0;
+    fd.nblk = (g.vh + NT - 1) / NT;
+    fd.norm = 1.0 / (9.0 * 8.0 * g.vh);
+    fd.t_lo = t_lo;
+    fd.t_hi = t_hi;
+    FieldDesc* d_desc = (FieldDesc*)scratch_device("slab.desc", sizeof(FieldDesc), &rc);
+    if (rc) return rc;
+    FieldState* d_state = (FieldState*)scratch_device("slab.state", sizeof(FieldState), &rc);
+    if (rc) return rc;
+    double* d_partial = (double*)scratch_device("slab.partial", sizeof(double) * fd.nblk * (NT / 32), &rc);
+    if (rc) return rc;
+    double* d_R = (double*)scratch_device("slab.R", sizeof(double), &rc);
+    if (rc) return rc;
+    FieldDesc* h_desc = (FieldDesc*)scratch_host("slab.desc", sizeof(FieldDesc), &rc);
+    if (rc) return rc;
+    MCG_CK(cudaStreamSynchronize(stream));  // the previous call may still read the staging buffer
+    *h_desc = fd;
+    MCG_CK(cudaMemcpyAsync(d_desc, h_desc, sizeof fd, cudaMemcpyHostToDevice, stream));
+    MCG_CK(cudaMemsetAsync(d_state, 0, sizeof(FieldState), stream));
+    SweepBatch bt;
+    bt.desc = d_desc;
+    bt.nf = 1;
+    bt.total_blocks = fd.nblk;
+    bt.state = d_state;
+    bt.partial = d_partial;
+    bt.ppb = NT / 32;
+    bt.R_hist = nullptr;
+    bt.hist_len = 0;
+    bt.tol = 0;
+    bt.window = 1;
+    bt.reunit_every = 0;
+    bt.omega = 1.0;
+    bt.solve32 = 0;
+    if ((rc = prepare_halfsweep<double>(NT))) return rc;
+    launch_halfsweep<double>(NT, want_R, bt, parity, fd.nblk, stream);
+    note_launches(1);
+    MCG_CK(cudaGetLastError());
+    if (want_R) {
+        k_sum_slab_partials<<<1, 256, 0, stream>>>(d_partial, fd.nblk * (NT / 32), d_R);
+        note_launches(1);
+        MCG_CK(cudaGetLastError());
+        MCG_CK(cudaMemcpyAsync(R_host, d_R, sizeof(double), cudaMemcpyDeviceToHost, stream));
+        MCG_CK(cudaStreamSynchronize(stream));
+    }
+    return 0;
+}
+
 template int time_halfsweep<float>(void*, void*, const Geom&, int, int, int, float*, cudaStream_t);
 template int time_halfsweep<double>(void*, void*, const Geom&, int, int, int, float*, cudaStream_t);
 
 template int run_fix_phase<float>(const std::vector<FieldDesc>&, FieldState*, FieldState*, double*, int, double,
                                   int, double, int, int, int, bool, cudaStream_t, bool);
+template int run_fix_phase<DoubleFloat>(const std::vector<FieldDesc>&, FieldState*, FieldState*, double*, int,
+                                        double, int, double, int, int, int, bool, cudaStream_t, bool);
 template int run_fix_phase<double>(const std::vector<FieldDesc>&, FieldState*, FieldState*, double*, int, double,
                                    int, double, int, int, int, bool, cudaStream_t, bool);
 

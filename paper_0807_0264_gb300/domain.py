@@ -217,3 +217,61 @@ def run_rank(sweeper: Sweeper, tol: float, max_sweeps: int, reunit_every: int = 
             return dict(sweeps=k, converged=True, R_hist=hist)
         R_prev = R
     return dict(sweeps=max_sweeps, converged=False, R_hist=hist)
+
+
+class DeviceSlab:
+    """Slab backend on libmcg: the rank's local arrays (FP64, even/odd layout)
+    on its GPU; half-sweeps by mcg_halfsweep_slab (exact FP64 local solve),
+    t-links read and written by index, R from the odd half-sweep's fused
+    partial (each link has exactly one odd end, so the slabs' partials add up
+    to the lattice's R)."""
+
+    def __init__(self, dom: SlabDomain, U, G, device="cuda"):
+        import torch
+
+        from . import mcg
+
+        self.dom, self.mcg, self.torch = dom, mcg, torch
+        d = dom.local_dims
+        self.U = mcg.mcg_pack_links(torch.from_numpy(U).unsqueeze(0).to(device), d)
+        self.G = mcg.mcg_pack_gauge(torch.from_numpy(G).unsqueeze(0).to(device), d)
+        self.R_owned = float(np.sum(np.abs(np.trace(dom.owned(U, G)[0], axis1=-2, axis2=-1)) ** 2))
+        nx, ny, nz, _ = d
+        i = np.arange(int(np.prod(d)))
+        self._par = ((i % nx) + (i // nx) % ny + (i // (nx * ny)) % nz + i // (nx * ny * nz)) & 1
+        self._dev = device
+
+    def halfsweep(self, parity):
+        d = self.dom
+        r = self.mcg.mcg_halfsweep_slab(self.U, self.G, d.local_dims, parity ^ d.t_offset, 1, d.L + 1,
+                                        want_R=(parity == 1))
+        if parity == 1:
+            self.R_owned = r
+
+    def _index(self, sites):
+        t = self.torch
+        return t.from_numpy(self._par[sites]).to(self._dev), t.from_numpy(sites // 2).to(self._dev)
+
+    def get_tlinks(self, sites):
+        p, s = self._index(sites)
+        v = self.U[0, 3][p, :, s, :]  # (n, 9, 2)
+        a = v.cpu().numpy()
+        return np.ascontiguousarray((a[..., 0] + 1j * a[..., 1]).reshape(-1, 3, 3))
+
+    def set_tlinks(self, sites, a):
+        p, s = self._index(sites)
+        a = np.ascontiguousarray(a).reshape(-1, 9)
+        v = np.stack([a.real, a.imag], axis=-1)
+        self.U[0, 3][p, :, s, :] = self.torch.from_numpy(v).to(self._dev)
+
+    def owned_R(self):
+        return self.R_owned
+
+    def reunitarise(self):
+        self.mcg.mcg_reunitarise(self.U, 0, self.dom.local_dims)
+        self.mcg.mcg_reunitarise(self.G, 1, self.dom.local_dims)
+
+    def local_arrays(self):
+        d = self.dom.local_dims
+        return (self.mcg.mcg_unpack_links(self.U, d)[0].cpu().numpy(),
+                self.mcg.mcg_unpack_gauge(self.G, d)[0].cpu().numpy())

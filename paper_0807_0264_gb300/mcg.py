@@ -43,7 +43,7 @@ class mcg_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_sweeps", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("reunit_every", ctypes.c_int), ("fp32_sweeps", ctypes.c_int), ("fp32_tol", ctypes.c_double),
                 ("fp32_window", ctypes.c_int), ("fp32_overrelax", ctypes.c_double),
-                ("fp64_solve32", ctypes.c_int)]
+                ("fp64_solve32", ctypes.c_int), ("fp64_df", ctypes.c_int)]
 
 
 class mcg_field(ctypes.Structure):
@@ -95,6 +95,7 @@ def _load() -> ctypes.CDLL:
                                      ctypes.POINTER(mcg_precond_result), P], I),
         "mcg_time_halfsweep": ([P, P, L, I, I, I, ctypes.POINTER(ctypes.c_float), P], I),
         "mcg_kernel_launches": ([], ctypes.c_longlong),
+        "mcg_halfsweep_slab": ([P, P, L, I, I, I, P, P], I),
         "mcg_phase_stats": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), I], I),
         "mcg_plaquette_static": ([P, P, L, P], I),
         "mcg_set_sweep_block": ([I, I], I),
@@ -124,7 +125,8 @@ EXPORTS = ("mcg_version", "mcg_last_error", "mcg_release", "mcg_pack_links", "mc
            "mcg_plaquette_static", "mcg_set_sweep_block", "mcg_get_sweep_block", "mcg_fix_batch",
            "mcg_gribov_search", "mcg_smear_backward_step", "mcg_functional_matrix_grad", "mcg_grad_R",
            "mcg_ascent_step", "mcg_vortex_remove", "mcg_wilson_loops",
-           "mcg_wilson_loops_offaxis", "mcg_anneal", "mcg_phase_stats")
+           "mcg_wilson_loops_offaxis", "mcg_anneal", "mcg_phase_stats",
+           "mcg_halfsweep_slab")
 
 
 def library() -> ctypes.CDLL:
@@ -150,11 +152,12 @@ class Params:
     fp32_window: int = 25
     fp32_overrelax: float = 1.0
     fp64_solve32: int = 0
+    fp64_df: int = 0
 
     def c(self) -> mcg_params:
         return mcg_params(self.tol, self.max_sweeps, self.check_every, self.reunit_every, self.fp32_sweeps,
                           self.fp32_tol, self.fp32_window, self.fp32_overrelax,
-                          int(self.fp64_solve32))
+                          int(self.fp64_solve32), int(self.fp64_df))
 
 
 def lattice(dims, nfields: int = 1, precision: int = F64) -> mcg_lattice:
@@ -489,6 +492,18 @@ def mcg_time_halfsweep(U: torch.Tensor, G: torch.Tensor, dims, parity: int = 1, 
                                                          int(parity), int(nreps), int(bool(flush_l2)),
                                                          ctypes.byref(ms), _stream(stream)))
     return ms.value
+
+
+def mcg_halfsweep_slab(U: torch.Tensor, G: torch.Tensor, dims, parity: int, t_lo: int, t_hi: int,
+                       want_R: bool = False, stream=None):
+    """FP64 half-sweep of the sites of `parity` with t_lo <= t < t_hi (one
+    field, in place); returns R over the updated sites' links if want_R."""
+    _need_cuda(U, G)
+    R = ctypes.c_double(0.0)
+    _check("mcg_halfsweep_slab", _lib.mcg_halfsweep_slab(_ptr(U), _ptr(G), lattice(dims, 1, F64), int(parity),
+                                                         int(t_lo), int(t_hi), ctypes.byref(R) if want_R else None,
+                                                         _stream(stream)))
+    return R.value if want_R else None
 
 
 def mcg_kernel_launches() -> int:
