@@ -67,3 +67,36 @@ def test_anneal_study_matches_oracle():
     ref = transition_tables(V, n)
     assert np.array_equal(np.nan_to_num(st["tables"]["higher_max_pct"], nan=-1),
                           np.nan_to_num(ref["higher_max_pct"], nan=-1))
+
+
+def test_precondition_levels_mixed_fp32_smearing_matches_oracle_pipeline():
+    """The entry point the benchmark times, with the benchmark's schedule
+    (FP32 smearing, over-relaxed FP32 phase, double-float FP64-class finish),
+    against the oracle's FP64 pipeline (plain relaxation, FP64 smearing) level
+    by level on 8^4: the same maxima (V_U of the smeared and of the fixed
+    field, the latter to 1e-9), the same P-vortex counts, the plaquette
+    unchanged, and every output field equal to the input transformed by its
+    output transform.  On this field each level has one dominant maximum, so
+    the over-relaxed schedule and the plain relaxation end on it."""
+    from paper_0807_0264_gb300 import mcg
+
+    dims = (8, 8, 8, 8)
+    U = synth.make_field(dims, 0.5, 7)
+    levels = [0, 2, 4]
+    Ud = mcg.mcg_pack_links(torch.from_numpy(U).unsqueeze(0).cuda(), dims)
+    p = mcg.Params(tol=1e-10, max_sweeps=20000, check_every=25, reunit_every=50, fp32_sweeps=20000, fp32_tol=5e-11,
+                   fp32_window=25, fp32_overrelax=1.85, fp64_solve32=1, fp64_df=1)
+    Uo, Go, Zo, res = mcg.mcg_precondition_levels(Ud, dims, levels, p, rho=0.1, eps=1.0, smear_precision=mcg.F32)
+    V4 = 36.0 * 4096
+    for l, n in enumerate(levels):
+        o = oracle.precondition_and_fix(dims, U, rho=0.1, eps=1.0, nsmear=n, tol=1e-10, max_sweeps=20000)
+        r = res[l]
+        assert r["status"] == 0
+        assert abs(r["V_fixed"] - o["fixed"]["R_hist"][-1] / V4) < 1e-9
+        if n:
+            assert abs(r["V_smeared"] - o["smeared"]["R_hist"][-1] / V4) < 1e-6  # FP32 smearing
+        assert r["vortices"] == o["vortices"]
+        assert abs(r["plaquette_out"] - r["plaquette_in"]) < 1e-13
+        Uf = mcg.mcg_unpack_links(Uo[l:l + 1], dims)[0].cpu().numpy()
+        Gf = mcg.mcg_unpack_gauge(Go[l:l + 1], dims)[0].cpu().numpy()
+        assert np.abs(oracle.apply_gauge(dims, U, Gf) - Uf).max() < 1e-12
