@@ -10,13 +10,13 @@ namespace mcg {
 
 // ---------------------------------------------------------------------------
 // FP32 half-sweep on the compact storage: one thread per site, the site's
-// nine matrices (forward links U_mu(x), backward links U_mu(x - mu), W(x)) in
-// registers as their rows 0 and 1 (108 floats), the three subgroup steps
-// unrolled with compile-time indices.  Row-2 entries are rebuilt where a step
-// needs them; G acting on rows (P, 2) of a forward link changes row P only in
-// the stored part (row 2 stays implied), and M G^dag acts on each row of a
-// backward link separately.  No shared memory: the loads of all nine matrices
-// are in flight at once, straight into registers.
+// nine matrices (forward links U_mu(x), backward links U_mu(x - mu), W(x)) as
+// their rows 0 and 1: the forward links in registers (48 floats), the
+// backward links and W in shared memory; the three subgroup steps unrolled
+// with compile-time indices.  Row-2 entries are rebuilt where a step needs
+// them; G acting on rows (P, 2) of a forward link changes row P only in the
+// stored part (row 2 stays implied), and M G^dag acts on each row of a
+// backward link separately.
 // ---------------------------------------------------------------------------
 
 // Makes the compiler treat the forward links as redefined here (no code
@@ -137,12 +137,12 @@ __device__ __forceinline__ void c12_left_update_pk(cplx<float>* m, const PackedS
 }
 
 // One SU(2)-subgroup step (rows/columns P < Q, R the third index) on the
-// compact forward links m[0..3] (registers) and the compact backward links
-// in shared memory.  Writes the (over-relaxed) subgroup element to `a` for the
-// update of W; returns 1 if the local solve left the Newton path.
+// compact forward links m[0..3] (registers), the compact backward links and
+// the transform W in shared memory (wst: 3 chunks per thread).  Returns 1 if
+// the local solve left the Newton path.
 template <int P, int Q, int R, int NT>
-__device__ __forceinline__ int c12_subgroup_step(cplx<float> (&m)[4][6], float4* bst, const float omega,
-                                                 float (&a)[4]) {
+__device__ __forceinline__ int c12_subgroup_step(cplx<float> (&m)[4][6], float4* bst, float4* wst,
+                                                 const float omega) {
     // A = sum Re(conj(w) w^T), b = sum Re(conj(c) w): each entry accumulated as
     // a pair (sum of x-products, sum of y-products), added at the end.  For a
     // backward link w_1..w_3 change sign, which flips b_1..b_3 and A_0j (j > 0).
@@ -196,6 +196,7 @@ __device__ __forceinline__ int c12_subgroup_step(cplx<float> (&m)[4][6], float4*
     }
     c12_opaque(m);
     asm volatile("" ::: "memory");
+    float a[4];
     int fb = 0;
     if (!kkt_newton_f32(A, b, a)) {
         const float4 r = solve_f32_fallback(A[0][0], A[0][1], A[0][2], A[0][3], A[1][1], A[1][2], A[1][3], A[2][2],
@@ -234,17 +235,32 @@ __device__ __forceinline__ int c12_subgroup_step(cplx<float> (&m)[4][6], float4*
         }
         bwd_store<NT>(bst, l, mb);
     }
+    // the transform: rows P, Q of G W (kept in shared memory between the
+    // steps, so no subgroup element stays live in registers)
+    {
+        cplx<float> w[6];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const float4 v = wst[q * NT + threadIdx.x];
+            w[2 * q] = mk(v.x, v.y);
+            w[2 * q + 1] = mk(v.z, v.w);
+        }
+        c12_left_update_pk<P, Q>(w, G);
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            wst[q * NT + threadIdx.x] = make_float4(w[2 * q].x, w[2 * q].y, w[2 * q + 1].x, w[2 * q + 1].y);
+    }
     asm volatile("" ::: "memory");
     return fb;
 }
 
 // One thread per site.  The 4 forward links are loaded straight into
 // registers (12 16-byte loads in flight); the 4 backward links and W are
-// staged into shared memory by cp.async meanwhile.  The backward links are
-// read and written there by each subgroup step; W, needed only after the
-// three steps, is updated at the end with the three subgroup elements.
-// Keeping half of the site's state out of registers removes most spills at
-// the 168-register budget of 3 blocks of 128 threads per SM.
+// staged into shared memory by cp.async meanwhile.  The backward links and W
+// are read and written there by each subgroup step.  Keeping half of the
+// site's state out of registers removes most spills at the 168-register
+// budget of 3 blocks of 128 threads per SM (W in shared memory: +3 % inside a
+// fix over keeping the three subgroup elements for a final update of W).
 template <bool ACC, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_halfsweep_c12(SweepBatch bt, int parity) {
     extern __shared__ float4 c12_smem[];  // W: 3 chunks x NT, then backward links: 12 chunks x NT
@@ -284,10 +300,9 @@ __global__ void __launch_bounds__(NT, MINB) k_halfsweep_c12(SweepBatch bt, int p
         cp_async_wait_all();
 
         const float omega = (float)bt.omega;
-        float a01[4], a02[4], a12[4];
-        fb += c12_subgroup_step<0, 1, 2, NT>(m, bst, omega, a01);
-        fb += c12_subgroup_step<0, 2, 1, NT>(m, bst, omega, a02);
-        fb += c12_subgroup_step<1, 2, 0, NT>(m, bst, omega, a12);
+        fb += c12_subgroup_step<0, 1, 2, NT>(m, bst, wstage, omega);
+        fb += c12_subgroup_step<0, 2, 1, NT>(m, bst, wstage, omega);
+        fb += c12_subgroup_step<1, 2, 0, NT>(m, bst, wstage, omega);
 
         // FP32 re-unitarisation every sweep: the 8 links in the odd half-sweep
         // (which touches every link once), W every half-sweep.  FP32 rounding
@@ -325,13 +340,6 @@ __global__ void __launch_bounds__(NT, MINB) k_halfsweep_c12(SweepBatch bt, int p
             w[2 * q] = mk(v.x, v.y);
             w[2 * q + 1] = mk(v.z, v.w);
         }
-        PackedSU2 G;
-        packed_su2(a01, G);
-        c12_left_update_pk<0, 1>(w, G);
-        packed_su2(a02, G);
-        c12_left_update_pk<0, 2>(w, G);
-        packed_su2(a12, G);
-        c12_left_update_pk<1, 2>(w, G);
         c12_reunitarise(w);
         c12_store(W + c12_gidx(g, parity, 0, s), vh, w);
     }
