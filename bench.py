@@ -666,7 +666,7 @@ def main():
     if args.profile_slice:
         # FP32 : FP64 sweeps 100 : 1 per fix, close to the full step's ratio
         sl = mcg.Params(tol=-1e300, max_sweeps=101, check_every=25, reunit_every=50, fp32_sweeps=100,
-                        fp32_tol=-1e300, fp32_window=25, fp32_overrelax=OMEGA, fp64_solve32=1)
+                        fp32_tol=-1e300, fp32_window=25, fp32_overrelax=OMEGA, fp64_solve32=1, fp64_df=1)
         mcg.mcg_set_sweep_block(mcg.F32, 128)
         mcg.mcg_set_sweep_block(mcg.F64, 128)
         torch.cuda.synchronize(dev)
