@@ -150,3 +150,36 @@ def test_anneal_schedule_is_geometric(mcg):
     assert max(r) - min(r) < 1e-14 and abs(r[0] - 0.1 ** 0.5) < 1e-14
     assert mcg.anneal_schedule(3.0, 0.1, 1) == [3.0]
     assert mcg.anneal_schedule(3.0, 0.1, 0) == []
+
+
+def test_slab_phase_stats_and_bounds_validation_without_gpu(mcg):
+    """The slab half-sweep, the phase statistics, the double-float flag and the
+    lattice bounds are checked on the host before any device work."""
+    lib = mcg.library()
+    one, two = ctypes.c_void_p(1), ctypes.c_void_p(1 << 40)
+    good = mcg.lattice((4, 4, 4, 6))
+
+    def code(rc, want, why):
+        assert rc == want, rc
+        assert why.encode() in lib.mcg_last_error(), lib.mcg_last_error()
+
+    for t_lo, t_hi in ((0, 0), (-1, 3), (2, 7), (4, 3)):
+        code(lib.mcg_halfsweep_slab(one, two, ctypes.byref(good), 0, t_lo, t_hi, None, None), 3, "t_lo")
+    code(lib.mcg_halfsweep_slab(one, two, ctypes.byref(good), 2, 0, 6, None, None), 3, "parity")
+    code(lib.mcg_halfsweep_slab(one, two, ctypes.byref(mcg.lattice((4, 4, 4, 6), 1, mcg.F32)), 0, 0, 6, None, None),
+         3, "FP64")
+    code(lib.mcg_halfsweep_slab(one, two, ctypes.byref(mcg.lattice((4, 4, 4, 6), 2)), 0, 0, 6, None, None), 3,
+         "FP64")
+    code(lib.mcg_halfsweep_slab(None, two, ctypes.byref(good), 0, 0, 6, None, None), 3, "null")
+    code(lib.mcg_phase_stats(None, None, 0), 3, "null")
+    ms = (ctypes.c_double * 2)()
+    su = (ctypes.c_longlong * 2)()
+    assert lib.mcg_phase_stats(ms, su, 1) == 0 and ms[0] >= 0 and su[1] >= 0
+    p = mcg.Params(fp64_df=2).c()
+    code(lib.mcg_fix(one, two, ctypes.byref(good), ctypes.byref(p), None, None, None, None), 3, "fp64_df")
+    # extents are bounded before the volume is formed: no int input overflows
+    for dims in ((1 << 16, 2, 2, 2), (2, 2, 2, (1 << 31) - 1 - 1)):
+        huge = mcg.lattice(dims)
+        code(lib.mcg_plaquette_static(one, one, ctypes.byref(huge), None), 2, "")
+        code(lib.mcg_plaquette(one, None, ctypes.byref(huge), None), 2, "")
+    code(lib.mcg_plaquette(one, None, ctypes.byref(mcg.lattice((4, 4, 4, 4), 1 << 21)), None), 2, "nfields")

@@ -414,6 +414,24 @@ def test_batched_fields_match_single(mcg):
         assert np.abs(out[f] - r["U"]).max() < 1e-9
 
 
+def test_heterogeneous_batch_with_mixed_df_schedule_equals_single_fields(mcg):
+    """A batch of fields of three sizes through the mixed schedule with the
+    double-float finish gives each field exactly what it gets alone (the
+    same sweeps, bit for bit): fields stop independently in both phases."""
+    dims_list = [(4, 4, 4, 6), (6, 4, 4, 4), (4, 4, 4, 4)]
+    p = mcg.Params(tol=1e-10, max_sweeps=3000, check_every=25, fp32_sweeps=3000, fp32_tol=5e-11,
+                   fp32_overrelax=1.85, fp64_df=1)
+    Us = [synth.make_field(d, 0.5, 30 + k) for k, d in enumerate(dims_list)]
+    Ub = [pack(mcg, U, d) for U, d in zip(Us, dims_list)]
+    Gb = [mcg.identity_gauge(d) for d in dims_list]
+    rb = mcg.mcg_fix_batch(Ub, Gb, dims_list, p)
+    for k, (U, d) in enumerate(zip(Us, dims_list)):
+        Us1, Gs1 = pack(mcg, U, d), mcg.identity_gauge(d)
+        r1 = mcg.mcg_fix(Us1, Gs1, d, p)
+        assert rb["sweeps"][k] == r1["sweeps"][0]
+        assert torch.equal(Ub[k], Us1) and torch.equal(Gb[k], Gs1)
+
+
 @pytest.mark.parametrize("nsmear,eps,rho", [(0, 1.0, 0.1), (4, 1.0, 0.1), (3, -0.25, 0.06)])
 def test_precondition_pipeline_parity(mcg, nsmear, eps, rho):
     dims = (4, 4, 4, 4)
