@@ -110,6 +110,8 @@ def parse():
                          "over-improved, fix phases FP32/FP64 exact/FP64 with FP32 solve, hand-off, gauge "
                          "transforms, observables, center projection, vortex removal, Wilson loops, annealing, "
                          "gradients, input check): the launches for a per-kernel ncu metrics capture")
+    ap.add_argument("--probe-peaks", action="store_true",
+                    help="measured FMA throughput of the GPU (FP64, FP32, packed FP32), one JSON line")
     ap.add_argument("--profile-kernel", choices=["f32", "f64"],
                     help="time the FP32 (or FP64) half-sweep on the field after 300 FP32 sweeps (the regime the FP32 "
                          "phase runs in), odd then even sites, 3 launches each, L2 flushed: the launches for an ncu "
@@ -659,6 +661,10 @@ def main():
         print(json.dumps({"profile_kernel": args.profile_kernel, "dims": dims, "ms_per_launch": ms}), flush=True)
         return
 
+    if args.probe_peaks:
+        print(json.dumps({"probe_peaks": mcg.mcg_probe_peaks(), "hbm_gbs": hbm_peak()[0]}), flush=True)
+        return
+
     if args.profile_kernels:
         profile_kernels(mcg, U, dims, dev)
         return
@@ -899,6 +905,7 @@ def main():
                "sample": f"{n} oracle FP64 MCG sweeps of the {dims[0]}x{dims[1]}x{dims[2]}x{dims[3]} workload field",
                "one_core": {"value": v1, "sample": f"{n1} sweeps on 1 thread"}}
 
+    pipes = mcg.mcg_probe_peaks()  # after the timed region: denominators of the ALU-bound kernels
     mixed_err = None
     if rank == 0 and world == 1 and not args.no_mixed_error:
         mixed_err = mixed_error_block(args, mcg, U, dims, args.mixed_error_levels or levels, mixed, dev)
@@ -928,7 +935,8 @@ def main():
                 "roofline": roof, "cpu_baseline": cpu, "autotune": tuned,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": canon_pinned.numel() * 16,
                         "d2h_bytes_per_step": z_host.numel(), "ms_per_step": e2e_ms / args.steps},
-                "clocks": clk.summary(), "gpu_launches": launches, "sec3d": sec3d, "mixed_error": mixed_err}
+                "clocks": clk.summary(), "gpu_launches": launches, "sec3d": sec3d, "mixed_error": mixed_err,
+                "measured_pipes": pipes}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

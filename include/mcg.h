@@ -472,6 +472,14 @@ long long mcg_kernel_launches(void);
  * site_updates_out: host, 2 long long.  reset != 0 zeroes the counters. */
 int mcg_phase_stats(double* ms_out, long long* site_updates_out, int reset);
 
+/* Arithmetic throughput of the current device (instrumentation, the
+ * denominators of ALU-bound kernels): tflops_out[0] = FP64 FMA, [1] = FP32
+ * FMA, [2] = packed FP32 FMA (two FMAs on a register pair), in TFLOP/s at
+ * 2 flop per FMA, each from ~20 ms of independent FMA chains in every thread
+ * of 8 blocks of 256 per SM, timed with CUDA events.  tflops_out: host, 3
+ * doubles.  Synchronises. */
+int mcg_probe_peaks(double* tflops_out, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

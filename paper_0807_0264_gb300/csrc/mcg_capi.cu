@@ -685,6 +685,11 @@ int mcg_precondition_fix(void* U, void* G, int8_t* Z, const mcg_lattice* lat, co
 
 long long mcg_kernel_launches(void) { return g_launches.load(); }
 
+int mcg_probe_peaks(double* tflops_out, cudaStream_t stream) {
+    if (!tflops_out) return fail(MCG_BAD_ARG, "null pointer");
+    return probe_peaks(tflops_out, stream);
+}
+
 int mcg_phase_stats(double* ms_out, long long* site_updates_out, int reset) {
     if (!ms_out || !site_updates_out) return fail(MCG_BAD_ARG, "null pointer");
     std::lock_guard<std::mutex> lk(g_phase_mu);

@@ -3,6 +3,7 @@
 // All are HBM-bound streaming kernels (one thread per site of one parity).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <mutex>
 #include <vector>
@@ -600,6 +601,85 @@ int validate_su3(const void* M, int prec, const Geom& g, int nslots, int nfields
                  "in-parity site %zu)",
                  what, h_bad[0], prec == MCG_F64 ? kSU3TolF64 : kSU3TolF32, f, slot, s);
     return fail(MCG_BAD_INPUT, buf);
+}
+
+// ---------------------------------------------------------------------------
+// Arithmetic throughput probes (instrumentation): FMA rate of the FP64 pipe,
+// the FP32 pipe and the packed FP32 instruction (two FMAs on a register pair)
+// ---------------------------------------------------------------------------
+// Each thread runs kChains independent FMA chains x <- x * m + a for `iters`
+// iterations (no dependency between chains, so the pipes, not the latency,
+// bound the rate); the result is stored only if it equals an impossible value,
+// which keeps the work without memory traffic.
+constexpr int kChains = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_probe(T* out, int iters) {
+    T x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = (T)(1.0 + 1e-3 * c + 1e-7 * threadIdx.x);
+    const T m = (T)0.999999, a = (T)1e-7;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) x[c] = fma(x[c], m, a);
+    }
+    T sum = 0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) sum += x[c];
+    if (sum == (T)-1.25) out[threadIdx.x] = sum;
+}
+
+__global__ void __launch_bounds__(256) k_fma2_probe(float* out, int iters) {
+    float2 x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = make_float2(1.f + 1e-3f * c, 1.f + 1e-7f * threadIdx.x);
+    const float2 m = make_float2(0.999999f, 0.999999f), a = make_float2(1e-7f, 1e-7f);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) x[c] = __ffma2_rn(x[c], m, a);
+    }
+    float sum = 0.f;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) sum += x[c].x + x[c].y;
+    if (sum == -1.25f) out[threadIdx.x] = sum;
+}
+
+int probe_peaks(double* tflops, cudaStream_t st) {
+    int dev = 0, nsm = 0, rc = 0;
+    MCG_CK(cudaGetDevice(&dev));
+    MCG_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    double* sink = (double*)scratch_device("probe.sink", 256 * sizeof(double), &rc);
+    if (rc) return rc;
+    const unsigned blocks = (unsigned)nsm * 8;
+    const double threads = (double)blocks * 256;
+    cudaEvent_t e0, e1;
+    MCG_CK(cudaEventCreate(&e0));
+    MCG_CK(cudaEventCreate(&e1));
+    for (int kind = 0; kind < 3; ++kind) {
+        // iterations for ~20 ms, from a short calibration launch
+        int iters = 64;
+        float ms = 0.f;
+        for (int pass = 0; pass < 2; ++pass) {
+            cudaEventRecord(e0, st);
+            if (kind == 0)
+                k_fma_probe<double><<<blocks, 256, 0, st>>>(sink, iters);
+            else if (kind == 1)
+                k_fma_probe<float><<<blocks, 256, 0, st>>>((float*)sink, iters);
+            else
+                k_fma2_probe<<<blocks, 256, 0, st>>>((float*)sink, iters);
+            cudaEventRecord(e1, st);
+            MCG_CK(cudaEventSynchronize(e1));
+            MCG_CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (pass == 0) iters = (int)std::min(1.0e7, std::max(64.0, iters * 20.0 / std::max(ms, 1e-3f)));
+        }
+        const double flop_per_iter = threads * kChains * 2.0 * (kind == 2 ? 2.0 : 1.0);
+        tflops[kind] = flop_per_iter * iters / (ms * 1e-3) / 1e12;
+    }
+    note_launches(6);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    MCG_CK(cudaGetLastError());
+    return 0;
 }
 
 int launch_identity_gauge(void* G, int prec, const Geom& g, int nfields, cudaStream_t st) {

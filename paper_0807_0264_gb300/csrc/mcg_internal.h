@@ -161,6 +161,10 @@ constexpr float kSU3TolF32 = 1e-4f;
 int validate_su3(const void* M, int prec, const Geom& g, int nslots, int nfields, const char* what,
                  cudaStream_t st, bool finite_only = false);
 
+// Arithmetic throughput probes: tflops[0..2] = FP64 FMA, FP32 FMA, packed FP32
+// FMA (TFLOP/s, 2 flop per FMA lane), measured on the current device.
+int probe_peaks(double* tflops, cudaStream_t st);
+
 // ---- field kernels (mcg_field.cu) -------------------------------------------
 int launch_convert(const void* src, int src_prec, void* dst, int dst_prec, size_t n, cudaStream_t st);
 int launch_identity_gauge(void* G, int prec, const Geom& g, int nfields, cudaStream_t st);

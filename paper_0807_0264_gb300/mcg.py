@@ -96,6 +96,7 @@ def _load() -> ctypes.CDLL:
         "mcg_time_halfsweep": ([P, P, L, I, I, I, ctypes.POINTER(ctypes.c_float), P], I),
         "mcg_kernel_launches": ([], ctypes.c_longlong),
         "mcg_halfsweep_slab": ([P, P, L, I, I, I, P, P], I),
+        "mcg_probe_peaks": ([ctypes.POINTER(ctypes.c_double), P], I),
         "mcg_phase_stats": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), I], I),
         "mcg_plaquette_static": ([P, P, L, P], I),
         "mcg_set_sweep_block": ([I, I], I),
@@ -126,7 +127,7 @@ EXPORTS = ("mcg_version", "mcg_last_error", "mcg_release", "mcg_pack_links", "mc
            "mcg_gribov_search", "mcg_smear_backward_step", "mcg_functional_matrix_grad", "mcg_grad_R",
            "mcg_ascent_step", "mcg_vortex_remove", "mcg_wilson_loops",
            "mcg_wilson_loops_offaxis", "mcg_anneal", "mcg_phase_stats",
-           "mcg_halfsweep_slab")
+           "mcg_halfsweep_slab", "mcg_probe_peaks")
 
 
 def library() -> ctypes.CDLL:
@@ -504,6 +505,13 @@ def mcg_halfsweep_slab(U: torch.Tensor, G: torch.Tensor, dims, parity: int, t_lo
                                                          int(t_lo), int(t_hi), ctypes.byref(R) if want_R else None,
                                                          _stream(stream)))
     return R.value if want_R else None
+
+
+def mcg_probe_peaks(stream=None) -> dict:
+    """Measured FMA throughput of the device (TFLOP/s): FP64, FP32, packed FP32."""
+    out = (ctypes.c_double * 3)()
+    _check("mcg_probe_peaks", _lib.mcg_probe_peaks(out, _stream(stream)))
+    return {"fp64_tflops": out[0], "fp32_tflops": out[1], "fp32x2_tflops": out[2]}
 
 
 def mcg_kernel_launches() -> int:
