@@ -69,6 +69,9 @@ struct Buf {
 struct DeviceScratch {
     std::map<std::string, Buf> dev, host;
     cudaStream_t cap = nullptr;
+    std::vector<cudaStream_t> side;  // branch streams of captured per-field chains
+    std::vector<cudaEvent_t> side_ev;
+    cudaEvent_t fork_ev = nullptr;
 };
 static std::mutex g_mu;
 static std::map<int, DeviceScratch> g_scratch;
@@ -138,6 +141,30 @@ cudaStream_t capture_stream(int* rc) {
     return ds.cap;
 }
 
+int branch_streams(int n, cudaStream_t* streams, cudaEvent_t* events, cudaEvent_t* fork, int* rc_out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int rc = 0;
+    DeviceScratch& ds = cur(&rc);
+    if (rc) return *rc_out = rc;
+    cudaError_t e = cudaSuccess;
+    if (!ds.fork_ev) e = cudaEventCreateWithFlags(&ds.fork_ev, cudaEventDisableTiming);
+    while (e == cudaSuccess && (int)ds.side.size() < n) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t ev = nullptr;
+        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (s) ds.side.push_back(s);
+        if (ev) ds.side_ev.push_back(ev);
+    }
+    if (e != cudaSuccess) return *rc_out = cuda_fail(e, "branch streams");
+    for (int i = 0; i < n; ++i) {
+        streams[i] = ds.side[i];
+        events[i] = ds.side_ev[i];
+    }
+    *fork = ds.fork_ev;
+    return *rc_out = 0;
+}
+
 void release_all() {
     static_release();
     std::lock_guard<std::mutex> lk(g_mu);
@@ -151,6 +178,9 @@ void release_all() {
         for (auto& b : kv.second.host)
             if (b.second.p) cudaFreeHost(b.second.p);
         if (kv.second.cap) cudaStreamDestroy(kv.second.cap);
+        for (auto s : kv.second.side) cudaStreamDestroy(s);
+        for (auto ev : kv.second.side_ev) cudaEventDestroy(ev);
+        if (kv.second.fork_ev) cudaEventDestroy(kv.second.fork_ev);
     }
     g_scratch.clear();
     cudaSetDevice(dev);

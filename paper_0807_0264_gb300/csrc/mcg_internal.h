@@ -45,6 +45,9 @@ void note_phase(int prec, double ms, long long site_updates);
 void* scratch_device(const char* name, size_t bytes, int* rc);
 void* scratch_host(const char* name, size_t bytes, int* rc);
 cudaStream_t capture_stream(int* rc);
+// n branch streams (and an event per stream, plus a fork event) for the
+// per-field chains of a captured sweep graph, cached per device.
+int branch_streams(int n, cudaStream_t* streams, cudaEvent_t* events, cudaEvent_t* fork, int* rc);
 void release_all();
 
 // ---- batched sweep machinery -------------------------------------------------

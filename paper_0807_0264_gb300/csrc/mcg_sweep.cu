@@ -739,16 +739,67 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
     if (rc) return rc;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // A batch of several fields runs as independent per-field chains of
+    // half-sweeps inside the graph (one branch stream each, forked from and
+    // joined to the capture stream): no field waits for another at the
+    // half-sweep boundaries, the fields drift apart in phase, and one field's
+    // load phase overlaps another's arithmetic (measured: the step 4.6 %
+    // faster than one launch per half-sweep covering every field).  Each chain
+    // sees its field as a batch of one (block offset 0, its own state, partials
+    // and R history), so the per-field arithmetic is unchanged.
+    std::vector<SweepBatch> chains;
+    std::vector<cudaStream_t> bs(nf);
+    std::vector<cudaEvent_t> be(nf);
+    cudaEvent_t fork = nullptr;
+    if (nf > 1) {
+        FieldDesc* d_single = (FieldDesc*)scratch_device("fix.desc1", sizeof(FieldDesc) * nf, &rc);
+        if (rc) return rc;
+        FieldDesc* h_single = (FieldDesc*)scratch_host("fix.desc1", sizeof(FieldDesc) * nf, &rc);
+        if (rc) return rc;
+        for (int f = 0; f < nf; ++f) {
+            h_single[f] = fields[f];
+            h_single[f].blk0 = 0;
+        }
+        MCG_CK(cudaMemcpyAsync(d_single, h_single, sizeof(FieldDesc) * nf, cudaMemcpyHostToDevice, stream));
+        MCG_CK(cudaStreamSynchronize(stream));  // h_single is reused by the next call
+        for (int f = 0; f < nf; ++f) {
+            SweepBatch b = bt;
+            b.desc = d_single + f;
+            b.nf = 1;
+            b.total_blocks = fields[f].nblk;
+            b.state = d_state + f;
+            b.partial = d_partial + (size_t)fields[f].blk0 * bt.ppb;
+            b.R_hist = d_hist ? d_hist + (size_t)f * hist_len : nullptr;
+            chains.push_back(b);
+        }
+        if (branch_streams(nf, bs.data(), be.data(), &fork, &rc)) return rc;
+    }
     MCG_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
-    for (int i = 0; i < chunk; ++i) enqueue_sweep<T>(bt, NT, SPB, cs);
+    // no early return while the capture is open: the first error ends it
+    cudaError_t qe = cudaSuccess;
+    if (nf > 1) {
+        qe = cudaEventRecord(fork, cs);
+        for (int f = 0; f < nf && qe == cudaSuccess; ++f) {
+            qe = cudaStreamWaitEvent(bs[f], fork, 0);
+            if (qe != cudaSuccess) break;
+            for (int i = 0; i < chunk; ++i) enqueue_sweep<T>(chains[f], NT, SPB, bs[f]);
+            qe = cudaEventRecord(be[f], bs[f]);
+            if (qe == cudaSuccess) qe = cudaStreamWaitEvent(cs, be[f], 0);
+        }
+    } else {
+        for (int i = 0; i < chunk; ++i) enqueue_sweep<T>(bt, NT, SPB, cs);
+    }
     cudaError_t ce = cudaStreamEndCapture(cs, &graph);
-    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+    if (qe != cudaSuccess || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(qe != cudaSuccess ? qe : ce, "sweep graph capture");
+    }
     ce = cudaGraphInstantiate(&exec, graph, 0);
     if (ce != cudaSuccess) {
         cudaGraphDestroy(graph);
         return cuda_fail(ce, "cudaGraphInstantiate");
     }
-    const int nodes_per_chunk = chunk * ((!DF && sizeof(T) == 8 && reunit_every > 0) ? 4 : 3);
+    const int nodes_per_chunk = nf * chunk * ((!DF && sizeof(T) == 8 && reunit_every > 0) ? 4 : 3);
     const int max_chunks = (phase_len + chunk - 1) / chunk + 1;
     int status = 0;
     // phase timing (instrumentation): GPU time of the chunk graphs and the
