@@ -110,6 +110,9 @@ def parse():
                          "over-improved, fix phases FP32/FP64 exact/FP64 with FP32 solve, hand-off, gauge "
                          "transforms, observables, center projection, vortex removal, Wilson loops, annealing, "
                          "gradients, input check): the launches for a per-kernel ncu metrics capture")
+    ap.add_argument("--slabs", action="store_true",
+                    help="time the t-slab decomposition of the FP64 relaxation (slabs in lockstep on this GPU, "
+                         "faces exchanged on the device) against the single-domain FP64 sweep")
     ap.add_argument("--probe-peaks", action="store_true",
                     help="measured FMA throughput of the GPU (FP64, FP32, packed FP32), one JSON line")
     ap.add_argument("--profile-kernel", choices=["f32", "f64"],
@@ -402,6 +405,55 @@ def anneal_flop_per_site(nhit: int) -> int:
     return 3 * (512 + 756 + 56 + 110 * nhit)
 
 
+def run_slabs(mcg, dims, U_host, dev, sweeps=20):
+    """The domain decomposition along t (paper_0807_0264_gb300.domain) on one
+    GPU: W slabs of the workload field driven in lockstep from the host, each
+    half-sweep one mcg_halfsweep_slab launch per slab and one face copy each
+    way per boundary (mcg_slab_face, device to device).  Times `sweeps` exact
+    FP64 sweeps after 2 warm-up sweeps, against the single-domain FP64 sweep
+    (mcg_fix, same arithmetic), and checks the links are the same bits."""
+    import time
+
+    import numpy as np
+    import torch
+
+    from paper_0807_0264_gb300 import domain, synth
+
+    NEVER = -1e300
+    G_host = synth.identity_gauge(dims)
+    Ud = mcg.mcg_pack_links(torch.from_numpy(U_host).unsqueeze(0).to(dev), dims)
+    Gd = mcg.identity_gauge(dims, 1, mcg.F64, dev)
+    mcg.mcg_fix(Ud, Gd, dims, mcg.Params(tol=NEVER, max_sweeps=2, check_every=2, reunit_every=0))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    mcg.mcg_fix(Ud, Gd, dims, mcg.Params(tol=NEVER, max_sweeps=sweeps, check_every=sweeps, reunit_every=0))
+    torch.cuda.synchronize(dev)
+    single_ms = (time.perf_counter() - t0) * 1e3 / sweeps
+    U_single = mcg.mcg_unpack_links(Ud, dims)[0].cpu().numpy()
+    del Ud, Gd
+    face_bytes = 9 * dims[0] * dims[1] * dims[2] // 2 * 16
+    out = {"slabs": {"dims": list(dims), "sweeps": sweeps, "single_domain_ms_per_sweep": single_ms,
+                     "face_bytes": face_bytes, "runs": []}}
+    for W in (1, 2, 4):
+        doms = [domain.SlabDomain(dims, r, W) for r in range(W)]
+        bks = [domain.DeviceSlab(d, *d.scatter(U_host, G_host), device=dev) for d in doms]
+        sw = [domain.Sweeper(d, b) for d, b in zip(doms, bks)]
+        domain.run_ranks_lockstep(sw, NEVER, 2, reunit_every=0)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        domain.run_ranks_lockstep(sw, NEVER, sweeps, reunit_every=0)
+        torch.cuda.synchronize(dev)
+        ms = (time.perf_counter() - t0) * 1e3 / sweeps
+        Uo = np.concatenate([d.owned(*b.local_arrays())[0] for d, b in zip(doms, bks)])
+        out["slabs"]["runs"].append({"W": W, "slab_layers": dims[3] // W, "ms_per_sweep": ms,
+                                     "overhead": ms / single_ms - 1.0,
+                                     "face_copies_per_sweep": 4 * W, "same_bits_as_single_domain":
+                                     bool(np.array_equal(Uo, U_single))})
+        del bks, sw
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
 def run_anneal(args, mcg, dev, rank):
     import torch
 
@@ -667,6 +719,10 @@ def main():
 
     if args.profile_kernels:
         profile_kernels(mcg, U, dims, dev)
+        return
+
+    if args.slabs:
+        run_slabs(mcg, dims, U_host, dev)
         return
 
     if args.profile_slice:

@@ -363,8 +363,31 @@ int mcg_halfsweep_slab(void* U, void* G, const mcg_lattice* lat, int parity, int
                        cudaStream_t stream);
 
 /*
+ * The halo face of a t-slab (domain decomposition of the Sec. II.A
+ * relaxation): the forward t-links U_t(x) (mu = 3, all nine entries) of the
+ * sites of one t-layer and one checkerboard parity, copied between a field
+ * and a contiguous buffer on the device.  A half-sweep of parity P reads the
+ * t-link of a first-layer site's backward neighbour, which lies on the last
+ * layer of the slab below and has parity 1 - P: that face is the one
+ * message each way per half-sweep.
+ * U: one field (lat->nfields must be 1), MCG_F64 or MCG_F32, device.
+ * t: the layer, 0 <= t < N_t; parity: 0 or 1, the parity of the sites in
+ * U's own checkerboard.  buf: device, 9 * (N_x N_y N_z / 2) elements of U's
+ * type (complex, 16 or 8 bytes), entry-major: buf[e * n + i] is entry
+ * e = 3*row + col of the i-th site of the face, sites in (x, y, z)
+ * lexicographic order (x fastest) -- the same order on both sides of a slab
+ * boundary, so a face read from layer L of one slab is written unchanged into
+ * layer 0 of the next.  to_field: 0 copies U -> buf, 1 copies buf -> U (only
+ * the face's t-links change).  buf must not overlap U.  Asynchronous on
+ * `stream` (one pitched device-to-device copy).
+ * Returns MCG_OK, MCG_BAD_DIMS, MCG_BAD_ARG or MCG_CUDA_ERROR.
+ */
+int mcg_slab_face(void* U, void* buf, const mcg_lattice* lat, int t, int parity, int to_field, cudaStream_t stream);
+
+/*
  * MCG relaxation (as mcg_fix) of a batch of fields of any sizes, all of one
- * precision: one launch per half-sweep covers every field; a field stops
+ * precision: each field's half-sweeps run as their own chain of launches
+ * (the chains concurrent inside one graph per chunk of sweeps); a field stops
  * (its blocks exit at entry) once it has converged.  fields: host array of
  * nfields entries.  R_out / sweeps_out: host, nfields entries (may be NULL).
  * Returns MCG_OK when every field converged, else MCG_NOT_CONVERGED.

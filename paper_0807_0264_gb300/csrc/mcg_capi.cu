@@ -777,6 +777,28 @@ int mcg_halfsweep_slab(void* U, void* G, const mcg_lattice* lat, int parity, int
     return run_halfsweep_slab(U, G, g, parity, t_lo, t_hi, R_out != nullptr, R_out, stream);
 }
 
+int mcg_slab_face(void* U, void* buf, const mcg_lattice* lat, int t, int parity, int to_field, cudaStream_t stream) {
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if (!U || !buf) return fail(MCG_BAD_ARG, "null pointer");
+    if (lat->nfields != 1) return fail(MCG_BAD_ARG, "one field");
+    if (parity != 0 && parity != 1) return fail(MCG_BAD_ARG, "parity must be 0 or 1");
+    if (to_field != 0 && to_field != 1) return fail(MCG_BAD_ARG, "to_field must be 0 or 1");
+    if (t < 0 || t >= g.n[3]) return fail(MCG_BAD_ARG, "need 0 <= t < N_t");
+    const size_t eb = elem_bytes(lat->precision);
+    // sites of one parity on one layer: a contiguous in-parity range
+    // [t * n, (t + 1) * n), n = Nx Ny Nz / 2, in every entry array of U_t
+    const size_t n = (size_t)g.n[0] * g.n[1] * g.n[2] / 2;
+    if (overlap(U, eb * link_elems(g), buf, eb * 9 * n)) return fail(MCG_BAD_ARG, "buf overlaps U");
+    char* face = static_cast<char*>(U) + eb * (((size_t)(3 * 2 + parity) * 9) * g.vh + (size_t)t * n);
+    const size_t field_pitch = eb * (size_t)g.vh, width = eb * n;
+    cudaError_t e = to_field ? cudaMemcpy2DAsync(face, field_pitch, buf, width, width, 9, cudaMemcpyDeviceToDevice, stream)
+                             : cudaMemcpy2DAsync(buf, width, face, field_pitch, width, 9, cudaMemcpyDeviceToDevice, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mcg_slab_face copy");
+    return MCG_OK;
+}
+
 int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_out, const mcg_lattice* lat,
                             const mcg_params* params, double rho, double eps, const int* nsmear, int nlevels,
                             int smear_precision, mcg_precond_result* results, cudaStream_t stream) {

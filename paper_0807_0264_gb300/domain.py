@@ -28,8 +28,8 @@ one all-reduce per sweep; every rank then takes the same stop decision
 and Omega.
 
 The driver is independent of where the slab lives: a backend supplies the
-slab half-sweep, reads and writes of given t-links, the owned R and the
-re-unitarisation; `run_ranks_lockstep` drives all ranks from one process
+slab half-sweep, reads and writes of one face (the t-links of one parity on
+one layer), the owned R and the re-unitarisation; `run_ranks_lockstep` drives all ranks from one process
 (phase by phase, no rank ever waits on another), `run_rank` drives one rank
 of a torch.distributed group.
 """
@@ -83,6 +83,16 @@ class SlabDomain:
         same (x, y, z) order as rank r - 1's last_layer_sites(parity)."""
         return self.layer_sites(0)[self.global_parity_of_layer(0) == parity]
 
+    def face_sites(self, t_local: int, parity: int) -> np.ndarray:
+        """Sites of local layer t_local with global parity `parity`, in
+        (x, y, z) order: one face of the exchange."""
+        return self.layer_sites(t_local)[self.global_parity_of_layer(t_local) == parity]
+
+    def local_parity(self, parity: int) -> int:
+        """Parity, in the local array's own checkerboard, of the sites of
+        global parity `parity` (the same on every layer)."""
+        return parity ^ self.t_offset
+
     def owned_sites(self) -> np.ndarray:
         return np.arange(self.layer, (self.L + 1) * self.layer)
 
@@ -111,11 +121,13 @@ class SlabDomain:
 
 class Sweeper:
     """The decomposed relaxation for one rank, phase by phase.  `backend`:
-      halfsweep(parity)            update the owned sites of global parity
-      get_tlinks(sites) -> array   t-links (mu = 3) of local sites
-      set_tlinks(sites, array)
-      owned_R() -> float           sum |tr U|^2 over the owned links
-      reunitarise()                owned links and Omega
+      halfsweep(parity)              update the owned sites of global parity
+      get_face(t_local, parity)      t-links (mu = 3) of the sites of global
+                                     parity `parity` on a local layer, in
+                                     (x, y, z) order (any array type)
+      set_face(t_local, parity, d)   write such a face back
+      owned_R() -> float             sum |tr U|^2 over the owned links
+      reunitarise()                  owned links and Omega
     """
 
     def __init__(self, dom: SlabDomain, backend):
@@ -123,19 +135,19 @@ class Sweeper:
         self.b = backend
 
     def send_up(self, P):
-        return self.b.get_tlinks(self.dom.last_layer_sites(1 - P))
+        return self.b.get_face(self.dom.L, 1 - P)
 
     def recv_from_below(self, P, data):
-        self.b.set_tlinks(self.dom.ghost_sites(1 - P), data)
+        self.b.set_face(0, 1 - P, data)
 
     def compute(self, P):
         self.b.halfsweep(P)
 
     def send_down(self, P):
-        return self.b.get_tlinks(self.dom.ghost_sites(1 - P))
+        return self.b.get_face(0, 1 - P)
 
     def recv_from_above(self, P, data):
-        self.b.set_tlinks(self.dom.last_layer_sites(1 - P), data)
+        self.b.set_face(self.dom.L, 1 - P, data)
 
 
 def _stop(R, R_prev, norm, tol):
@@ -185,8 +197,15 @@ def run_rank(sweeper: Sweeper, tol: float, max_sweeps: int, reunit_every: int = 
     up_rank, down_rank = (r + 1) % W, (r - 1) % W
     norm = 1.0 / (36.0 * float(np.prod(dom.dims)))
 
-    def sendrecv(arr, to, frm):
-        t_send = torch.from_numpy(np.ascontiguousarray(arr).view(np.float64))
+    # faces travel as they are when the group's backend can send them (host
+    # tensors; device tensors under NCCL), else through host memory
+    device_ok = W > 1 and dist.get_backend(group) == "nccl"
+
+    def sendrecv(x, to, frm):
+        host = isinstance(x, np.ndarray)
+        t_send = torch.from_numpy(np.ascontiguousarray(x).view(np.float64)) if host else x.contiguous()
+        if not host and t_send.is_cuda and not device_ok:
+            t_send = t_send.cpu()
         t_recv = torch.empty_like(t_send)
         if W == 1:
             t_recv.copy_(t_send)
@@ -194,7 +213,7 @@ def run_rank(sweeper: Sweeper, tol: float, max_sweeps: int, reunit_every: int = 
             req = dist.isend(t_send, to, group=group)
             dist.recv(t_recv, frm, group=group)
             req.wait()
-        return t_recv.numpy().view(np.complex128).reshape(arr.shape)
+        return t_recv.numpy().view(np.complex128).reshape(x.shape) if host else t_recv
 
     def allreduce(x):
         t = torch.tensor([x], dtype=torch.float64)
@@ -222,7 +241,9 @@ def run_rank(sweeper: Sweeper, tol: float, max_sweeps: int, reunit_every: int = 
 class DeviceSlab:
     """Slab backend on libmcg: the rank's local arrays (FP64, even/odd layout)
     on its GPU; half-sweeps by mcg_halfsweep_slab (exact FP64 local solve),
-    t-links read and written by index, R from the odd half-sweep's fused
+    faces read and written on the device by mcg_slab_face (a face is a
+    (9, Nx Ny Nz / 2, 2) float64 tensor on the slab's device, ready for a
+    device-to-device copy or an NCCL send), R from the odd half-sweep's fused
     partial (each link has exactly one odd end, so the slabs' partials add up
     to the lattice's R)."""
 
@@ -236,33 +257,24 @@ class DeviceSlab:
         self.U = mcg.mcg_pack_links(torch.from_numpy(U).unsqueeze(0).to(device), d)
         self.G = mcg.mcg_pack_gauge(torch.from_numpy(G).unsqueeze(0).to(device), d)
         self.R_owned = float(np.sum(np.abs(np.trace(dom.owned(U, G)[0], axis1=-2, axis2=-1)) ** 2))
-        nx, ny, nz, _ = d
-        i = np.arange(int(np.prod(d)))
-        self._par = ((i % nx) + (i // nx) % ny + (i // (nx * ny)) % nz + i // (nx * ny * nz)) & 1
-        self._dev = device
+        self._dev = self.U.device
 
     def halfsweep(self, parity):
         d = self.dom
-        r = self.mcg.mcg_halfsweep_slab(self.U, self.G, d.local_dims, parity ^ d.t_offset, 1, d.L + 1,
+        r = self.mcg.mcg_halfsweep_slab(self.U, self.G, d.local_dims, d.local_parity(parity), 1, d.L + 1,
                                         want_R=(parity == 1))
         if parity == 1:
             self.R_owned = r
 
-    def _index(self, sites):
-        t = self.torch
-        return t.from_numpy(self._par[sites]).to(self._dev), t.from_numpy(sites // 2).to(self._dev)
+    def get_face(self, t_local, parity):
+        d = self.dom
+        buf = self.mcg.empty_face(d.local_dims, self.mcg.F64, self._dev)
+        return self.mcg.mcg_slab_face(self.U, buf, d.local_dims, t_local, d.local_parity(parity), False)
 
-    def get_tlinks(self, sites):
-        p, s = self._index(sites)
-        v = self.U[0, 3][p, :, s, :]  # (n, 9, 2)
-        a = v.cpu().numpy()
-        return np.ascontiguousarray((a[..., 0] + 1j * a[..., 1]).reshape(-1, 3, 3))
-
-    def set_tlinks(self, sites, a):
-        p, s = self._index(sites)
-        a = np.ascontiguousarray(a).reshape(-1, 9)
-        v = np.stack([a.real, a.imag], axis=-1)
-        self.U[0, 3][p, :, s, :] = self.torch.from_numpy(v).to(self._dev)
+    def set_face(self, t_local, parity, data):
+        d = self.dom
+        buf = data.to(self._dev).contiguous()
+        self.mcg.mcg_slab_face(self.U, buf, d.local_dims, t_local, d.local_parity(parity), True)
 
     def owned_R(self):
         return self.R_owned

@@ -96,6 +96,7 @@ def _load() -> ctypes.CDLL:
         "mcg_time_halfsweep": ([P, P, L, I, I, I, ctypes.POINTER(ctypes.c_float), P], I),
         "mcg_kernel_launches": ([], ctypes.c_longlong),
         "mcg_halfsweep_slab": ([P, P, L, I, I, I, P, P], I),
+        "mcg_slab_face": ([P, P, L, I, I, I, P], I),
         "mcg_probe_peaks": ([ctypes.POINTER(ctypes.c_double), P], I),
         "mcg_phase_stats": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), I], I),
         "mcg_plaquette_static": ([P, P, L, P], I),
@@ -127,7 +128,7 @@ EXPORTS = ("mcg_version", "mcg_last_error", "mcg_release", "mcg_pack_links", "mc
            "mcg_gribov_search", "mcg_smear_backward_step", "mcg_functional_matrix_grad", "mcg_grad_R",
            "mcg_ascent_step", "mcg_vortex_remove", "mcg_wilson_loops",
            "mcg_wilson_loops_offaxis", "mcg_anneal", "mcg_phase_stats",
-           "mcg_halfsweep_slab", "mcg_probe_peaks")
+           "mcg_halfsweep_slab", "mcg_slab_face", "mcg_probe_peaks")
 
 
 def library() -> ctypes.CDLL:
@@ -202,6 +203,12 @@ def empty_links(dims, nfields=1, precision=F64, device="cuda"):
 
 def empty_gauge(dims, nfields=1, precision=F64, device="cuda"):
     return torch.empty((nfields, 2, 9, vh_of(dims), 2), dtype=_real_dtype(precision), device=device)
+
+
+def empty_face(dims, precision=F64, device="cuda"):
+    """Buffer of one slab face (mcg_slab_face): (9, Nx*Ny*Nz/2, 2) reals."""
+    return torch.empty((9, int(dims[0]) * int(dims[1]) * int(dims[2]) // 2, 2), dtype=_real_dtype(precision),
+                       device=device)
 
 
 def precision_of(t: torch.Tensor) -> int:
@@ -505,6 +512,23 @@ def mcg_halfsweep_slab(U: torch.Tensor, G: torch.Tensor, dims, parity: int, t_lo
                                                          int(t_lo), int(t_hi), ctypes.byref(R) if want_R else None,
                                                          _stream(stream)))
     return R.value if want_R else None
+
+
+def mcg_slab_face(U: torch.Tensor, buf: torch.Tensor, dims, t: int, parity: int, to_field: bool,
+                  precision: int = None, stream=None) -> torch.Tensor:
+    """Copy the t-links of the parity-`parity` sites of layer t between the
+    field U and the device buffer buf (9 * Nx*Ny*Nz/2 complex entries,
+    entry-major, sites in (x, y, z) order); to_field=False reads the face
+    into buf, True writes buf into U.  Returns buf."""
+    _need_cuda(U, buf)
+    prec = precision_of(U) if precision is None else precision
+    n = dims[0] * dims[1] * dims[2] // 2
+    need = 9 * n * (16 if prec == F64 else 8)
+    if not buf.is_contiguous() or buf.numel() * buf.element_size() < need:
+        raise ValueError(f"face buffer must be contiguous and hold {need} bytes")
+    _check("mcg_slab_face", _lib.mcg_slab_face(_ptr(U), _ptr(buf), lattice(dims, 1, prec), int(t), int(parity),
+                                               int(bool(to_field)), _stream(stream)))
+    return buf
 
 
 def mcg_probe_peaks(stream=None) -> dict:

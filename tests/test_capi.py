@@ -183,3 +183,27 @@ def test_slab_phase_stats_and_bounds_validation_without_gpu(mcg):
         code(lib.mcg_plaquette_static(one, one, ctypes.byref(huge), None), 2, "")
         code(lib.mcg_plaquette(one, None, ctypes.byref(huge), None), 2, "")
     code(lib.mcg_plaquette(one, None, ctypes.byref(mcg.lattice((4, 4, 4, 4), 1 << 21)), None), 2, "nfields")
+
+
+def test_slab_face_validation_without_gpu(mcg):
+    """The slab face copy checks layer, parity, direction, field count,
+    pointers and overlap on the host before any device work."""
+    lib = mcg.library()
+    U, buf = ctypes.c_void_p(1 << 20), ctypes.c_void_p(1 << 40)
+    good = mcg.lattice((4, 4, 4, 6))
+
+    def code(rc, want, why):
+        assert rc == want, rc
+        assert why.encode() in lib.mcg_last_error(), lib.mcg_last_error()
+
+    for t in (-1, 6):
+        code(lib.mcg_slab_face(U, buf, ctypes.byref(good), t, 0, 0, None), 3, "N_t")
+    code(lib.mcg_slab_face(U, buf, ctypes.byref(good), 0, 2, 0, None), 3, "parity")
+    code(lib.mcg_slab_face(U, buf, ctypes.byref(good), 0, 0, 2, None), 3, "to_field")
+    code(lib.mcg_slab_face(U, buf, ctypes.byref(mcg.lattice((4, 4, 4, 6), 2)), 0, 0, 0, None), 3, "one field")
+    code(lib.mcg_slab_face(None, buf, ctypes.byref(good), 0, 0, 0, None), 3, "null")
+    code(lib.mcg_slab_face(U, None, ctypes.byref(good), 0, 0, 0, None), 3, "null")
+    # a buffer inside the field (FP64 links of 4^3 x 6: 72 x 192 x 16 bytes)
+    inside = ctypes.c_void_p((1 << 20) + 4096)
+    code(lib.mcg_slab_face(U, inside, ctypes.byref(good), 0, 0, 0, None), 3, "overlaps")
+    code(lib.mcg_slab_face(U, buf, ctypes.byref(mcg.lattice((4, 3, 4, 6))), 0, 0, 0, None), 2, "")

@@ -33,11 +33,11 @@ class OracleSlab:
         d = self.dom
         oracle.halfsweep_slab(d.local_dims, self.U, self.G, parity, 1, d.L + 1, d.t_offset, self.omega)
 
-    def get_tlinks(self, sites):
-        return self.U[sites, 3].copy()
+    def get_face(self, t_local, parity):
+        return self.U[self.dom.face_sites(t_local, parity), 3].copy()
 
-    def set_tlinks(self, sites, a):
-        self.U[sites, 3] = a
+    def set_face(self, t_local, parity, a):
+        self.U[self.dom.face_sites(t_local, parity), 3] = a
 
     def owned_R(self):
         Uo, _ = self.dom.owned(self.U, self.G)
@@ -60,6 +60,14 @@ def test_partition_geometry():
     for P in (0, 1):
         g, t = dom.ghost_sites(P), dom.last_layer_sites(P)
         assert len(g) == len(t) == 4 * 6 * 2 // 2
+        assert np.array_equal(dom.face_sites(0, P), g) and np.array_equal(dom.face_sites(dom.L, P), t)
+        # a face's sites are one contiguous in-parity range of the local array,
+        # of local parity P ^ t_offset, in (x, y, z) order on both layers
+        for layer in (0, dom.L):
+            f = dom.face_sites(layer, P)
+            x, y, z, tl = f % 4, (f // 4) % 6, (f // 24) % 2, f // 48
+            assert np.all((x + y + z + tl) % 2 == dom.local_parity(P))
+            assert np.array_equal(f // 2, layer * 24 + np.arange(24))
     # the ghost layer is global t0 - 1 = 3 (odd): parity of (x, y, z) flipped
     assert dom.global_parity_of_layer(0)[0] == 1 and dom.global_parity_of_layer(1)[0] == 0
     with pytest.raises(ValueError):
