@@ -937,6 +937,7 @@ def main():
     # end to end through the public API: host canonical field in, results out
     barrier()
     z_host = torch.empty((nl, V, 4), dtype=torch.int8).pin_memory()
+    g_host = torch.empty(G_out.shape, dtype=G_out.dtype).pin_memory()  # each level's transform Omega
     h0 = torch.cuda.Event(enable_timing=True)
     h1 = torch.cuda.Event(enable_timing=True)
     h0.record(stream)
@@ -947,6 +948,7 @@ def main():
         r2 = mcg.mcg_precondition_levels(Ue, dims, levels, mixed, rho=args.rho, eps=args.eps,
                                          smear_precision=mcg.F32, U_out=U_out, G_out=G_out, Z_out=Z_out)[3]
         z_host.copy_(mcg.mcg_unpack_center(Z_out, dims), non_blocking=True)
+        g_host.copy_(G_out, non_blocking=True)
         e2e_updates += sum(r["sweeps_smeared"] + r["sweeps_fixed"] for r in r2) * V
     h1.record(stream)
     barrier()
@@ -990,7 +992,8 @@ def main():
                                        "converged": r["status"] == 0} for n, r in zip(levels, mixed_res)]},
                 "roofline": roof, "cpu_baseline": cpu, "autotune": tuned,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": canon_pinned.numel() * 16,
-                        "d2h_bytes_per_step": z_host.numel(), "ms_per_step": e2e_ms / args.steps},
+                        "d2h_bytes_per_step": z_host.numel() + g_host.numel() * g_host.element_size(),
+                        "d2h": "center sectors and gauge transform of every level", "ms_per_step": e2e_ms / args.steps},
                 "clocks": clk.summary(), "gpu_launches": launches, "sec3d": sec3d, "mixed_error": mixed_err,
                 "measured_pipes": pipes}
         print(json.dumps(line), flush=True)

@@ -332,10 +332,12 @@ int mcg_precondition_fix(void* U, void* G, int8_t* Z, const mcg_lattice* lat, co
  * preconditioning conducted independently from the same original field.
  * One smearing chain of U produces the smeared field at every requested level
  * (nsmear: host array, nlevels entries, non-decreasing; 0 = no
- * preconditioning); the smeared fields are MCG-fixed as one batch; each
- * level's transform (re-unitarised) is applied to a copy of U; the
- * preconditioned copies are MCG-fixed as one batch; then center projection,
- * P-vortex counts and plaquettes per level.
+ * preconditioning); the smeared fields and the copies of U for the levels
+ * without smearing are MCG-fixed as one batch; each smeared level's
+ * transform (re-unitarised) is applied to a copy of U; those preconditioned
+ * copies are MCG-fixed as a second batch; then center projection, P-vortex
+ * counts and plaquettes per level.  Each field's result does not depend on
+ * the batch it is fixed in.
  * U: one input field (lat->nfields must be 1), not modified.
  * U_out: nlevels fields (device) receiving the fixed fields; G_out: nlevels
  * transforms (U_out[l] = U^G_out[l]); Z_out (device int8, nlevels fields, may

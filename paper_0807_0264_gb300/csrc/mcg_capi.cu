@@ -832,14 +832,16 @@ int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_o
     for (int l = 0; l < nlevels; ++l)
         MCG_CK(cudaMemcpyAsync((char*)U_out + eb * le * l, U, eb * le, cudaMemcpyDeviceToDevice, stream));
     if ((rc = launch_identity_gauge(G_out, prec, g, nlevels, stream))) return rc;
+    void* Sp = nullptr;  // the smeared fields, then their transforms
+    void* W = nullptr;
     if (ns > 0) {
         void* cur = scratch_device("lev.cur", seb * le, &rc);
         if (rc) return rc;
         void* tmp = scratch_device("lev.tmp", seb * le, &rc);
         if (rc) return rc;
-        void* Sp = scratch_device("lev.Sp", eb * le * ns, &rc);
+        Sp = scratch_device("lev.Sp", eb * le * ns, &rc);
         if (rc) return rc;
-        void* W = scratch_device("lev.W", eb * ge * ns, &rc);
+        W = scratch_device("lev.W", eb * ge * ns, &rc);
         if (rc) return rc;
         if ((rc = launch_convert(U, prec, cur, smear_precision, le, stream))) return rc;
         int done_steps = 0;
@@ -854,22 +856,58 @@ int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_o
         }
         if (smear_precision != prec && (rc = launch_reunitarise(Sp, 0, prec, g, ns, stream))) return rc;
         if ((rc = launch_identity_gauge(W, prec, g, ns, stream))) return rc;
-        mcg_lattice lb = *lat;
-        lb.nfields = ns;
-        rc = fix_impl(Sp, W, &lb, g, params, Rs.data(), sw_s.data(), sw32_s.data(), nullptr, stream);
+    }
+    // First batch: the smeared fields and the unsmeared levels (whose fix
+    // needs no smearing), so the long fixes run side by side; second batch:
+    // the preconditioned copies of the smeared levels.  Per-field arithmetic
+    // does not depend on the batch.
+    std::vector<FieldSpec> b1, b2;
+    std::vector<int> plain_levels;
+    for (int k = 0; k < ns; ++k) b1.push_back({(char*)Sp + eb * le * k, (char*)W + eb * ge * k, g});
+    for (int l = 0; l < nlevels; ++l)
+        if (nsmear[l] == 0) {
+            b1.push_back({(char*)U_out + eb * le * l, (char*)G_out + eb * ge * l, g});
+            plain_levels.push_back(l);
+        }
+    {
+        const int n1 = (int)b1.size();
+        std::vector<double> R1(n1);
+        std::vector<int> s1(n1), s321(n1);
+        rc = fix_fields(b1, prec, params, R1.data(), s1.data(), s321.data(), nullptr, stream);
         if (rc != MCG_OK && rc != MCG_NOT_CONVERGED) return rc;
         if (rc == MCG_NOT_CONVERGED) status = MCG_NOT_CONVERGED;
-        for (int k = 0; k < ns; ++k)
-            MCG_CK(cudaMemcpyAsync((char*)G_out + eb * ge * smeared[k], (char*)W + eb * ge * k, eb * ge,
-                                   cudaMemcpyDeviceToDevice, stream));
-        if ((rc = launch_reunitarise(G_out, 1, prec, g, nlevels, stream))) return rc;
-        if ((rc = launch_apply_gauge(U_out, G_out, prec, g, nlevels, stream))) return rc;
+        for (int k = 0; k < ns; ++k) {
+            Rs[k] = R1[k];
+            sw_s[k] = s1[k];
+            sw32_s[k] = s321[k];
+        }
+        for (size_t j = 0; j < plain_levels.size(); ++j) {
+            const int l = plain_levels[j];
+            Rf[l] = R1[ns + j];
+            sw_f[l] = s1[ns + j];
+            sw32_f[l] = s321[ns + j];
+        }
     }
-    mcg_lattice lb = *lat;
-    lb.nfields = nlevels;
-    rc = fix_impl(U_out, G_out, &lb, g, params, Rf.data(), sw_f.data(), sw32_f.data(), nullptr, stream);
-    if (rc != MCG_OK && rc != MCG_NOT_CONVERGED) return rc;
-    if (rc == MCG_NOT_CONVERGED) status = MCG_NOT_CONVERGED;
+    if (ns > 0) {
+        for (int k = 0; k < ns; ++k) {
+            char* Gl = (char*)G_out + eb * ge * smeared[k];
+            char* Ul = (char*)U_out + eb * le * smeared[k];
+            MCG_CK(cudaMemcpyAsync(Gl, (char*)W + eb * ge * k, eb * ge, cudaMemcpyDeviceToDevice, stream));
+            if ((rc = launch_reunitarise(Gl, 1, prec, g, 1, stream))) return rc;
+            if ((rc = launch_apply_gauge(Ul, Gl, prec, g, 1, stream))) return rc;
+            b2.push_back({Ul, Gl, g});
+        }
+        std::vector<double> R2(ns);
+        std::vector<int> s2(ns), s322(ns);
+        rc = fix_fields(b2, prec, params, R2.data(), s2.data(), s322.data(), nullptr, stream);
+        if (rc != MCG_OK && rc != MCG_NOT_CONVERGED) return rc;
+        if (rc == MCG_NOT_CONVERGED) status = MCG_NOT_CONVERGED;
+        for (int k = 0; k < ns; ++k) {
+            Rf[smeared[k]] = R2[k];
+            sw_f[smeared[k]] = s2[k];
+            sw32_f[smeared[k]] = s322[k];
+        }
+    }
     int8_t* Zb = Z_out;
     if (!Zb) {
         Zb = (int8_t*)scratch_device("lev.Z", 8 * (size_t)g.vh * nlevels, &rc);
