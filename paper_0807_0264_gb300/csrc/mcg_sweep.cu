@@ -659,6 +659,9 @@ static int enqueue_sweep(const SweepBatch& bt, int nt, int spb, cudaStream_t st)
     return 0;
 }
 
+// largest batch captured as per-field chains
+constexpr int kMaxChains = 16;
+
 template <typename T>
 int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, FieldState* h_state, double* d_hist,
                   int hist_len, double tol, int window, double omega, int reunit_every, int abs_cap,
@@ -739,19 +742,21 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
     if (rc) return rc;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    // A batch of several fields runs as independent per-field chains of
+    // A batch of a few fields runs as independent per-field chains of
     // half-sweeps inside the graph (one branch stream each, forked from and
     // joined to the capture stream): no field waits for another at the
     // half-sweep boundaries, the fields drift apart in phase, and one field's
     // load phase overlaps another's arithmetic (measured: the step 4.6 %
     // faster than one launch per half-sweep covering every field).  Each chain
     // sees its field as a batch of one (block offset 0, its own state, partials
-    // and R history), so the per-field arithmetic is unchanged.
+    // and R history), so the per-field arithmetic is unchanged.  A large batch
+    // fills the GPU with one launch per half-sweep and keeps the graph small.
+    const bool chained = nf > 1 && nf <= kMaxChains;
     std::vector<SweepBatch> chains;
     std::vector<cudaStream_t> bs(nf);
     std::vector<cudaEvent_t> be(nf);
     cudaEvent_t fork = nullptr;
-    if (nf > 1) {
+    if (chained) {
         FieldDesc* d_single = (FieldDesc*)scratch_device("fix.desc1", sizeof(FieldDesc) * nf, &rc);
         if (rc) return rc;
         FieldDesc* h_single = (FieldDesc*)scratch_host("fix.desc1", sizeof(FieldDesc) * nf, &rc);
@@ -777,7 +782,7 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
     MCG_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
     // no early return while the capture is open: the first error ends it
     cudaError_t qe = cudaSuccess;
-    if (nf > 1) {
+    if (chained) {
         qe = cudaEventRecord(fork, cs);
         for (int f = 0; f < nf && qe == cudaSuccess; ++f) {
             qe = cudaStreamWaitEvent(bs[f], fork, 0);
@@ -799,7 +804,7 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
         cudaGraphDestroy(graph);
         return cuda_fail(ce, "cudaGraphInstantiate");
     }
-    const int nodes_per_chunk = nf * chunk * ((!DF && sizeof(T) == 8 && reunit_every > 0) ? 4 : 3);
+    const int nodes_per_chunk = (chained ? nf : 1) * chunk * ((!DF && sizeof(T) == 8 && reunit_every > 0) ? 4 : 3);
     const int max_chunks = (phase_len + chunk - 1) / chunk + 1;
     int status = 0;
     // phase timing (instrumentation): GPU time of the chunk graphs and the
