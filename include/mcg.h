@@ -387,6 +387,17 @@ int mcg_halfsweep_slab(void* U, void* G, const mcg_lattice* lat, int parity, int
 int mcg_slab_face(void* U, void* buf, const mcg_lattice* lat, int t, int parity, int to_field, cudaStream_t stream);
 
 /*
+ * Index checks (not in the paper: a debugging aid).  In a library built with
+ * -DMCG_CHECK (paper_0807_0264_gb300.build.build(check=True)) the kernels'
+ * layout helpers test every index against its array; an index out of range
+ * is counted and replaced by a valid one, so the access stays inside the
+ * array and no kernel traps.  Returns the number of such indices met since
+ * the last reset (synchronises the device; reset != 0 zeroes the counters),
+ * or -1 in a regular build (no device call).
+ */
+long long mcg_bounds_violations(int reset);
+
+/*
  * MCG relaxation (as mcg_fix) of a batch of fields of any sizes, all of one
  * precision: each field's half-sweeps run as their own chain of launches
  * (the chains concurrent inside one graph per chunk of sweeps); a field stops

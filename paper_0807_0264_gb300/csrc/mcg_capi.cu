@@ -2,6 +2,7 @@
 // validation, error reporting, scratch management and the host-side
 // orchestration of the MCG relaxation and the preconditioning pipeline.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cstdlib>
@@ -42,6 +43,16 @@ int cuda_fail(cudaError_t e, const char* what) {
     set_error(buf);
     return MCG_CUDA_ERROR;
 }
+
+// ---------------------------------------------------------------------------
+// NVTX ranges (header-only NVTX 3: no cost unless a profiler is attached)
+// ---------------------------------------------------------------------------
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---------------------------------------------------------------------------
 // launch accounting
@@ -288,6 +299,7 @@ static int fix_fields(const std::vector<FieldSpec>& fs, int prec, const mcg_para
     };
 
     if (prec == MCG_F64 && prm->fp32_sweeps > 0) {
+        NvtxRange nvtx_phase_("fix: FP32 phase");
         // FP32 phase on compact copies of the links and on the transform W of
         // this call (starting from the identity)
         std::vector<FieldDesc> fds;
@@ -309,6 +321,7 @@ static int fix_fields(const std::vector<FieldSpec>& fs, int prec, const mcg_para
         fresh = false;
     }
     if (prec == MCG_F64 && prm->fp64_df) {
+        NvtxRange nvtx_phase_("fix: double-float phase");
         // FP64-class sweeps in double-float on compact copies of the links and
         // a transform W of the phase (from the identity); at the end W is
         // re-unitarised in FP64 and applied to the FP64 links and transform
@@ -495,6 +508,7 @@ int mcg_set_identity_gauge(void* G, const mcg_lattice* lat, cudaStream_t stream)
 }
 
 int mcg_plaquette(const void* U, double* out, const mcg_lattice* lat, cudaStream_t stream) {
+    NvtxRange nvtx_range_("mcg_plaquette");
     Geom g;
     int rc = check_lat(lat, &g);
     if (rc) return rc;
@@ -511,6 +525,7 @@ int mcg_functional(const void* U, double* R_out, const mcg_lattice* lat, cudaStr
 }
 
 int mcg_apply_gauge(void* U, const void* G, const mcg_lattice* lat, cudaStream_t stream) {
+    NvtxRange nvtx_range_("mcg_apply_gauge");
     Geom g;
     int rc = check_lat(lat, &g);
     if (rc) return rc;
@@ -532,6 +547,7 @@ int mcg_reunitarise(void* M, int which, const mcg_lattice* lat, cudaStream_t str
 
 int mcg_smear(const void* U_in, void* U_out, const mcg_lattice* lat, double rho, double eps, int n,
               cudaStream_t stream) {
+    NvtxRange nvtx_range_("mcg_smear");
     Geom g;
     int rc = check_lat(lat, &g);
     if (rc) return rc;
@@ -546,6 +562,7 @@ int mcg_smear(const void* U_in, void* U_out, const mcg_lattice* lat, double rho,
 
 int mcg_fix(void* U, void* G, const mcg_lattice* lat, const mcg_params* params, double* R_out, int* sweeps_out,
             double* R_hist, cudaStream_t stream) {
+    NvtxRange nvtx_range_("mcg_fix");
     Geom g;
     int rc = check_lat(lat, &g);
     if (rc) return rc;
@@ -561,6 +578,7 @@ int mcg_fix(void* U, void* G, const mcg_lattice* lat, const mcg_params* params, 
 
 int mcg_anneal(void* U, void* G, const mcg_lattice* lat, const double* T, int nsweeps, long long first_sweep,
                int nhit, double eps, unsigned long long seed, long long* accepted_out, cudaStream_t stream) {
+    NvtxRange nvtx_range_("mcg_anneal");
     Geom g;
     int rc = check_lat(lat, &g);
     if (rc) return rc;
@@ -581,6 +599,7 @@ int mcg_anneal(void* U, void* G, const mcg_lattice* lat, const double* T, int ns
 }
 
 int mcg_center_project(const void* U, int8_t* Z, long long* counts, const mcg_lattice* lat, cudaStream_t stream) {
+    NvtxRange nvtx_range_("mcg_center_project");
     Geom g;
     int rc = check_lat(lat, &g);
     if (rc) return rc;
@@ -592,6 +611,7 @@ int mcg_center_project(const void* U, int8_t* Z, long long* counts, const mcg_la
 
 int mcg_vortex_remove(const void* U, const int8_t* Z, void* U_removed, void* U_center, const mcg_lattice* lat,
                       cudaStream_t stream) {
+    NvtxRange nvtx_range_("mcg_vortex_remove");
     Geom g;
     int rc = check_lat(lat, &g);
     if (rc) return rc;
@@ -606,6 +626,7 @@ int mcg_vortex_remove(const void* U, const int8_t* Z, void* U_removed, void* U_c
 }
 
 int mcg_wilson_loops(const void* U, const mcg_lattice* lat, int Rmax, int Tmax, double* W_out, cudaStream_t stream) {
+    NvtxRange nvtx_range_("mcg_wilson_loops");
     Geom g;
     int rc = check_lat(lat, &g);
     if (rc) return rc;
@@ -618,6 +639,7 @@ int mcg_wilson_loops(const void* U, const mcg_lattice* lat, int Rmax, int Tmax, 
 
 int mcg_wilson_loops_offaxis(const void* U, const mcg_lattice* lat, const int* vectors, int nvec, int Tmax,
                              double* W_out, cudaStream_t stream) {
+    NvtxRange nvtx_range_("mcg_wilson_loops_offaxis");
     Geom g;
     int rc = check_lat(lat, &g);
     if (rc) return rc;
@@ -640,6 +662,7 @@ int mcg_wilson_loops_offaxis(const void* U, const mcg_lattice* lat, const int* v
 int mcg_precondition_fix(void* U, void* G, int8_t* Z, const mcg_lattice* lat, const mcg_params* params, double rho,
                          double eps, int nsmear, int smear_precision, mcg_precond_result* results,
                          cudaStream_t stream) {
+    NvtxRange nvtx_range_("mcg_precondition_fix");
     Geom g;
     int rc = check_lat(lat, &g);
     if (rc) return rc;
@@ -720,6 +743,18 @@ int mcg_probe_peaks(double* tflops_out, cudaStream_t stream) {
     return probe_peaks(tflops_out, stream);
 }
 
+long long mcg_bounds_violations(int reset) {
+#ifdef MCG_CHECK
+    cudaDeviceSynchronize();
+    const bool r = reset != 0;
+    return (long long)(bound_hits_field(r) + bound_hits_observables(r) + bound_hits_smear(r) + bound_hits_sweep(r) +
+                       bound_hits_sweep_f32(r) + bound_hits_sweep_df(r));
+#else
+    (void)reset;
+    return -1;
+#endif
+}
+
 int mcg_phase_stats(double* ms_out, long long* site_updates_out, int reset) {
     if (!ms_out || !site_updates_out) return fail(MCG_BAD_ARG, "null pointer");
     std::lock_guard<std::mutex> lk(g_phase_mu);
@@ -766,6 +801,7 @@ int mcg_time_halfsweep(void* U, void* G, const mcg_lattice* lat, int parity, int
 
 int mcg_halfsweep_slab(void* U, void* G, const mcg_lattice* lat, int parity, int t_lo, int t_hi, double* R_out,
                       cudaStream_t stream) {
+    NvtxRange nvtx_range_("mcg_halfsweep_slab");
     Geom g;
     int rc = check_lat(lat, &g);
     if (rc) return rc;
@@ -802,6 +838,7 @@ int mcg_slab_face(void* U, void* buf, const mcg_lattice* lat, int t, int parity,
 int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_out, const mcg_lattice* lat,
                             const mcg_params* params, double rho, double eps, const int* nsmear, int nlevels,
                             int smear_precision, mcg_precond_result* results, cudaStream_t stream) {
+    NvtxRange nvtx_range_("mcg_precondition_levels");
     Geom g;
     int rc = check_lat(lat, &g);
     if (rc) return rc;
@@ -938,6 +975,7 @@ int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_o
 
 int mcg_fix_batch(const mcg_field* fields, int nfields, int precision, const mcg_params* params, double* R_out,
                   int* sweeps_out, cudaStream_t stream) {
+    NvtxRange nvtx_range_("mcg_fix_batch");
     if (!fields || nfields < 1) return fail(MCG_BAD_ARG, "fields is NULL or nfields < 1");
     if (precision != MCG_F64 && precision != MCG_F32) return fail(MCG_BAD_ARG, "bad precision");
     int rc = check_params(params);
@@ -955,6 +993,7 @@ int mcg_fix_batch(const mcg_field* fields, int nfields, int precision, const mcg
 int mcg_gribov_search(const mcg_field* copies, int ncopies, const int* config_of_copy, int nconfigs, int precision,
                       const mcg_params* params, double* R_out, int* sweeps_out, int* best_copy, double* best_V,
                       cudaStream_t stream) {
+    NvtxRange nvtx_range_("mcg_gribov_search");
     if (!copies || ncopies < 1 || !config_of_copy || nconfigs < 1) return fail(MCG_BAD_ARG, "bad copy list");
     if (precision != MCG_F64 && precision != MCG_F32) return fail(MCG_BAD_ARG, "bad precision");
     int rc = check_params(params);

@@ -192,18 +192,60 @@ struct Geom {
     int vh;  // V / 2
 };
 
+// ---------------------------------------------------------------------------
+// Index checks of the MCG_CHECK build (nvcc -DMCG_CHECK): the layout helpers
+// below test every component of an index against its range (direction,
+// parity, entry or chunk, site, coordinate); a bad one is counted in a
+// device counter of the translation unit and the helper returns index 0, so
+// the access stays inside the array and no kernel traps.  Each unit's counter
+// is read by the host function its MCG_BOUND_READER defines
+// (mcg_bounds_violations sums them).  Without MCG_CHECK the checks compile to
+// nothing.
+// ---------------------------------------------------------------------------
+#ifdef MCG_CHECK
+static __device__ unsigned long long g_bound_hits;
+__device__ __forceinline__ bool mcg_bad(bool bad) {
+    if (bad) atomicAdd(&g_bound_hits, 1ULL);
+    return bad;
+}
+#define MCG_BOUND_READER(fn)                                                   \
+    unsigned long long fn(bool reset) {                                        \
+        unsigned long long v = 0;                                              \
+        cudaMemcpyFromSymbol(&v, g_bound_hits, sizeof v);                      \
+        if (reset) {                                                           \
+            const unsigned long long z = 0;                                    \
+            cudaMemcpyToSymbol(g_bound_hits, &z, sizeof z);                    \
+        }                                                                      \
+        return v;                                                              \
+    }
+#else
+__device__ __forceinline__ bool mcg_bad(bool) { return false; }
+#define MCG_BOUND_READER(fn) \
+    unsigned long long fn(bool) { return 0; }
+#endif
+
 __host__ __device__ __forceinline__ size_t link_elems(const Geom& g) { return (size_t)72 * g.vh; }
 __host__ __device__ __forceinline__ size_t gauge_elems(const Geom& g) { return (size_t)18 * g.vh; }
 
 __device__ __forceinline__ size_t lidx(const Geom& g, int mu, int p, int e, int s) {
+#ifdef MCG_CHECK
+    if (mcg_bad((unsigned)mu >= 4u || (unsigned)p >= 2u || (unsigned)e >= 9u || (unsigned)s >= (unsigned)g.vh))
+        return 0;
+#endif
     return ((size_t)((mu * 2 + p) * 9 + e)) * g.vh + s;
 }
 __device__ __forceinline__ size_t gidx(const Geom& g, int p, int e, int s) {
+#ifdef MCG_CHECK
+    if (mcg_bad((unsigned)p >= 2u || (unsigned)e >= 9u || (unsigned)s >= (unsigned)g.vh)) return 0;
+#endif
     return ((size_t)(p * 9 + e)) * g.vh + s;
 }
 
 // coordinates (x,y,z,t) of site s in parity p
 __device__ __forceinline__ void eo_coords(const Geom& g, int p, int s, int c[4]) {
+#ifdef MCG_CHECK
+    if (mcg_bad((unsigned)p >= 2u || (unsigned)s >= (unsigned)g.vh)) s = 0;
+#endif
     int i2 = 2 * s;
     int x0 = i2 % g.n[0];
     int r = i2 / g.n[0];
@@ -214,6 +256,11 @@ __device__ __forceinline__ void eo_coords(const Geom& g, int p, int s, int c[4])
     c[0] = x0 + ((c[1] + c[2] + c[3] + p) & 1);
 }
 __device__ __forceinline__ int eo_index(const Geom& g, const int c[4]) {
+#ifdef MCG_CHECK
+    if (mcg_bad((unsigned)c[0] >= (unsigned)g.n[0] || (unsigned)c[1] >= (unsigned)g.n[1] ||
+                (unsigned)c[2] >= (unsigned)g.n[2] || (unsigned)c[3] >= (unsigned)g.n[3]))
+        return 0;
+#endif
     return (c[0] + g.n[0] * (c[1] + g.n[1] * (c[2] + g.n[2] * c[3]))) >> 1;
 }
 // in-parity index of the neighbour c +- mu (step = +1 or -1), periodic
@@ -249,9 +296,16 @@ __device__ __forceinline__ void store_link(cplx<T>* __restrict__ U, const Geom& 
 __host__ __device__ __forceinline__ size_t c12_link_chunks(const Geom& g) { return (size_t)24 * g.vh; }
 __host__ __device__ __forceinline__ size_t c12_gauge_chunks(const Geom& g) { return (size_t)6 * g.vh; }
 __device__ __forceinline__ size_t c12_lidx(const Geom& g, int mu, int p, int q, int s) {
+#ifdef MCG_CHECK
+    if (mcg_bad((unsigned)mu >= 4u || (unsigned)p >= 2u || (unsigned)q >= 3u || (unsigned)s >= (unsigned)g.vh))
+        return 0;
+#endif
     return ((size_t)((mu * 2 + p) * 3 + q)) * g.vh + s;
 }
 __device__ __forceinline__ size_t c12_gidx(const Geom& g, int p, int q, int s) {
+#ifdef MCG_CHECK
+    if (mcg_bad((unsigned)p >= 2u || (unsigned)q >= 3u || (unsigned)s >= (unsigned)g.vh)) return 0;
+#endif
     return ((size_t)(p * 3 + q)) * g.vh + s;
 }
 

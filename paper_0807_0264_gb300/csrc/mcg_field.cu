@@ -879,6 +879,9 @@ void static_release() {
     for (auto& p : g_static_addr) p = nullptr;
 }
 
+// index-check counter of this unit (MCG_CHECK builds)
+MCG_BOUND_READER(bound_hits_field)
+
 }  // namespace mcg
 
 extern "C" int mcg_plaquette_static(const void* U, double* out, const mcg_lattice* lat, cudaStream_t stream) {

@@ -48,6 +48,13 @@ cudaStream_t capture_stream(int* rc);
 // n branch streams (and an event per stream, plus a fork event) for the
 // per-field chains of a captured sweep graph, cached per device.
 int branch_streams(int n, cudaStream_t* streams, cudaEvent_t* events, cudaEvent_t* fork, int* rc);
+// index-check counters of the kernel units (0 unless built with MCG_CHECK)
+unsigned long long bound_hits_field(bool reset);
+unsigned long long bound_hits_observables(bool reset);
+unsigned long long bound_hits_smear(bool reset);
+unsigned long long bound_hits_sweep(bool reset);
+unsigned long long bound_hits_sweep_f32(bool reset);
+unsigned long long bound_hits_sweep_df(bool reset);
 void release_all();
 
 // ---- batched sweep machinery -------------------------------------------------

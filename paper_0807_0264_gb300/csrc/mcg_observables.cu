@@ -426,4 +426,7 @@ int compute_wilson_loops_offaxis(const void* U, int prec, const Geom& g, int nfi
     return wilson_offaxis_impl<float>((const cplx<float>*)U, g, nfields, vecs, nvec, Tmax, W_host, st);
 }
 
+// index-check counter of this unit (MCG_CHECK builds)
+MCG_BOUND_READER(bound_hits_observables)
+
 }  // namespace mcg

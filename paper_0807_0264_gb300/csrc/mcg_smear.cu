@@ -745,4 +745,7 @@ int run_ascent_step(void* U, void* G, const double* grad, double alpha, int prec
     return launch_apply_gauge(U, W, prec, g, nfields, st);
 }
 
+// index-check counter of this unit (MCG_CHECK builds)
+MCG_BOUND_READER(bound_hits_smear)
+
 }  // namespace mcg

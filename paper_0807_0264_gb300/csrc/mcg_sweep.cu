@@ -1025,4 +1025,7 @@ template int run_fix_phase<DoubleFloat>(const std::vector<FieldDesc>&, FieldStat
 template int run_fix_phase<double>(const std::vector<FieldDesc>&, FieldState*, FieldState*, double*, int, double,
                                    int, double, int, int, int, bool, cudaStream_t, bool);
 
+// index-check counter of this unit (MCG_CHECK builds)
+MCG_BOUND_READER(bound_hits_sweep)
+
 }  // namespace mcg

@@ -642,6 +642,9 @@ __device__ __forceinline__ int field_of_block(const FieldDesc* __restrict__ d, i
         else
             hi = mid - 1;
     }
+#ifdef MCG_CHECK
+    mcg_bad(b < d[lo].blk0 || b >= d[lo].blk0 + d[lo].nblk);
+#endif
     return lo;
 }
 

@@ -489,4 +489,7 @@ int launch_identity_df(void* hi, void* lo, const Geom& g, int nfields, cudaStrea
     return 0;
 }
 
+// index-check counter of this unit (MCG_CHECK builds)
+MCG_BOUND_READER(bound_hits_sweep_df)
+
 }  // namespace mcg

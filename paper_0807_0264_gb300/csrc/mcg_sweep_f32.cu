@@ -402,4 +402,7 @@ void launch_halfsweep_c12(int nt, bool acc, const SweepBatch& bt, int parity, in
     }
 }
 
+// index-check counter of this unit (MCG_CHECK builds)
+MCG_BOUND_READER(bound_hits_sweep_f32)
+
 }  // namespace mcg

@@ -61,8 +61,9 @@ class mcg_precond_result(ctypes.Structure):
 
 
 def _load() -> ctypes.CDLL:
-    path = _build.LIB
-    if not os.path.exists(path):
+    # MCG_LIBRARY: an explicit libmcg build (e.g. the index-checking one)
+    path = os.environ.get("MCG_LIBRARY") or _build.LIB
+    if path == _build.LIB and not os.path.exists(path):
         _build.build()
     lib = ctypes.CDLL(path)
     P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
@@ -97,6 +98,7 @@ def _load() -> ctypes.CDLL:
         "mcg_kernel_launches": ([], ctypes.c_longlong),
         "mcg_halfsweep_slab": ([P, P, L, I, I, I, P, P], I),
         "mcg_slab_face": ([P, P, L, I, I, I, P], I),
+        "mcg_bounds_violations": ([I], ctypes.c_longlong),
         "mcg_probe_peaks": ([ctypes.POINTER(ctypes.c_double), P], I),
         "mcg_phase_stats": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), I], I),
         "mcg_plaquette_static": ([P, P, L, P], I),
@@ -128,7 +130,7 @@ EXPORTS = ("mcg_version", "mcg_last_error", "mcg_release", "mcg_pack_links", "mc
            "mcg_gribov_search", "mcg_smear_backward_step", "mcg_functional_matrix_grad", "mcg_grad_R",
            "mcg_ascent_step", "mcg_vortex_remove", "mcg_wilson_loops",
            "mcg_wilson_loops_offaxis", "mcg_anneal", "mcg_phase_stats",
-           "mcg_halfsweep_slab", "mcg_slab_face", "mcg_probe_peaks")
+           "mcg_halfsweep_slab", "mcg_slab_face", "mcg_bounds_violations", "mcg_probe_peaks")
 
 
 def library() -> ctypes.CDLL:
@@ -529,6 +531,12 @@ def mcg_slab_face(U: torch.Tensor, buf: torch.Tensor, dims, t: int, parity: int,
     _check("mcg_slab_face", _lib.mcg_slab_face(_ptr(U), _ptr(buf), lattice(dims, 1, prec), int(t), int(parity),
                                                int(bool(to_field)), _stream(stream)))
     return buf
+
+
+def mcg_bounds_violations(reset: bool = False) -> int:
+    """Out-of-range indices the kernels met (index-checking build), -1 in a
+    regular build."""
+    return int(_lib.mcg_bounds_violations(int(bool(reset))))
 
 
 def mcg_probe_peaks(stream=None) -> dict:

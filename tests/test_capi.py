@@ -185,6 +185,12 @@ def test_slab_phase_stats_and_bounds_validation_without_gpu(mcg):
     code(lib.mcg_plaquette(one, None, ctypes.byref(mcg.lattice((4, 4, 4, 4), 1 << 21)), None), 2, "nfields")
 
 
+def test_regular_build_reports_no_index_checks(mcg):
+    """mcg_bounds_violations answers -1 in a build without -DMCG_CHECK, with
+    no device call."""
+    assert mcg.library().mcg_bounds_violations(0) == -1
+
+
 def test_slab_face_validation_without_gpu(mcg):
     """The slab face copy checks layer, parity, direction, field count,
     pointers and overlap on the host before any device work."""
