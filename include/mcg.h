@@ -124,7 +124,8 @@ typedef struct {
     int sweeps_smeared;    /* sweeps spent fixing the smeared field            */
     int sweeps_fixed;      /* sweeps spent fixing the preconditioned field     */
     int sweeps_fp32;       /* of those, sweeps run in the FP32 phase           */
-    int status;            /* MCG_OK or MCG_NOT_CONVERGED                       */
+    int status;            /* this field's (level's) fixes: MCG_OK when both    */
+                           /* converged, else MCG_NOT_CONVERGED                 */
 } mcg_precond_result;
 
 /*

@@ -257,7 +257,7 @@ struct FieldSpec {
 // MCG relaxation of a batch of fields (all of one precision, any sizes), one
 // launch per half-sweep for the whole batch.
 static int fix_fields(const std::vector<FieldSpec>& fs, int prec, const mcg_params* prm, double* R_out,
-                      int* sweeps_out, int* sweeps32_out, double* R_hist, cudaStream_t st) {
+                      int* sweeps_out, int* sweeps32_out, double* R_hist, cudaStream_t st, int* converged_out = nullptr) {
     const int nf = (int)fs.size();
     int rc = 0;
     FieldState* d_state = (FieldState*)scratch_device("fix.state", sizeof(FieldState) * nf, &rc);
@@ -392,6 +392,7 @@ static int fix_fields(const std::vector<FieldSpec>& fs, int prec, const mcg_para
         if (R_out) R_out[f] = h_state[f].R_last;
         if (sweeps_out) sweeps_out[f] = h_state[f].sweep;
         if (sweeps32_out) sweeps32_out[f] = s32[f];
+        if (converged_out) converged_out[f] = h_state[f].done == 1;
         all = all && h_state[f].done == 1;
     }
     if (R_hist) {
@@ -403,7 +404,7 @@ static int fix_fields(const std::vector<FieldSpec>& fs, int prec, const mcg_para
 
 // uniform batch: nfields fields of lat's dims stored back to back
 static int fix_impl(void* U, void* G, const mcg_lattice* lat, const Geom& g, const mcg_params* prm, double* R_out,
-                    int* sweeps_out, int* sweeps32_out, double* R_hist, cudaStream_t st) {
+                    int* sweeps_out, int* sweeps32_out, double* R_hist, cudaStream_t st, int* converged_out = nullptr) {
     const size_t eb = elem_bytes(lat->precision);
     std::vector<FieldSpec> fs(lat->nfields);
     for (int f = 0; f < lat->nfields; ++f) {
@@ -411,7 +412,7 @@ static int fix_impl(void* U, void* G, const mcg_lattice* lat, const Geom& g, con
         fs[f].G = (char*)G + eb * gauge_elems(g) * f;
         fs[f].g = g;
     }
-    return fix_fields(fs, lat->precision, prm, R_out, sweeps_out, sweeps32_out, R_hist, st);
+    return fix_fields(fs, lat->precision, prm, R_out, sweeps_out, sweeps32_out, R_hist, st, converged_out);
 }
 
 // validate one entry of an mcg_field array
@@ -675,6 +676,7 @@ int mcg_precondition_fix(void* U, void* G, int8_t* Z, const mcg_lattice* lat, co
     const size_t le = link_elems(g), ge = gauge_elems(g), eb = elem_bytes(prec);
     std::vector<double> plaq_in(nf), plaq_out(nf), Rs(nf, 0.0), Rf(nf);
     std::vector<int> sw_s(nf, 0), sw_f(nf), sw32_s(nf, 0), sw32_f(nf, 0);
+    std::vector<int> conv_s(nf, 1), conv_f(nf, 1);
     std::vector<long long> counts(7 * (size_t)nf);
     if ((rc = compute_plaquette(U, prec, g, nf, plaq_in.data(), stream))) return rc;
     int status = MCG_OK;
@@ -701,7 +703,7 @@ int mcg_precondition_fix(void* U, void* G, int8_t* Z, const mcg_lattice* lat, co
         if ((rc = launch_convert(S, smear_precision, Sp, prec, le * nf, stream))) return rc;
         if (smear_precision != prec && (rc = launch_reunitarise(Sp, 0, prec, g, nf, stream))) return rc;
         if ((rc = launch_identity_gauge(W, prec, g, nf, stream))) return rc;
-        rc = fix_impl(Sp, W, lat, g, params, Rs.data(), sw_s.data(), sw32_s.data(), nullptr, stream);
+        rc = fix_impl(Sp, W, lat, g, params, Rs.data(), sw_s.data(), sw32_s.data(), nullptr, stream, conv_s.data());
         if (rc != MCG_OK && rc != MCG_NOT_CONVERGED) return rc;
         if (rc == MCG_NOT_CONVERGED) status = MCG_NOT_CONVERGED;
         // G <- reunit(W), then U <- U^G (the preconditioning transform)
@@ -710,7 +712,7 @@ int mcg_precondition_fix(void* U, void* G, int8_t* Z, const mcg_lattice* lat, co
         if ((rc = launch_apply_gauge(U, G, prec, g, nf, stream))) return rc;
     }
     // fix the preconditioned original field, accumulating into G
-    rc = fix_impl(U, G, lat, g, params, Rf.data(), sw_f.data(), sw32_f.data(), nullptr, stream);
+    rc = fix_impl(U, G, lat, g, params, Rf.data(), sw_f.data(), sw32_f.data(), nullptr, stream, conv_f.data());
     if (rc != MCG_OK && rc != MCG_NOT_CONVERGED) return rc;
     if (rc == MCG_NOT_CONVERGED) status = MCG_NOT_CONVERGED;
     int8_t* Zb = Z;
@@ -731,7 +733,7 @@ int mcg_precondition_fix(void* U, void* G, int8_t* Z, const mcg_lattice* lat, co
         r.sweeps_smeared = sw_s[f];
         r.sweeps_fixed = sw_f[f];
         r.sweeps_fp32 = sw32_s[f] + sw32_f[f];
-        r.status = status;
+        r.status = (conv_s[f] && conv_f[f]) ? MCG_OK : MCG_NOT_CONVERGED;
     }
     return status;
 }
@@ -864,6 +866,7 @@ int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_o
     const int ns = (int)smeared.size();
     std::vector<double> Rs(std::max(ns, 1), 0.0), Rf(nlevels);
     std::vector<int> sw_s(std::max(ns, 1), 0), sw32_s(std::max(ns, 1), 0), sw_f(nlevels), sw32_f(nlevels);
+    std::vector<int> conv_s(std::max(ns, 1), 1), conv_f(nlevels, 1);
     int status = MCG_OK;
     // every level starts from the input field and the identity transform
     for (int l = 0; l < nlevels; ++l)
@@ -910,19 +913,22 @@ int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_o
         const int n1 = (int)b1.size();
         std::vector<double> R1(n1);
         std::vector<int> s1(n1), s321(n1);
-        rc = fix_fields(b1, prec, params, R1.data(), s1.data(), s321.data(), nullptr, stream);
+        std::vector<int> c1(n1, 1);
+        rc = fix_fields(b1, prec, params, R1.data(), s1.data(), s321.data(), nullptr, stream, c1.data());
         if (rc != MCG_OK && rc != MCG_NOT_CONVERGED) return rc;
         if (rc == MCG_NOT_CONVERGED) status = MCG_NOT_CONVERGED;
         for (int k = 0; k < ns; ++k) {
             Rs[k] = R1[k];
             sw_s[k] = s1[k];
             sw32_s[k] = s321[k];
+            conv_s[k] = c1[k];
         }
         for (size_t j = 0; j < plain_levels.size(); ++j) {
             const int l = plain_levels[j];
             Rf[l] = R1[ns + j];
             sw_f[l] = s1[ns + j];
             sw32_f[l] = s321[ns + j];
+            conv_f[l] = c1[ns + j];
         }
     }
     if (ns > 0) {
@@ -936,13 +942,15 @@ int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_o
         }
         std::vector<double> R2(ns);
         std::vector<int> s2(ns), s322(ns);
-        rc = fix_fields(b2, prec, params, R2.data(), s2.data(), s322.data(), nullptr, stream);
+        std::vector<int> c2(ns, 1);
+        rc = fix_fields(b2, prec, params, R2.data(), s2.data(), s322.data(), nullptr, stream, c2.data());
         if (rc != MCG_OK && rc != MCG_NOT_CONVERGED) return rc;
         if (rc == MCG_NOT_CONVERGED) status = MCG_NOT_CONVERGED;
         for (int k = 0; k < ns; ++k) {
             Rf[smeared[k]] = R2[k];
             sw_f[smeared[k]] = s2[k];
             sw32_f[smeared[k]] = s322[k];
+            conv_f[smeared[k]] = c2[k];
         }
     }
     int8_t* Zb = Z_out;
@@ -968,7 +976,7 @@ int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_o
         r.vortex_density = (double)counts[7 * l] / (6.0 * 2.0 * g.vh);
         r.sweeps_fixed = sw_f[l];
         r.sweeps_fp32 = (k >= 0 ? sw32_s[k] : 0) + sw32_f[l];
-        r.status = status;
+        r.status = ((k < 0 || conv_s[k]) && conv_f[l]) ? MCG_OK : MCG_NOT_CONVERGED;
     }
     return status;
 }

@@ -100,3 +100,25 @@ def test_precondition_levels_mixed_fp32_smearing_matches_oracle_pipeline():
         Uf = mcg.mcg_unpack_links(Uo[l:l + 1], dims)[0].cpu().numpy()
         Gf = mcg.mcg_unpack_gauge(Go[l:l + 1], dims)[0].cpu().numpy()
         assert np.abs(oracle.apply_gauge(dims, U, Gf) - Uf).max() < 1e-12
+
+
+def test_levels_report_convergence_per_level():
+    """A level's status is its own: MCG_OK exactly when its fixes stopped
+    below the sweep cap; the call's status is MCG_NOT_CONVERGED when any
+    level is not converged."""
+    from paper_0807_0264_gb300 import mcg
+
+    dims = (6, 6, 6, 6)
+    U = mcg.mcg_pack_links(torch.from_numpy(synth.make_field(dims, 0.9, 41)).unsqueeze(0).cuda(), dims)
+    # the oracle's plain FP64 relaxation needs 2209 sweeps at n = 0, 91 + 1073
+    # at n = 6 and 56 + 1456 at n = 12 on this field: a cap of 1200 stops
+    # levels 0 and 12 and lets level 6 converge
+    cap = 1200
+    res = mcg.mcg_precondition_levels(U, dims, [0, 6, 12], mcg.Params(tol=1e-10, max_sweeps=cap), rho=0.1,
+                                      eps=1.0, smear_precision=mcg.F64)[3]
+    hit = []
+    for n, r in zip((0, 6, 12), res):
+        capped = r["sweeps_fixed"] >= cap or (n > 0 and r["sweeps_smeared"] >= cap)
+        assert (r["status"] == mcg.OK) == (not capped), (n, r)
+        hit.append(capped)
+    assert hit == [True, False, True]
