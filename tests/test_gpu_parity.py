@@ -432,6 +432,26 @@ def test_heterogeneous_batch_with_mixed_df_schedule_equals_single_fields(mcg):
         assert torch.equal(Ub[k], Us1) and torch.equal(Gb[k], Gs1)
 
 
+def test_large_batch_one_launch_per_half_sweep_equals_single_fields(mcg):
+    """Above 16 fields a batch runs one launch per half-sweep for all its
+    fields instead of per-field chains: each of 18 fields of two sizes still
+    gets exactly what it gets alone (sweeps, links and transform, bit for
+    bit), through both phases of the mixed schedule."""
+    dims_list = [(4, 4, 4, 6) if k % 2 else (4, 4, 4, 4) for k in range(18)]
+    p = mcg.Params(tol=1e-10, max_sweeps=2000, check_every=25, fp32_sweeps=2000, fp32_tol=5e-11,
+                   fp32_overrelax=1.85, fp64_df=1)
+    Us = [synth.make_field(d, 0.5, 60 + k) for k, d in enumerate(dims_list)]
+    Ub = [pack(mcg, U, d) for U, d in zip(Us, dims_list)]
+    Gb = [mcg.identity_gauge(d) for d in dims_list]
+    rb = mcg.mcg_fix_batch(Ub, Gb, dims_list, p)
+    for k in (0, 1, 7, 16, 17):
+        d = dims_list[k]
+        Us1, Gs1 = pack(mcg, Us[k], d), mcg.identity_gauge(d)
+        r1 = mcg.mcg_fix(Us1, Gs1, d, p)
+        assert rb["sweeps"][k] == r1["sweeps"][0]
+        assert torch.equal(Ub[k], Us1) and torch.equal(Gb[k], Gs1)
+
+
 @pytest.mark.parametrize("nsmear,eps,rho", [(0, 1.0, 0.1), (4, 1.0, 0.1), (3, -0.25, 0.06)])
 def test_precondition_pipeline_parity(mcg, nsmear, eps, rho):
     dims = (4, 4, 4, 4)
