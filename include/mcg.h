@@ -19,6 +19,9 @@
  *    crosses this boundary.
  *  - The library allocates only internal scratch (device work buffers, pinned
  *    host staging), cached across calls and freed by mcg_release().
+ *  - That scratch, and the streams on which the relaxation captures its CUDA
+ *    graphs, belong to the device: calls for one device are made from one
+ *    host thread at a time (calls for different devices may run in parallel).
  *
  * LAYOUT (device, "even/odd SoA"), for a lattice Nx x Ny x Nz x Nt with every
  * extent even and >= 2, V = Nx Ny Nz Nt, Vh = V / 2:
