@@ -821,43 +821,86 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
     const int nodes_per_chunk = (chained ? nf : 1) * chunk * ((!DF && sizeof(T) == 8 && reunit_every > 0) ? 4 : 3);
     const int max_chunks = (phase_len + chunk - 1) / chunk + 1;
     int status = 0;
-    // phase timing (instrumentation): GPU time of the chunk graphs and the
-    // site-updates they performed
-    cudaEvent_t t0 = nullptr, t1 = nullptr;
-    const bool timed = cudaEventCreate(&t0) == cudaSuccess && cudaEventCreate(&t1) == cudaSuccess;
+    // The next chunk is launched before the host reads the state after the
+    // current one, so the GPU does not wait for the host between chunks: a
+    // field that is done makes every later kernel of its chain exit at entry,
+    // so a chunk launched after the last field finished sweeps nothing and the
+    // results are those of launching chunk by chunk.  The state after each
+    // chunk is copied to one of two pinned buffers.  Phase timing
+    // (instrumentation): GPU time of the chunk graphs and the site-updates
+    // they performed.
+    FieldState* h_ring = (FieldState*)scratch_host("fix.state2", sizeof(FieldState) * 2 * nf, &rc);
+    cudaEvent_t t0[2] = {nullptr, nullptr}, t1[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
+    bool evs = rc == 0;
+    for (int i = 0; i < 2 && evs; ++i)
+        evs = cudaEventCreate(&t0[i]) == cudaSuccess && cudaEventCreate(&t1[i]) == cudaSuccess &&
+              cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming) == cudaSuccess;
+    auto launch = [&](int c) -> cudaError_t {
+        const int b = c & 1;
+        cudaError_t e = cudaEventRecord(t0[b], stream);
+        if (e == cudaSuccess) e = cudaGraphLaunch(exec, stream);
+        if (e == cudaSuccess) e = cudaEventRecord(t1[b], stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_ring + (size_t)b * nf, d_state, sizeof(FieldState) * nf, cudaMemcpyDeviceToHost,
+                                stream);
+        if (e == cudaSuccess) e = cudaEventRecord(copied[b], stream);
+        if (e == cudaSuccess) note_launches(nodes_per_chunk);
+        return e;
+    };
     std::vector<int> sw0(nf);
     for (int f = 0; f < nf; ++f) sw0[f] = h_state[f].sweep;
-    for (int c = 0; c < max_chunks; ++c) {
-        if (timed) cudaEventRecord(t0, stream);
-        ce = cudaGraphLaunch(exec, stream);
-        if (ce != cudaSuccess) {
-            status = cuda_fail(ce, "cudaGraphLaunch");
-            break;
+    int in_flight = -1;  // a chunk launched after the last one read
+    if (!evs) {
+        status = rc ? rc : fail(MCG_CUDA_ERROR, "sweep chunk events");
+    } else if ((ce = launch(0)) != cudaSuccess) {
+        status = cuda_fail(ce, "cudaGraphLaunch");
+    }
+    for (int c = 0; status == 0 && c < max_chunks; ++c) {
+        const int b = c & 1;
+        in_flight = -1;
+        if (c + 1 < max_chunks) {
+            if ((ce = launch(c + 1)) != cudaSuccess) {
+                status = cuda_fail(ce, "cudaGraphLaunch");
+                break;
+            }
+            in_flight = c + 1;
         }
-        if (timed) cudaEventRecord(t1, stream);
-        note_launches(nodes_per_chunk);
-        ce = cudaMemcpyAsync(h_state, d_state, sizeof(FieldState) * nf, cudaMemcpyDeviceToHost, stream);
-        if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
-        if (ce != cudaSuccess) {
+        if ((ce = cudaEventSynchronize(copied[b])) != cudaSuccess) {
             status = cuda_fail(ce, "sweep chunk");
             break;
         }
-        if (timed) {
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, t0, t1);
-            long long su = 0;
-            for (int f = 0; f < nf; ++f) {
-                su += (long long)(h_state[f].sweep - sw0[f]) * 2LL * fields[f].geo.vh;
-                sw0[f] = h_state[f].sweep;
-            }
-            note_phase(prec, ms, su);
+        const FieldState* hs = h_ring + (size_t)b * nf;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t0[b], t1[b]);
+        long long su = 0;
+        for (int f = 0; f < nf; ++f) {
+            su += (long long)(hs[f].sweep - sw0[f]) * 2LL * fields[f].geo.vh;
+            sw0[f] = hs[f].sweep;
         }
+        note_phase(prec, ms, su);
         bool all = true;
-        for (int f = 0; f < nf; ++f) all = all && h_state[f].done != 0;
+        for (int f = 0; f < nf; ++f) all = all && hs[f].done != 0;
         if (all) break;
     }
-    if (t0) cudaEventDestroy(t0);
-    if (t1) cudaEventDestroy(t1);
+    // the chunk still in flight (if any) sweeps nothing once every field is
+    // done; its GPU time is counted with the phase
+    ce = cudaStreamSynchronize(stream);
+    if (ce != cudaSuccess && status == 0) status = cuda_fail(ce, "sweep chunk");
+    if (status == 0 && in_flight >= 0) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t0[in_flight & 1], t1[in_flight & 1]) == cudaSuccess) note_phase(prec, ms, 0);
+    }
+    // the caller's copy of the state after the phase
+    if (status == 0) {
+        ce = cudaMemcpyAsync(h_state, d_state, sizeof(FieldState) * nf, cudaMemcpyDeviceToHost, stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
+        if (ce != cudaSuccess) status = cuda_fail(ce, "sweep state");
+    }
+    for (int i = 0; i < 2; ++i) {
+        if (t0[i]) cudaEventDestroy(t0[i]);
+        if (t1[i]) cudaEventDestroy(t1[i]);
+        if (copied[i]) cudaEventDestroy(copied[i]);
+    }
     cudaGraphExecDestroy(exec);
     cudaGraphDestroy(graph);
     return status;
