@@ -536,20 +536,28 @@ struct Solver<double> {
 // which is the Newton step written without the residual b - (mu - A) a (the
 // two solves share one LDL^T and run interleaved).  Stops when the correction
 // is below 2e-6 or when the quadratic rate over the last two corrections puts
-// the next one below it.  Returns true with a normalised when the last
-// factorisation shows mu - A positive definite with pivots above 1e-5 of the
-// largest (mu >= lambda_max: the global maximum), false otherwise.
+// the next one below it.  Returns true with a normalised when the accepted
+// mu = mu_f + dmu (mu_f the multiplier of the last factorisation, dmu its
+// step) is shown to lie above lambda_max(A), which makes a the global maximum
+// (Sec. II.A): the pivots of mu_f - A are positive and above 1e-5 of the
+// largest, and a step down (dmu < 0) stays below the smallest eigenvalue of
+// mu_f - A with that margin.  The smallest eigenvalue is bounded from below
+// by 27 det / tr^3 (det the product of the pivots, tr the trace; the other
+// three eigenvalues have a product at most (tr / 3)^3).  Without the second
+// test a step that crosses lambda_max near the hard case (beta_top ~ 0) would
+// end on a stationary point that is not the maximum.  False otherwise.
 __device__ __forceinline__ bool kkt_newton_f32(const float (&A)[4][4], const float (&b)[4], float (&a)[4]) {
     const float conv = 2e-6f;
     a[0] = 1.f;
     a[1] = a[2] = a[3] = 0.f;
     float mu = A[0][0] + b[0];
-    float dprev = -1.f, dmin = 0.f, dabs = 0.f;
+    float dprev = -1.f, dmin = 0.f, dabs = 0.f, dmu_last = 0.f;
+    float D[4];
     bool ok = false;
 #pragma unroll 1
     for (int it = 0; it < 8; ++it) {
         // LDL^T of M = mu - A
-        float D[4], Dinv[4], L10, L20, L30, L21, L31, L32;
+        float Dinv[4], L10, L20, L30, L21, L31, L32;
         D[0] = mu - A[0][0];
         Dinv[0] = frcp(D[0]);
         L10 = -A[1][0] * Dinv[0];
@@ -592,6 +600,7 @@ __device__ __forceinline__ bool kkt_newton_f32(const float (&A)[4][4], const flo
         a[2] = n2;
         a[3] = n3;
         mu += dmu;
+        dmu_last = dmu;
         if (dmax <= conv || (dprev > 0.f && dmax * dmax * dmax <= conv * dprev * dprev)) {
             ok = true;
             break;
@@ -602,9 +611,14 @@ __device__ __forceinline__ bool kkt_newton_f32(const float (&A)[4][4], const flo
     const float inv = rsqrtf(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
 #pragma unroll
     for (int k = 0; k < 4; ++k) a[k] *= inv;
-    // certificate from the last factorisation (at mu - dmu, |dmu| far below
-    // the pivot margin)
-    return dmin > 1e-5f * dabs;
+    if (!(dmin > 1e-5f * dabs)) return false;
+    if (dmu_last < 0.f) {
+        const float mf = mu - dmu_last;
+        const float det = (D[0] * D[1]) * (D[2] * D[3]);
+        const float tr = ((mf - A[0][0]) + (mf - A[1][1])) + ((mf - A[2][2]) + (mf - A[3][3]));
+        return 27.f * det > (1e-5f * dabs - dmu_last) * (tr * tr * tr);
+    }
+    return true;
 }
 
 // FP32 fallback of the local solve (Jacobi + secular), out of line with its
