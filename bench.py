@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 # DRAM traffic of the dominant kernel per launch, from one ncu capture of a
 # full 20^3 x 40 launch (the profile named below); reported only while the
 # kernel source is the one that was profiled
-TRAFFIC_FP32 = {"bytes_per_launch": 79.12e6, "source_sha256_prefix": "f38cac6fe19988e4",
+TRAFFIC_FP32 = {"bytes_per_launch": 79.40e6, "source_sha256_prefix": "9ab9c476e101969d",
                 "profile": "profiles/k_halfsweep_c12_f32_20x20x20x40.md"}
 
 def fp32_kernel_fingerprint() -> str:
