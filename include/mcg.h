@@ -236,6 +236,26 @@ int mcg_fix(void* U, void* G, const mcg_lattice* lat, const mcg_params* params, 
             int* sweeps_out, double* R_hist, cudaStream_t stream);
 
 /*
+ * The local problem of one subgroup step of mcg_fix on its own, for n
+ * problems at once (Sec. II.A: with the SU(2) element written a0 + i a.sigma,
+ * |a| = 1, the site's share of R is a^T A a + 2 b.a + const; the step takes
+ * the global maximum over the sphere).  A: DEVICE, n row-major 4x4 FP64
+ * matrices (16 doubles each; only the upper triangle, column >= row, is read,
+ * A is taken symmetric).  b: DEVICE, n x 4 FP64.  a_out: DEVICE, n x 4 FP64,
+ * the maximisers.  fallback_out: DEVICE, n ints, or NULL: 1 where the solve
+ * left the warm-started Newton path for the Jacobi + secular one.
+ * precision MCG_F32: the solve of the FP32 and double-float sweeps (A and b
+ * rounded to FP32, Newton from a = e0 on the KKT system with its certificate
+ * that the multiplier lies above lambda_max(A), else FP32 Jacobi + secular);
+ * MCG_F64: the solve of the exact FP64 sweep.  In the hard case (b orthogonal
+ * to the top eigenspace, a maximum that is not unique) any maximiser may be
+ * returned.  n = 0 does nothing; n < 0, a null array (n > 0) or another
+ * precision return MCG_BAD_ARG.  Asynchronous on `stream`.
+ */
+int mcg_local_solve(const double* A, const double* b, double* a_out, int* fallback_out, int n, int precision,
+                    cudaStream_t stream);
+
+/*
  * Simulated annealing of the gauge transform: a Gribov-copy search variant
  * run ahead of mcg_fix (Sec. III.B names annealing as the route to higher maxima
  * taken in SU(2); the paper does not specify it, so this is the library's

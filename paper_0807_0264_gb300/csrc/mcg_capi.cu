@@ -577,6 +577,16 @@ int mcg_fix(void* U, void* G, const mcg_lattice* lat, const mcg_params* params, 
     return fix_impl(U, G, lat, g, params, R_out, sweeps_out, nullptr, R_hist, stream);
 }
 
+int mcg_local_solve(const double* A, const double* b, double* a_out, int* fallback_out, int n, int precision,
+                    cudaStream_t stream) {
+    NvtxRange nvtx_range_("mcg_local_solve");
+    if (n < 0) return fail(MCG_BAD_ARG, "n must be >= 0");
+    if (precision != MCG_F64 && precision != MCG_F32) return fail(MCG_BAD_ARG, "bad precision");
+    if (n == 0) return MCG_OK;
+    if (!A || !b || !a_out) return fail(MCG_BAD_ARG, "null pointer");
+    return launch_local_solve(A, b, a_out, fallback_out, n, precision, stream);
+}
+
 int mcg_anneal(void* U, void* G, const mcg_lattice* lat, const double* T, int nsweeps, long long first_sweep,
                int nhit, double eps, unsigned long long seed, long long* accepted_out, cudaStream_t stream) {
     NvtxRange nvtx_range_("mcg_anneal");

@@ -122,6 +122,12 @@ template <typename T>
 int time_halfsweep(void* U, void* G, const Geom& g, int parity, int nreps, int flush_l2, float* ms,
                    cudaStream_t stream);
 
+// n local problems (A16: n row-major 4x4 matrices, upper triangle read; b4:
+// n 4-vectors) solved on the device by the FP32 sweeps' solve (prec MCG_F32)
+// or the exact FP64 sweep's (MCG_F64): a4 the maximisers, fb (may be null) 1
+// where the solve left the Newton path.
+int launch_local_solve(const double* A16, const double* b4, double* a4, int* fb, int n, int prec, cudaStream_t st);
+
 // One FP64 half-sweep (exact local solve) of the sites of `parity` with
 // t_lo <= t < t_hi on one field; want_R: the odd-parity R partial of those
 // sites' 8 links to *R_host (synchronises).

@@ -1072,6 +1072,57 @@ int run_halfsweep_slab(void* U, void* G, const Geom& g, int parity, int t_lo, in
     return 0;
 }
 
+// One local problem per thread (the subgroup maximisation on its own): the
+// solve of the FP32 sweeps (A, b rounded to FP32; certified Newton, else the
+// FP32 Jacobi + secular path) or that of the exact FP64 sweep.
+__global__ void __launch_bounds__(128) k_local_solve(const double* __restrict__ A16, const double* __restrict__ b4,
+                                                     double* __restrict__ a4, int* __restrict__ fb, int n, int prec) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    double A[4][4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        b[i] = b4[4 * (size_t)k + i];
+#pragma unroll
+        for (int j = i; j < 4; ++j) A[i][j] = A[j][i] = A16[16 * (size_t)k + 4 * i + j];
+    }
+    double a[4];
+    int f = 0;
+    if (prec == MCG_F32) {
+        float Af[4][4], bf[4], af[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            bf[i] = (float)b[i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) Af[i][j] = (float)A[i][j];
+        }
+        if (!kkt_newton_f32(Af, bf, af)) {
+            const float4 r = solve_f32_fallback(Af[0][0], Af[0][1], Af[0][2], Af[0][3], Af[1][1], Af[1][2], Af[1][3],
+                                                Af[2][2], Af[2][3], Af[3][3], bf[0], bf[1], bf[2], bf[3]);
+            af[0] = r.x;
+            af[1] = r.y;
+            af[2] = r.z;
+            af[3] = r.w;
+            f = 1;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = (double)af[i];
+    } else {
+        f = Solver<double>::solve(A, b, a);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a4[4 * (size_t)k + i] = a[i];
+    if (fb) fb[k] = f;
+}
+
+int launch_local_solve(const double* A16, const double* b4, double* a4, int* fb, int n, int prec, cudaStream_t st) {
+    if (n <= 0) return 0;
+    k_local_solve<<<(n + 127) / 128, 128, 0, st>>>(A16, b4, a4, fb, n, prec);
+    MCG_CK(cudaGetLastError());
+    note_launches(1);
+    return 0;
+}
+
 template int time_halfsweep<float>(void*, void*, const Geom&, int, int, int, float*, cudaStream_t);
 template int time_halfsweep<double>(void*, void*, const Geom&, int, int, int, float*, cudaStream_t);
 

@@ -86,6 +86,15 @@ __device__ __forceinline__ void jacobi4(T (&S)[4][4], T (&V)[4][4], int max_swee
 
 // Trust-region maximiser from the eigen-decomposition (al, V columns).
 // Returns 0 easy case, 1 hard case.  mu_out is the multiplier.
+// The secular equation n(d) = 1, n(d)^2 = sum_i beta_i^2 / (d + g_i)^2, is
+// solved for the offset d = mu - al_max > 0 with g_i = al_max - al_i (0 on the
+// top eigenspace), so that d keeps its relative precision when it is tiny (a
+// weight beta_top near zero: near the hard case).  Newton on 1/n(d) - 1, which
+// is concave and increasing in d (the Moré-Sorensen form), climbs
+// monotonically to the root from any point where n >= 1: from d = |beta_top|,
+// or, when the other eigendirections alone have n >= 1 at d = 0 (then the
+// root lies beyond theirs), from the root of their equation, solved first the
+// same way.  Without that start a tiny beta_top makes every step tiny.
 template <typename T>
 __device__ __forceinline__ int trs_from_eigen(const T (&S)[4][4], const T (&V)[4][4], const T (&b)[4], T (&a)[4],
                                               T& mu_out) {
@@ -113,92 +122,115 @@ __device__ __forceinline__ int trs_from_eigen(const T (&S)[4][4], const T (&V)[4
             amax = al[i];
             imax = i;
         }
-    T beta[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) beta[i] = V[0][i] * b[0] + V[1][i] * b[1] + V[2][i] * b[2] + V[3][i] * b[3];
-    T btop2 = T(0);
+    T beta[4], gap[4];
+    T btop2 = T(0), pn2 = T(0);
     bool top[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        top[i] = (amax - al[i]) <= deg_tol * scale;
-        if (top[i]) btop2 += beta[i] * beta[i];
+        beta[i] = V[0][i] * b[0] + V[1][i] * b[1] + V[2][i] * b[2] + V[3][i] * b[3];
+        gap[i] = amax - al[i];
+        top[i] = gap[i] <= deg_tol * scale;
+        if (top[i]) {
+            gap[i] = T(0);
+            btop2 += beta[i] * beta[i];
+        } else {
+            const T c = fdiv(beta[i], gap[i]);
+            pn2 += c * c;
+        }
     }
     const T btop = fsqrt(btop2);
-    if (btop <= hard_tol * scale) {
-        T coef[4], pn2 = T(0);
+    if (btop <= hard_tol * scale && pn2 < T(1)) {
+        // hard case: the partial solution plus the top eigenvector, its
+        // largest component positive, filling the unit norm
+        T vm[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            coef[i] = top[i] ? T(0) : fdiv(beta[i], amax - al[i]);
-            pn2 += coef[i] * coef[i];
+        for (int k = 0; k < 4; ++k) {
+            vm[k] = V[k][0];
+#pragma unroll
+            for (int i = 1; i < 4; ++i)
+                if (i == imax) vm[k] = V[k][i];
         }
-        if (pn2 < T(1)) {
-            T vm[4];
+        int kb = 0;
+        T vb = fabs(vm[0]);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                vm[k] = V[k][0];
-#pragma unroll
-                for (int i = 1; i < 4; ++i)
-                    if (i == imax) vm[k] = V[k][i];
+        for (int k = 1; k < 4; ++k)
+            if (fabs(vm[k]) > vb) {
+                vb = fabs(vm[k]);
+                kb = k;
             }
-            int kb = 0;
-            T vb = fabs(vm[0]);
+        T sgn = T(1);
 #pragma unroll
-            for (int k = 1; k < 4; ++k)
-                if (fabs(vm[k]) > vb) {
-                    vb = fabs(vm[k]);
-                    kb = k;
-                }
-            T sgn = T(1);
+        for (int k = 0; k < 4; ++k)
+            if (k == kb) sgn = vm[k] >= T(0) ? T(1) : T(-1);
+        const T t = fsqrt(T(1) - pn2) * sgn;
+        T coef[4], n2 = T(0);
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (k == kb) sgn = vm[k] >= T(0) ? T(1) : T(-1);
-            const T t = fsqrt(T(1) - pn2) * sgn;
-            T n2 = T(0);
+        for (int i = 0; i < 4; ++i) coef[i] = top[i] ? T(0) : fdiv(beta[i], gap[i]);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                a[k] = V[k][0] * coef[0] + V[k][1] * coef[1] + V[k][2] * coef[2] + V[k][3] * coef[3] + t * vm[k];
-                n2 += a[k] * a[k];
-            }
-            const T inv = rsqrt(n2);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) a[k] *= inv;
-            mu_out = amax;
-            return 1;
+        for (int k = 0; k < 4; ++k) {
+            a[k] = V[k][0] * coef[0] + V[k][1] * coef[1] + V[k][2] * coef[2] + V[k][3] * coef[3] + t * vm[k];
+            n2 += a[k] * a[k];
         }
+        const T inv = rsqrt(n2);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a[k] *= inv;
+        mu_out = amax;
+        return 1;
     }
-    // easy case: root of ||a(mu)|| = 1 right of amax, bracket [amax+btop, amax+||b||]
-    T lo = amax + btop, hi = amax + bn, mu = lo;
     const int maxit = sizeof(T) == 8 ? 100 : 40;
+    // easy case: the root d lies in [btop, bn] (n >= 1 at btop from the top
+    // weights alone, n <= 1 at bn)
+    T lo = btop, hi = bn, d = btop;
+    if (pn2 >= T(1)) {
+        T dr = T(0);
+#pragma unroll 1
+        for (int it = 0; it < maxit; ++it) {
+            T s2 = T(0), s3 = T(0);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (top[i]) continue;
+                const T r = frcp(dr + gap[i]);
+                const T q = beta[i] * beta[i] * r * r;
+                s2 += q;
+                s3 += q * r;
+            }
+            if (!(s3 > T(0))) break;
+            const T step = fdiv((fsqrt(s2) - T(1)) * s2, s3);
+            dr += step;
+            if (!(step > T(4) * eps * dr)) break;
+        }
+        d = fmax(d, fmin(dr, hi));
+    }
 #pragma unroll 1
     for (int it = 0; it < maxit; ++it) {
         T s2 = T(0), s3 = T(0);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            // a zero weight contributes nothing (also when mu sits on al[i])
+            // a zero weight contributes nothing (also where d + gap is 0)
             if (beta[i] == T(0)) continue;
-            const T r = frcp(mu - al[i]);
+            const T r = frcp(d + gap[i]);
             const T q = beta[i] * beta[i] * r * r;
             s2 += q;
             s3 += q * r;
         }
         const T n = fsqrt(s2);
         if (n >= T(1))
-            lo = fmax(lo, mu);
+            lo = fmax(lo, d);
         else
-            hi = fmin(hi, mu);
-        T next = mu + fdiv((n - T(1)) * s2, s3);
+            hi = fmin(hi, d);
+        T next = d + fdiv((n - T(1)) * s2, s3);
         if (!(next > lo && next < hi)) next = T(0.5) * (lo + hi);
-        if (fabs(next - mu) <= T(4) * eps * fabs(mu)) {
-            mu = next;
+        if (fabs(next - d) <= T(4) * eps * d) {
+            d = next;
             break;
         }
-        mu = next;
-        if (hi - lo <= T(4) * eps * fabs(mu)) break;
+        d = next;
+        if (hi - lo <= T(4) * eps * d) break;
     }
     T n2 = T(0);
     T coef[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) coef[i] = beta[i] == T(0) ? T(0) : fdiv(beta[i], mu - al[i]);
+    for (int i = 0; i < 4; ++i) coef[i] = beta[i] == T(0) ? T(0) : fdiv(beta[i], d + gap[i]);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         a[k] = V[k][0] * coef[0] + V[k][1] * coef[1] + V[k][2] * coef[2] + V[k][3] * coef[3];
@@ -207,7 +239,7 @@ __device__ __forceinline__ int trs_from_eigen(const T (&S)[4][4], const T (&V)[4
     const T inv = rsqrt(n2);
 #pragma unroll
     for (int k = 0; k < 4; ++k) a[k] *= inv;
-    mu_out = mu;
+    mu_out = amax + d;
     return 0;
 }
 
@@ -257,19 +289,23 @@ __device__ __forceinline__ void ldlt4_solve(const T (&L)[4][4], const T (&Dinv)[
 
 // Newton iterations on (mu - A) a = b, |a| = 1 starting from a = (1,0,0,0)
 // (the current links, i.e. no change) with mu its Lagrange estimate.  On
-// success (converged, and mu - A positive definite: the global maximum of the
-// trust-region subproblem) returns true with a normalised, mu, and the LDL^T
-// factors of (mu - A) for later use.
+// convergence returns true with a normalised, mu, and the LDL^T factors of
+// (mu_f - A), mu_f the multiplier of the last factorisation (mu = mu_f plus
+// the last step), with pd its smallest pivot relative to the largest.  That mu
+// is above lambda_max(A) (a the global maximum of the trust-region
+// subproblem) is for the caller to certify: see above_lambda_max.
 template <typename T>
 __device__ __forceinline__ bool kkt_newton(const T (&A)[4][4], const T (&b)[4], T (&a)[4], T& mu, T (&L)[4][4],
-                                           T (&Dinv)[4], T& pd) {
+                                           T (&Dinv)[4], T& pd, T& mu_f) {
     const T conv = sizeof(T) == 8 ? T(1e-13) : T(2e-6);
     a[0] = T(1);
     a[1] = a[2] = a[3] = T(0);
     mu = A[0][0] + b[0];
+    mu_f = mu;
     bool ok = false;
 #pragma unroll 1
     for (int it = 0; it < 8; ++it) {
+        mu_f = mu;
         T M[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -303,9 +339,22 @@ __device__ __forceinline__ bool kkt_newton(const T (&A)[4][4], const T (&b)[4], 
     const T inv = rsqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
 #pragma unroll
     for (int k = 0; k < 4; ++k) a[k] *= inv;
-    // certificate: mu - A positive definite.  The factorization of the last
-    // step (at mu - dmu, with |dmu| far below the pivot margin) serves.
     return pd > (sizeof(T) == 8 ? T(1e-12) : T(1e-5));
+}
+
+// Certificate that a multiplier mu lies above lambda_max(A) by more than
+// margin times the trace of mu_f - A, given the inverse pivots Dinv of the
+// LDL^T of the positive definite matrix mu_f - A: its smallest eigenvalue is
+// at least 27 det / tr^3 (det the product of the pivots, tr the trace; the
+// other three eigenvalues have a product of at most (tr / 3)^3), so
+// lambda_max(A) <= mu_f - 27 det / tr^3.
+template <typename T>
+__device__ __forceinline__ bool above_lambda_max(const T (&A)[4][4], const T (&Dinv)[4], T mu_f, double mu,
+                                                 double margin) {
+    const double det = 1.0 / (((double)Dinv[0] * (double)Dinv[1]) * ((double)Dinv[2] * (double)Dinv[3]));
+    const double tr = (((double)mu_f - A[0][0]) + ((double)mu_f - A[1][1])) +
+                      (((double)mu_f - A[2][2]) + ((double)mu_f - A[3][3]));
+    return (mu - (double)mu_f) + 27.0 * det / (tr * tr * tr) > margin * tr;
 }
 
 // FP32 solve of the subproblem given A (symmetric) and b (Jacobi + secular;
@@ -398,7 +447,8 @@ struct Solver;
 // FP64 refinement with the FP32 LDL^T factors of (mu32 - A) as the fixed
 // approximate inverse (same iteration as kkt_refine).
 __device__ __forceinline__ bool kkt_refine_ldlt(const double (&A)[4][4], const double (&b)[4], const float (&L)[4][4],
-                                                const float (&Dinv)[4], const float (&af)[4], float muf, double (&a)[4]) {
+                                                const float (&Dinv)[4], const float (&af)[4], float muf, double (&a)[4],
+                                                double& mu_out) {
     float yf[4];
     ldlt4_solve(L, Dinv, af, yf);
     double y[4];
@@ -434,6 +484,7 @@ __device__ __forceinline__ bool kkt_refine_ldlt(const double (&A)[4][4], const d
             dmax = fmax(dmax, fabs(da));
         }
         mu += dmu;
+        mu_out = mu;
         if (!(dmax == dmax)) return false;
         if (dmax <= 1e-12) return true;
     }
@@ -509,11 +560,14 @@ struct Solver<double> {
         }
         bool ok = false;
         {
-            float L[4][4], Dinv[4], pd;
+            float L[4][4], Dinv[4], pd, mu_f;
             // warm-started FP32 Newton; the refinement contracts by ~cond * 1e-7,
-            // with cond ~ 1 / pd bounded by the pivot test
-            if (kkt_newton<float>(Af, bf, af, muf, L, Dinv, pd) && pd > 2e-4f)
-                ok = kkt_refine_ldlt(A, b, L, Dinv, af, muf, a);
+            // with cond ~ 1 / pd bounded by the pivot test.  Certificate: the
+            // refined multiplier above lambda_max of the FP32 copy of A by 1e-6
+            // of the trace of mu_f - A (far above the FP32 rounding of A)
+            double mu = 0.0;
+            if (kkt_newton<float>(Af, bf, af, muf, L, Dinv, pd, mu_f) && pd > 2e-4f)
+                ok = kkt_refine_ldlt(A, b, L, Dinv, af, muf, a, mu) && above_lambda_max(Af, Dinv, mu_f, mu, 1e-6);
         }
         if (!ok) {
             const Vec4d r = solve_f64_fallback(A[0][0], A[0][1], A[0][2], A[0][3], A[1][1], A[1][2], A[1][3],

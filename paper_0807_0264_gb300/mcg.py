@@ -87,6 +87,7 @@ def _load() -> ctypes.CDLL:
         "mcg_smear": ([P, P, L, D, D, I, P], I),
         "mcg_fix": ([P, P, L, PR, P, P, P, P], I),
         "mcg_anneal": ([P, P, L, P, I, ctypes.c_longlong, I, D, ctypes.c_ulonglong, P, P], I),
+        "mcg_local_solve": ([P, P, P, P, I, I, P], I),
         "mcg_center_project": ([P, P, P, L, P], I),
         "mcg_vortex_remove": ([P, P, P, P, L, P], I),
         "mcg_wilson_loops": ([P, L, I, I, P, P], I),
@@ -130,7 +131,7 @@ EXPORTS = ("mcg_version", "mcg_last_error", "mcg_release", "mcg_pack_links", "mc
            "mcg_gribov_search", "mcg_smear_backward_step", "mcg_functional_matrix_grad", "mcg_grad_R",
            "mcg_ascent_step", "mcg_vortex_remove", "mcg_wilson_loops",
            "mcg_wilson_loops_offaxis", "mcg_anneal", "mcg_phase_stats",
-           "mcg_halfsweep_slab", "mcg_slab_face", "mcg_bounds_violations", "mcg_probe_peaks")
+           "mcg_halfsweep_slab", "mcg_slab_face", "mcg_bounds_violations", "mcg_probe_peaks", "mcg_local_solve")
 
 
 def library() -> ctypes.CDLL:
@@ -400,6 +401,24 @@ def mcg_anneal(U: torch.Tensor, G: torch.Tensor, dims, T, nhit: int = 4, eps: fl
                                          _stream(stream)))
     hits = len(T) * 3 * int(nhit) * 2 * vh_of(dims)
     return dict(accepted=list(acc), acceptance=[a / hits if hits else 0.0 for a in acc])
+
+
+def mcg_local_solve(A: torch.Tensor, b: torch.Tensor, precision: int = F64, stream=None):
+    """Maximise a^T A a + 2 b.a over the unit sphere for a batch of local
+    problems (the subgroup step of the relaxation, Sec. II.A) with the solve of
+    the FP32 sweeps (precision F32) or of the exact FP64 sweep (F64).  A: (n, 4,
+    4) float64 CUDA tensor (upper triangle read), b: (n, 4).  Returns (a (n, 4)
+    float64, fallback (n,) int32: 1 where the Newton path gave way to Jacobi +
+    secular)."""
+    _need_cuda(A, b)
+    if A.dtype != torch.float64 or b.dtype != torch.float64 or A.shape[1:] != (4, 4) or b.shape != (A.shape[0], 4):
+        raise ValueError("A must be (n, 4, 4) and b (n, 4), float64")
+    n = A.shape[0]
+    a = torch.empty((n, 4), dtype=torch.float64, device=A.device)
+    fb = torch.empty((n,), dtype=torch.int32, device=A.device)
+    _check("mcg_local_solve", _lib.mcg_local_solve(_ptr(A), _ptr(b), _ptr(a), _ptr(fb), int(n), int(precision),
+                                                   _stream(stream)))
+    return a, fb
 
 
 def mcg_vortex_remove(U: torch.Tensor, Z: torch.Tensor, dims, removed: bool = True, center: bool = True,

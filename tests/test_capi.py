@@ -213,3 +213,20 @@ def test_slab_face_validation_without_gpu(mcg):
     inside = ctypes.c_void_p((1 << 20) + 4096)
     code(lib.mcg_slab_face(U, inside, ctypes.byref(good), 0, 0, 0, None), 3, "overlaps")
     code(lib.mcg_slab_face(U, buf, ctypes.byref(mcg.lattice((4, 3, 4, 6))), 0, 0, 0, None), 2, "")
+
+
+def test_local_solve_validation_without_gpu(mcg):
+    """The batched local solve checks its count, precision and pointers on the
+    host; n = 0 is a no-op that touches no device memory."""
+    lib = mcg.library()
+    one = ctypes.c_void_p(1 << 20)
+
+    def code(rc, want, why):
+        assert rc == want, rc
+        assert why.encode() in lib.mcg_last_error(), lib.mcg_last_error()
+
+    code(lib.mcg_local_solve(one, one, one, None, -1, mcg.F64, None), 3, "n must be")
+    code(lib.mcg_local_solve(one, one, one, None, 4, 2, None), 3, "precision")
+    code(lib.mcg_local_solve(None, one, one, None, 4, mcg.F32, None), 3, "null")
+    code(lib.mcg_local_solve(one, one, None, None, 4, mcg.F64, None), 3, "null")
+    assert lib.mcg_local_solve(None, None, None, None, 0, mcg.F32, None) == 0
