@@ -54,6 +54,12 @@ RHO = 0.1
 # from 1.85 to 1.93) on this workload converged every level only at 1.9 and
 # 1.92 (the others leave one to four levels creeping)
 OMEGA = float(os.environ.get("MCG_OMEGA", "1.9"))
+# restart of a field's FP32 phase (from the call's input, with the next
+# over-relaxation of omega -+ k * 0.03) once it has run this many sweeps
+# without reaching fp32_tol: converging phases on these workloads take 2 000 to
+# ~10 000 sweeps, the creeping (trap) ones run on to the cap
+RESTART = int(os.environ.get("MCG_FP32_RESTART", "10000"))
+RESTART_DOMEGA = float(os.environ.get("MCG_RESTART_DOMEGA", "0.03"))
 
 
 def hbm_peak():
@@ -349,7 +355,8 @@ def run_gribov(args, mcg, dev, rank):
     print(f"gribov: generated {len(Us)} fields in {t_gen:.1f} s", file=sys.stderr, flush=True)
     nconf_tot = c
     p = mcg.Params(tol=1e-10, max_sweeps=20000, check_every=25, reunit_every=50, fp32_sweeps=20000, fp32_tol=5e-11,
-                   fp32_window=25, fp32_overrelax=OMEGA, fp64_solve32=1)
+                   fp32_window=25, fp32_overrelax=OMEGA, fp64_solve32=1, fp32_restart=RESTART,
+                   fp32_restart_domega=RESTART_DOMEGA)
     tune = mcg.autotune_schedule(Us, dims_list, p, trial_sweeps=20, chunks=(25, 50))
     print(f"gribov: autotuned {tune['block']} x {tune['check_every']}", file=sys.stderr, flush=True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -588,7 +595,8 @@ def mixed_error_block(args, mcg, U, dims, levels, mixed, dev):
     handoff = mcg.Params(tol=1e300, max_sweeps=mixed.max_sweeps, check_every=mixed.check_every,
                          reunit_every=mixed.reunit_every, fp32_sweeps=mixed.fp32_sweeps, fp32_tol=mixed.fp32_tol,
                          fp32_window=mixed.fp32_window, fp32_overrelax=mixed.fp32_overrelax,
-                         fp64_solve32=mixed.fp64_solve32, fp64_df=mixed.fp64_df)
+                         fp64_solve32=mixed.fp64_solve32, fp64_df=mixed.fp64_df, fp32_restart=mixed.fp32_restart,
+                         fp32_restart_domega=mixed.fp32_restart_domega)
 
     def compare(F):
         """F (device, FP64) -> hand-off H in place; finishes from H compared."""
@@ -745,7 +753,8 @@ def main():
              "f64": mcg.autotune_sweep_block(U_warm.clone(), dims, reps=3)}
     mixed = mcg.Params(tol=1e-10, max_sweeps=30000, check_every=25, reunit_every=50, fp32_sweeps=30000,
                        fp32_tol=float(os.environ.get("MCG_FP32_TOL", "5e-11")), fp32_window=25,
-                       fp32_overrelax=OMEGA, fp64_solve32=1, fp64_df=int(os.environ.get("MCG_FP64_DF", "1")))
+                       fp32_overrelax=OMEGA, fp64_solve32=1, fp64_df=int(os.environ.get("MCG_FP64_DF", "1")),
+                       fp32_restart=RESTART, fp32_restart_domega=RESTART_DOMEGA)
     stream = torch.cuda.current_stream(dev)
 
     def step(params, smear_prec):
@@ -1006,7 +1015,9 @@ def main():
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": config_of(args, f"batched levels, FP32 smearing, FP32 sweeps (over-relaxed, omega="
                                           f"{mixed.fp32_overrelax}, until the 25-sweep mean dV_U < "
-                                          f"{mixed.fp32_tol:g}) then FP64-class plain relaxation ("
+                                          f"{mixed.fp32_tol:g}; a field still running after "
+                                          f"{mixed.fp32_restart} sweeps restarts from its input with omega -+ k*"
+                                          f"{mixed.fp32_restart_domega:g}) then FP64-class plain relaxation ("
                                           + ("double-float moves, local 4x4 solve in FP32, transform applied in "
                                              "FP64" if mixed.fp64_df else
                                              "local 4x4 solve in FP32, G normalised and applied in FP64")
@@ -1021,6 +1032,7 @@ def main():
                         "converged": all(r["status"] == 0 for r in mixed_res),
                         "per_level": [{"n_smear": n, "sweeps_smeared": r["sweeps_smeared"],
                                        "sweeps_fixed": r["sweeps_fixed"], "sweeps_fp32": r["sweeps_fp32"],
+                                       "fp32_restarts": r["fp32_restarts"],
                                        "converged": r["status"] == 0} for n, r in zip(levels, mixed_res)]},
                 "roofline": roof, "cpu_baseline": cpu, "autotune": tuned,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": canon_pinned.numel() * 16,

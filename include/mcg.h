@@ -106,6 +106,18 @@ typedef struct {
                        /* in FP64 and applied to the FP64 links at the end, so */
                        /* the result is exactly on its gauge orbit.  GB300     */
                        /* runs FP64 at ~1/60 of its FP32 rate.  0 = FP64.      */
+    int fp32_restart;  /* FP32 phase: a field that has run this many sweeps   */
+                       /* since its last (re)start without reaching fp32_tol  */
+                       /* restarts the phase from the call's input links and  */
+                       /* the identity transform with the next              */
+                       /* over-relaxation of omega - d, omega + d, omega - 2d, */
+                       /* omega + 2d, ... (d = fp32_restart_domega; no restart */
+                       /* once it leaves (0, 2)); its sweeps keep counting     */
+                       /* toward fp32_sweeps.  0 = off.  Not part of the      */
+                       /* paper's method: a way out of the slow, creeping     */
+                       /* approach to a lower maximum that some over-relaxed  */
+                       /* trajectories take.                                  */
+    double fp32_restart_domega; /* >= 0 */
 } mcg_params;
 
 /* One field of a heterogeneous batch: device pointers to its links and its
@@ -129,6 +141,8 @@ typedef struct {
     int sweeps_fp32;       /* of those, sweeps run in the FP32 phase           */
     int status;            /* this field's (level's) fixes: MCG_OK when both    */
                            /* converged, else MCG_NOT_CONVERGED                 */
+    int fp32_restarts;     /* restarts of the FP32 phase in this level's fixes */
+                           /* (mcg_params.fp32_restart)                         */
 } mcg_precond_result;
 
 /*

@@ -241,6 +241,8 @@ static int check_params(const mcg_params* p) {
     if (p->fp32_sweeps > 0 && (p->fp32_window < 1 || p->fp32_window > 31))
         return fail(MCG_BAD_ARG, "fp32_window must be in 1..31");
     if (!(p->tol == p->tol)) return fail(MCG_BAD_ARG, "tol is NaN");
+    if (p->fp32_restart < 0 || !(p->fp32_restart_domega >= 0.0 && p->fp32_restart_domega < 2.0))
+        return fail(MCG_BAD_ARG, "fp32_restart must be >= 0 and fp32_restart_domega in [0, 2)");
     return 0;
 }
 
@@ -257,7 +259,8 @@ struct FieldSpec {
 // MCG relaxation of a batch of fields (all of one precision, any sizes), one
 // launch per half-sweep for the whole batch.
 static int fix_fields(const std::vector<FieldSpec>& fs, int prec, const mcg_params* prm, double* R_out,
-                      int* sweeps_out, int* sweeps32_out, double* R_hist, cudaStream_t st, int* converged_out = nullptr) {
+                      int* sweeps_out, int* sweeps32_out, double* R_hist, cudaStream_t st, int* converged_out = nullptr,
+                      int* restarts_out = nullptr) {
     const int nf = (int)fs.size();
     int rc = 0;
     FieldState* d_state = (FieldState*)scratch_device("fix.state", sizeof(FieldState) * nf, &rc);
@@ -310,9 +313,24 @@ static int fix_fields(const std::vector<FieldSpec>& fs, int prec, const mcg_para
             if ((rc = launch_identity_c12(fds[f].G, fs[f].g, 1, st))) return rc;
         }
         const int cap = std::min(prm->fp32_sweeps, prm->max_sweeps);
+        // restarts from this call's input: the FP64 links are untouched until
+        // the hand-off
+        std::vector<int> nrs(nf, 0);
+        PhaseRestart rs;
+        rs.after = prm->fp32_restart;
+        rs.domega = prm->fp32_restart_domega;
+        rs.count = nrs.data();
+        rs.reset = [&](int f, cudaStream_t s) -> int {
+            int r = launch_to_c12(fs[f].U, MCG_F64, fds[f].U, fs[f].g, 4, 1, s);
+            if (!r) r = launch_identity_c12(fds[f].G, fs[f].g, 1, s);
+            return r;
+        };
         rc = run_fix_phase<float>(fds, d_state, h_state, d_hist, hist_len, prm->fp32_tol, prm->fp32_window,
-                                  prm->fp32_overrelax, 0, cap, prm->check_every, true, st);
+                                  prm->fp32_overrelax, 0, cap, prm->check_every, true, st, false,
+                                  prm->fp32_restart > 0 ? &rs : nullptr);
         if (rc) return rc;
+        if (restarts_out)
+            for (int f = 0; f < nf; ++f) restarts_out[f] = nrs[f];
         for (int f = 0; f < nf; ++f) s32[f] = h_state[f].sweep;
         // hand-off: FP64 re-unitarised transform applied to the FP64 links
         for (int f = 0; f < nf; ++f)
@@ -404,7 +422,8 @@ static int fix_fields(const std::vector<FieldSpec>& fs, int prec, const mcg_para
 
 // uniform batch: nfields fields of lat's dims stored back to back
 static int fix_impl(void* U, void* G, const mcg_lattice* lat, const Geom& g, const mcg_params* prm, double* R_out,
-                    int* sweeps_out, int* sweeps32_out, double* R_hist, cudaStream_t st, int* converged_out = nullptr) {
+                    int* sweeps_out, int* sweeps32_out, double* R_hist, cudaStream_t st, int* converged_out = nullptr,
+                    int* restarts_out = nullptr) {
     const size_t eb = elem_bytes(lat->precision);
     std::vector<FieldSpec> fs(lat->nfields);
     for (int f = 0; f < lat->nfields; ++f) {
@@ -412,7 +431,8 @@ static int fix_impl(void* U, void* G, const mcg_lattice* lat, const Geom& g, con
         fs[f].G = (char*)G + eb * gauge_elems(g) * f;
         fs[f].g = g;
     }
-    return fix_fields(fs, lat->precision, prm, R_out, sweeps_out, sweeps32_out, R_hist, st, converged_out);
+    return fix_fields(fs, lat->precision, prm, R_out, sweeps_out, sweeps32_out, R_hist, st, converged_out,
+                      restarts_out);
 }
 
 // validate one entry of an mcg_field array
@@ -686,7 +706,7 @@ int mcg_precondition_fix(void* U, void* G, int8_t* Z, const mcg_lattice* lat, co
     const size_t le = link_elems(g), ge = gauge_elems(g), eb = elem_bytes(prec);
     std::vector<double> plaq_in(nf), plaq_out(nf), Rs(nf, 0.0), Rf(nf);
     std::vector<int> sw_s(nf, 0), sw_f(nf), sw32_s(nf, 0), sw32_f(nf, 0);
-    std::vector<int> conv_s(nf, 1), conv_f(nf, 1);
+    std::vector<int> conv_s(nf, 1), conv_f(nf, 1), rs_s(nf, 0), rs_f(nf, 0);
     std::vector<long long> counts(7 * (size_t)nf);
     if ((rc = compute_plaquette(U, prec, g, nf, plaq_in.data(), stream))) return rc;
     int status = MCG_OK;
@@ -713,7 +733,8 @@ int mcg_precondition_fix(void* U, void* G, int8_t* Z, const mcg_lattice* lat, co
         if ((rc = launch_convert(S, smear_precision, Sp, prec, le * nf, stream))) return rc;
         if (smear_precision != prec && (rc = launch_reunitarise(Sp, 0, prec, g, nf, stream))) return rc;
         if ((rc = launch_identity_gauge(W, prec, g, nf, stream))) return rc;
-        rc = fix_impl(Sp, W, lat, g, params, Rs.data(), sw_s.data(), sw32_s.data(), nullptr, stream, conv_s.data());
+        rc = fix_impl(Sp, W, lat, g, params, Rs.data(), sw_s.data(), sw32_s.data(), nullptr, stream, conv_s.data(),
+                      rs_s.data());
         if (rc != MCG_OK && rc != MCG_NOT_CONVERGED) return rc;
         if (rc == MCG_NOT_CONVERGED) status = MCG_NOT_CONVERGED;
         // G <- reunit(W), then U <- U^G (the preconditioning transform)
@@ -722,7 +743,8 @@ int mcg_precondition_fix(void* U, void* G, int8_t* Z, const mcg_lattice* lat, co
         if ((rc = launch_apply_gauge(U, G, prec, g, nf, stream))) return rc;
     }
     // fix the preconditioned original field, accumulating into G
-    rc = fix_impl(U, G, lat, g, params, Rf.data(), sw_f.data(), sw32_f.data(), nullptr, stream, conv_f.data());
+    rc = fix_impl(U, G, lat, g, params, Rf.data(), sw_f.data(), sw32_f.data(), nullptr, stream, conv_f.data(),
+                  rs_f.data());
     if (rc != MCG_OK && rc != MCG_NOT_CONVERGED) return rc;
     if (rc == MCG_NOT_CONVERGED) status = MCG_NOT_CONVERGED;
     int8_t* Zb = Z;
@@ -744,6 +766,7 @@ int mcg_precondition_fix(void* U, void* G, int8_t* Z, const mcg_lattice* lat, co
         r.sweeps_fixed = sw_f[f];
         r.sweeps_fp32 = sw32_s[f] + sw32_f[f];
         r.status = (conv_s[f] && conv_f[f]) ? MCG_OK : MCG_NOT_CONVERGED;
+        r.fp32_restarts = rs_s[f] + rs_f[f];
     }
     return status;
 }
@@ -877,6 +900,7 @@ int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_o
     std::vector<double> Rs(std::max(ns, 1), 0.0), Rf(nlevels);
     std::vector<int> sw_s(std::max(ns, 1), 0), sw32_s(std::max(ns, 1), 0), sw_f(nlevels), sw32_f(nlevels);
     std::vector<int> conv_s(std::max(ns, 1), 1), conv_f(nlevels, 1);
+    std::vector<int> rs_s(std::max(ns, 1), 0), rs_f(nlevels, 0);
     int status = MCG_OK;
     // every level starts from the input field and the identity transform
     for (int l = 0; l < nlevels; ++l)
@@ -923,8 +947,8 @@ int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_o
         const int n1 = (int)b1.size();
         std::vector<double> R1(n1);
         std::vector<int> s1(n1), s321(n1);
-        std::vector<int> c1(n1, 1);
-        rc = fix_fields(b1, prec, params, R1.data(), s1.data(), s321.data(), nullptr, stream, c1.data());
+        std::vector<int> c1(n1, 1), r1(n1, 0);
+        rc = fix_fields(b1, prec, params, R1.data(), s1.data(), s321.data(), nullptr, stream, c1.data(), r1.data());
         if (rc != MCG_OK && rc != MCG_NOT_CONVERGED) return rc;
         if (rc == MCG_NOT_CONVERGED) status = MCG_NOT_CONVERGED;
         for (int k = 0; k < ns; ++k) {
@@ -932,6 +956,7 @@ int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_o
             sw_s[k] = s1[k];
             sw32_s[k] = s321[k];
             conv_s[k] = c1[k];
+            rs_s[k] = r1[k];
         }
         for (size_t j = 0; j < plain_levels.size(); ++j) {
             const int l = plain_levels[j];
@@ -939,6 +964,7 @@ int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_o
             sw_f[l] = s1[ns + j];
             sw32_f[l] = s321[ns + j];
             conv_f[l] = c1[ns + j];
+            rs_f[l] = r1[ns + j];
         }
     }
     if (ns > 0) {
@@ -952,8 +978,8 @@ int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_o
         }
         std::vector<double> R2(ns);
         std::vector<int> s2(ns), s322(ns);
-        std::vector<int> c2(ns, 1);
-        rc = fix_fields(b2, prec, params, R2.data(), s2.data(), s322.data(), nullptr, stream, c2.data());
+        std::vector<int> c2(ns, 1), r2(ns, 0);
+        rc = fix_fields(b2, prec, params, R2.data(), s2.data(), s322.data(), nullptr, stream, c2.data(), r2.data());
         if (rc != MCG_OK && rc != MCG_NOT_CONVERGED) return rc;
         if (rc == MCG_NOT_CONVERGED) status = MCG_NOT_CONVERGED;
         for (int k = 0; k < ns; ++k) {
@@ -961,6 +987,7 @@ int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_o
             sw_f[smeared[k]] = s2[k];
             sw32_f[smeared[k]] = s322[k];
             conv_f[smeared[k]] = c2[k];
+            rs_f[smeared[k]] = r2[k];
         }
     }
     int8_t* Zb = Z_out;
@@ -987,6 +1014,7 @@ int mcg_precondition_levels(const void* U, void* U_out, void* G_out, int8_t* Z_o
         r.sweeps_fixed = sw_f[l];
         r.sweeps_fp32 = (k >= 0 ? sw32_s[k] : 0) + sw32_f[l];
         r.status = ((k < 0 || conv_s[k]) && conv_f[l]) ? MCG_OK : MCG_NOT_CONVERGED;
+        r.fp32_restarts = (k >= 0 ? rs_s[k] : 0) + rs_f[l];
     }
     return status;
 }

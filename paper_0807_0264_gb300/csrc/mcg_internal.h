@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <functional>
+
 #include <string>
 #include <vector>
 
@@ -69,6 +71,7 @@ struct FieldDesc {
     void* Glo = nullptr;  // then hold the hi parts), compact layout
     int t_lo = 0;         // FP64 half-sweep: only sites with t_lo <= t < t_hi
     int t_hi = 1 << 30;   // (a t-slab of a decomposed lattice)
+    double omega = 1.0;   // FP32 (compact) sweeps: this field's over-relaxation
 };
 
 // Tag of the double-float sweep phase in run_fix_phase<T> (T = float: compact
@@ -105,14 +108,37 @@ struct SweepBatch {
     int solve32;   // FP64 sweeps: local problem built and solved in FP32
 };
 
+// Restarts of the FP32 (compact) phase: a field that has run `after` sweeps
+// since its last (re)start without stopping gets its working copies reset by
+// reset(f, stream) (enqueued on the phase's stream) and continues with the
+// over-relaxation omega_k of its k-th restart, k = 1, 2, ...: omega - d,
+// omega + d, omega - 2d, omega + 2d, ... (d = domega); no restart once
+// omega_k leaves (0, 2).  Its sweeps keep counting toward the phase's cap.
+// count (nf entries, may be null): restarts per field.
+struct PhaseRestart {
+    int after = 0;
+    double domega = 0.0;
+    std::function<int(int, cudaStream_t)> reset;
+    int* count = nullptr;
+};
+
+// Over-relaxation of a field's k-th restart (k = 0: the phase's own), or a
+// value outside (0, 2) when there is none.
+inline double restart_omega(double omega, double domega, int k) {
+    const int m = (k + 1) / 2;
+    return omega + (k % 2 ? -1.0 : 1.0) * m * domega;
+}
+
 // Run MCG relaxation on a batch (all fields same precision T) until every
 // field is done: converged (dV_U < tol) or at abs_cap sweeps counted from the
 // start of the history.  `fresh`: start a new history (sweep = 0); otherwise
-// continue the sweep count in `state` (a new phase).  Returns 0 or an error.
+// continue the sweep count in `state` (a new phase).  restart (T = float
+// only, may be null): see PhaseRestart.  Returns 0 or an error.
 template <typename T>
 int run_fix_phase(const std::vector<FieldDesc>& fields, FieldState* d_state, FieldState* h_state, double* d_hist,
                   int hist_len, double tol, int window, double omega, int reunit_every, int abs_cap,
-                  int check_every, bool fresh, cudaStream_t stream, bool solve32 = false);
+                  int check_every, bool fresh, cudaStream_t stream, bool solve32 = false,
+                  const PhaseRestart* restart = nullptr);
 
 // Time `nreps` launches of one half-sweep kernel (parity 1 includes the fused
 // R reduction) on a single field, each bracketed by CUDA events on `stream`;

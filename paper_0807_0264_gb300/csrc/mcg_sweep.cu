@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <type_traits>
 #include <vector>
@@ -679,7 +680,7 @@ constexpr int kMaxChains = 16;
 template <typename T>
 int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, FieldState* h_state, double* d_hist,
                   int hist_len, double tol, int window, double omega, int reunit_every, int abs_cap,
-                  int check_every, bool fresh, cudaStream_t stream, bool solve32) {
+                  int check_every, bool fresh, cudaStream_t stream, bool solve32, const PhaseRestart* restart) {
     constexpr bool DF = std::is_same<T, DoubleFloat>::value;
     const int prec = (DF || sizeof(T) == 8) ? MCG_F64 : MCG_F32;
     const int NT = DF ? df_threads() : sweep_block(prec);
@@ -690,8 +691,10 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
     for (auto& fd : fields) {
         fd.nblk = (fd.geo.vh + SPB - 1) / SPB;
         fd.blk0 = total;
+        fd.omega = omega;
         total += fd.nblk;
     }
+    const bool restarts = restart && restart->after > 0 && std::is_same<T, float>::value;
     int rc = 0;
     FieldDesc* d_desc = (FieldDesc*)scratch_device("fix.desc", sizeof(FieldDesc) * nf, &rc);
     if (rc) return rc;
@@ -770,8 +773,10 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
     std::vector<cudaStream_t> bs(nf);
     std::vector<cudaEvent_t> be(nf);
     cudaEvent_t fork = nullptr;
-    if (chained) {
-        FieldDesc* d_single = (FieldDesc*)scratch_device("fix.desc1", sizeof(FieldDesc) * nf, &rc);
+    // each field as a batch of one (the chains, and the R of a restarted field)
+    FieldDesc* d_single = nullptr;
+    if (chained || restarts) {
+        d_single = (FieldDesc*)scratch_device("fix.desc1", sizeof(FieldDesc) * nf, &rc);
         if (rc) return rc;
         FieldDesc* h_single = (FieldDesc*)scratch_host("fix.desc1", sizeof(FieldDesc) * nf, &rc);
         if (rc) return rc;
@@ -791,7 +796,7 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
             b.R_hist = d_hist ? d_hist + (size_t)f * hist_len : nullptr;
             chains.push_back(b);
         }
-        if (branch_streams(nf, bs.data(), be.data(), &fork, &rc)) return rc;
+        if (chained && branch_streams(nf, bs.data(), be.data(), &fork, &rc)) return rc;
     }
     MCG_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
     // no early return while the capture is open: the first error ends it
@@ -849,6 +854,39 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
     };
     std::vector<int> sw0(nf);
     for (int f = 0; f < nf; ++f) sw0[f] = h_state[f].sweep;
+    // restarts: each field's restarts, the first chunk whose state read
+    // follows its last reset, and a pinned slot per field for the
+    // over-relaxation written to its descriptors.  A field's (re)start is its
+    // state's phase_start.
+    std::vector<int> nrestart(nf, 0), valid_from(nf, 0);
+    double* h_omega = nullptr;
+    if (restarts) {
+        h_omega = (double*)scratch_host("fix.restart.omega", sizeof(double) * nf, &rc);
+        if (rc) status = rc;
+    }
+    // enqueue the reset of field f after the chunk in flight (stream order)
+    auto restart_field = [&](int f, double om) -> int {
+        int r = restart->reset(f, stream);
+        if (r) return r;
+        h_omega[f] = om;
+        const size_t off = offsetof(FieldDesc, omega);
+        cudaError_t e = cudaMemcpyAsync((char*)(d_desc + f) + off, h_omega + f, sizeof(double),
+                                        cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync((char*)(d_single + f) + off, h_omega + f, sizeof(double), cudaMemcpyHostToDevice,
+                                stream);
+        if (e != cudaSuccess) return cuda_fail(e, "restart descriptors");
+        // R of the reset field and a new phase start for it (its sweep count
+        // goes on)
+        if constexpr (std::is_same<T, float>::value) {
+            k_functional<T><<<fields[f].nblk, SPB, 0, stream>>>(chains[f]);
+            k_finalize<<<1, 256, 0, stream>>>(chains[f], 2);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(e, "restart");
+            note_launches(2);
+        }
+        return 0;
+    };
     int in_flight = -1;  // a chunk launched after the last one read
     if (!evs) {
         status = rc ? rc : fail(MCG_CUDA_ERROR, "sweep chunk events");
@@ -879,9 +917,31 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
         }
         note_phase(prec, ms, su);
         bool all = true;
-        for (int f = 0; f < nf; ++f) all = all && hs[f].done != 0;
+        for (int f = 0; f < nf; ++f) {
+            if (c < valid_from[f]) {
+                all = false;  // a reset is pending behind the chunk read here
+                continue;
+            }
+            if (restarts && hs[f].done == 0 && hs[f].sweep - hs[f].phase_start >= restart->after) {
+                const double om = restart_omega(omega, restart->domega, nrestart[f] + 1);
+                if (om > 0.0 && om < 2.0 && in_flight == c + 1) {
+                    if ((rc = restart_field(f, om))) {
+                        status = rc;
+                        break;
+                    }
+                    ++nrestart[f];
+                    valid_from[f] = c + 2;
+                    all = false;
+                    continue;
+                }
+            }
+            all = all && hs[f].done != 0;
+        }
+        if (status) break;
         if (all) break;
     }
+    if (restarts && restart->count)
+        for (int f = 0; f < nf; ++f) restart->count[f] = nrestart[f];
     // the chunk still in flight (if any) sweeps nothing once every field is
     // done; its GPU time is counted with the phase
     ce = cudaStreamSynchronize(stream);
@@ -1127,11 +1187,12 @@ template int time_halfsweep<float>(void*, void*, const Geom&, int, int, int, flo
 template int time_halfsweep<double>(void*, void*, const Geom&, int, int, int, float*, cudaStream_t);
 
 template int run_fix_phase<float>(const std::vector<FieldDesc>&, FieldState*, FieldState*, double*, int, double,
-                                  int, double, int, int, int, bool, cudaStream_t, bool);
+                                  int, double, int, int, int, bool, cudaStream_t, bool, const PhaseRestart*);
 template int run_fix_phase<DoubleFloat>(const std::vector<FieldDesc>&, FieldState*, FieldState*, double*, int,
-                                        double, int, double, int, int, int, bool, cudaStream_t, bool);
+                                        double, int, double, int, int, int, bool, cudaStream_t, bool,
+                                        const PhaseRestart*);
 template int run_fix_phase<double>(const std::vector<FieldDesc>&, FieldState*, FieldState*, double*, int, double,
-                                   int, double, int, int, int, bool, cudaStream_t, bool);
+                                   int, double, int, int, int, bool, cudaStream_t, bool, const PhaseRestart*);
 
 // index-check counter of this unit (MCG_CHECK builds)
 MCG_BOUND_READER(bound_hits_sweep)

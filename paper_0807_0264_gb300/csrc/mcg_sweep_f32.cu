@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(NT, MINB) k_halfsweep_c12(SweepBatch bt, int p
         for (int mu = 0; mu < 4; ++mu) c12_load(U + c12_lidx(g, mu, parity, 0, s), vh, m[mu]);
         cp_async_wait_all();
 
-        const float omega = (float)bt.omega;
+        const float omega = (float)fd.omega;
         fb += c12_subgroup_step<0, 1, 2, NT>(m, bst, wstage, omega);
         fb += c12_subgroup_step<0, 2, 1, NT>(m, bst, wstage, omega);
         fb += c12_subgroup_step<1, 2, 0, NT>(m, bst, wstage, omega);

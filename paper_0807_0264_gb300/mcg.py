@@ -43,7 +43,8 @@ class mcg_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_sweeps", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("reunit_every", ctypes.c_int), ("fp32_sweeps", ctypes.c_int), ("fp32_tol", ctypes.c_double),
                 ("fp32_window", ctypes.c_int), ("fp32_overrelax", ctypes.c_double),
-                ("fp64_solve32", ctypes.c_int), ("fp64_df", ctypes.c_int)]
+                ("fp64_solve32", ctypes.c_int), ("fp64_df", ctypes.c_int), ("fp32_restart", ctypes.c_int),
+                ("fp32_restart_domega", ctypes.c_double)]
 
 
 class mcg_field(ctypes.Structure):
@@ -54,7 +55,8 @@ class mcg_precond_result(ctypes.Structure):
     _fields_ = [("V_smeared", ctypes.c_double), ("V_fixed", ctypes.c_double), ("plaquette_in", ctypes.c_double),
                 ("plaquette_out", ctypes.c_double), ("vortices", ctypes.c_longlong),
                 ("vortex_density", ctypes.c_double), ("sweeps_smeared", ctypes.c_int),
-                ("sweeps_fixed", ctypes.c_int), ("sweeps_fp32", ctypes.c_int), ("status", ctypes.c_int)]
+                ("sweeps_fixed", ctypes.c_int), ("sweeps_fp32", ctypes.c_int), ("status", ctypes.c_int),
+                ("fp32_restarts", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -158,11 +160,14 @@ class Params:
     fp32_overrelax: float = 1.0
     fp64_solve32: int = 0
     fp64_df: int = 0
+    fp32_restart: int = 0
+    fp32_restart_domega: float = 0.0
 
     def c(self) -> mcg_params:
         return mcg_params(self.tol, self.max_sweeps, self.check_every, self.reunit_every, self.fp32_sweeps,
                           self.fp32_tol, self.fp32_window, self.fp32_overrelax,
-                          int(self.fp64_solve32), int(self.fp64_df))
+                          int(self.fp64_solve32), int(self.fp64_df), int(self.fp32_restart),
+                          float(self.fp32_restart_domega))
 
 
 def lattice(dims, nfields: int = 1, precision: int = F64) -> mcg_lattice:

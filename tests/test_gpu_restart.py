@@ -1,0 +1,88 @@
+"""Restarts of the FP32 phase (mcg_params.fp32_restart): a field that has not
+reached fp32_tol after `fp32_restart` sweeps since its (re)start begins the
+phase again from the call's input with the next over-relaxation of the
+sequence omega - d, omega + d, omega - 2d, ...  The restarted phase is a fresh
+run with that over-relaxation: the same links and transform bit for bit, its
+sweeps added to those before the restart.  Per-field arithmetic does not
+depend on the batch, so a field restarted inside a batch (per-field chains
+up to 16 fields, one launch per half-sweep above) ends as it does alone."""
+import numpy as np
+import pytest
+
+from paper_0807_0264_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mcg():
+    from paper_0807_0264_gb300 import mcg as m
+
+    return m
+
+
+def params(mcg, omega, restart=0, domega=0.0):
+    # d = 0.15 from omega = 1.9: one restart (omega 1.75), then 2.05 is out of
+    # (0, 2) and the field carries on
+    return mcg.Params(tol=1e-10, max_sweeps=6000, check_every=10, reunit_every=50, fp32_sweeps=6000, fp32_tol=5e-11,
+                      fp32_window=25, fp32_overrelax=omega, fp64_df=1, fp32_restart=restart,
+                      fp32_restart_domega=domega)
+
+
+def packed(mcg, U, dims):
+    return mcg.mcg_pack_links(torch.from_numpy(U).unsqueeze(0).cuda(), dims)
+
+
+def test_restarted_phase_is_a_fresh_run_with_the_next_omega(mcg):
+    dims = (6, 4, 4, 6)
+    U = synth.make_field(dims, 0.5, 12)
+    Ur, Gr = packed(mcg, U, dims), mcg.identity_gauge(dims)
+    rr = mcg.mcg_precondition_fix(Ur, Gr, dims, params(mcg, 1.9, restart=30, domega=0.15))[0]
+    Uf, Gf = packed(mcg, U, dims), mcg.identity_gauge(dims)
+    rf = mcg.mcg_precondition_fix(Uf, Gf, dims, params(mcg, 1.75))[0]
+    assert rr["fp32_restarts"] == 1 and rf["fp32_restarts"] == 0
+    assert rr["status"] == 0 and rf["status"] == 0
+    assert torch.equal(Ur, Uf) and torch.equal(Gr, Gf)
+    assert rr["V_fixed"] == rf["V_fixed"]
+    # the sweeps before the restart: the first chunk boundary at or past 30,
+    # plus the chunk already in flight when it was read
+    pre = rr["sweeps_fixed"] - rf["sweeps_fixed"]
+    assert pre == rr["sweeps_fp32"] - rf["sweeps_fp32"]
+    assert 30 <= pre <= 50, pre
+
+
+@pytest.mark.parametrize("nfields", [3, 18])
+def test_restart_inside_a_batch_equals_the_field_alone(mcg, nfields):
+    """3 fields: per-field chains (restart descriptors of the chain); 18
+    fields: one launch per half-sweep for the batch (the batch's
+    descriptors).  Each field is compared with its own restarted run."""
+    dims_list = [(4, 4, 4, 6) if k % 2 else (4, 4, 4, 4) for k in range(nfields)]
+    Us = [synth.make_field(d, 0.5, 70 + k) for k, d in enumerate(dims_list)]
+    p = params(mcg, 1.9, restart=30, domega=0.15)
+    Ub = [packed(mcg, U, d) for U, d in zip(Us, dims_list)]
+    Gb = [mcg.identity_gauge(d) for d in dims_list]
+    rb = mcg.mcg_fix_batch(Ub, Gb, dims_list, p)
+    for k in sorted({0, 1, nfields // 2, nfields - 1}):
+        d = dims_list[k]
+        U1, G1 = packed(mcg, Us[k], d), mcg.identity_gauge(d)
+        r1 = mcg.mcg_fix(U1, G1, d, p)
+        assert rb["sweeps"][k] == r1["sweeps"][0]
+        assert torch.equal(Ub[k], U1) and torch.equal(Gb[k], G1)
+    # the restart took place: field 0 ends elsewhere without it
+    U0, G0 = packed(mcg, Us[0], dims_list[0]), mcg.identity_gauge(dims_list[0])
+    mcg.mcg_fix(U0, G0, dims_list[0], params(mcg, 1.9))
+    assert not torch.equal(Ub[0], U0)
+
+
+def test_restart_off_changes_nothing(mcg):
+    """fp32_restart = 0 (the default) is the schedule without restarts, bit
+    for bit, whatever fp32_restart_domega says."""
+    dims = (4, 4, 4, 6)
+    U = synth.make_field(dims, 0.5, 5)
+    a, ga = packed(mcg, U, dims), mcg.identity_gauge(dims)
+    ra = mcg.mcg_fix(a, ga, dims, params(mcg, 1.9))
+    b, gb = packed(mcg, U, dims), mcg.identity_gauge(dims)
+    rb = mcg.mcg_fix(b, gb, dims, params(mcg, 1.9, restart=0, domega=0.3))
+    assert ra["sweeps"] == rb["sweeps"] and torch.equal(a, b) and torch.equal(ga, gb)
