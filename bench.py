@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 # DRAM traffic of the dominant kernel per launch, from one ncu capture of a
 # full 20^3 x 40 launch (the profile named below); reported only while the
 # kernel source is the one that was profiled
-TRAFFIC_FP32 = {"bytes_per_launch": 79.40e6, "source_sha256_prefix": "9ab9c476e101969d",
+TRAFFIC_FP32 = {"bytes_per_launch": 79.17e6, "source_sha256_prefix": "4c98a7ce6c5570b0",
                 "profile": "profiles/k_halfsweep_c12_f32_20x20x20x40.md"}
 
 def fp32_kernel_fingerprint() -> str:
@@ -54,12 +54,13 @@ RHO = 0.1
 # from 1.85 to 1.93) on this workload converged every level only at 1.9 and
 # 1.92 (the others leave one to four levels creeping)
 OMEGA = float(os.environ.get("MCG_OMEGA", "1.9"))
-# restart of a field's FP32 phase (from the call's input, with the next
-# over-relaxation of omega -+ k * 0.03) once it has run this many sweeps
-# without reaching fp32_tol: converging phases on these workloads take 2 000 to
-# ~10 000 sweeps, the creeping (trap) ones run on to the cap
+# restart of a field's FP32 phase once it has run this many sweeps without
+# reaching fp32_tol, from a random gauge copy of its input with the next
+# over-relaxation of omega -+ k * 0.03: converging phases on these workloads
+# take 2 000 to ~10 000 sweeps, the creeping (trap) ones run on to the cap
 RESTART = int(os.environ.get("MCG_FP32_RESTART", "10000"))
 RESTART_DOMEGA = float(os.environ.get("MCG_RESTART_DOMEGA", "0.03"))
+RESTART_RANDOM = int(os.environ.get("MCG_RESTART_RANDOM", "1"))
 
 
 def hbm_peak():
@@ -356,7 +357,7 @@ def run_gribov(args, mcg, dev, rank):
     nconf_tot = c
     p = mcg.Params(tol=1e-10, max_sweeps=20000, check_every=25, reunit_every=50, fp32_sweeps=20000, fp32_tol=5e-11,
                    fp32_window=25, fp32_overrelax=OMEGA, fp64_solve32=1, fp32_restart=RESTART,
-                   fp32_restart_domega=RESTART_DOMEGA)
+                   fp32_restart_domega=RESTART_DOMEGA, fp32_restart_random=RESTART_RANDOM)
     tune = mcg.autotune_schedule(Us, dims_list, p, trial_sweeps=20, chunks=(25, 50))
     print(f"gribov: autotuned {tune['block']} x {tune['check_every']}", file=sys.stderr, flush=True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -596,7 +597,8 @@ def mixed_error_block(args, mcg, U, dims, levels, mixed, dev):
                          reunit_every=mixed.reunit_every, fp32_sweeps=mixed.fp32_sweeps, fp32_tol=mixed.fp32_tol,
                          fp32_window=mixed.fp32_window, fp32_overrelax=mixed.fp32_overrelax,
                          fp64_solve32=mixed.fp64_solve32, fp64_df=mixed.fp64_df, fp32_restart=mixed.fp32_restart,
-                         fp32_restart_domega=mixed.fp32_restart_domega)
+                         fp32_restart_domega=mixed.fp32_restart_domega,
+                         fp32_restart_random=mixed.fp32_restart_random)
 
     def compare(F):
         """F (device, FP64) -> hand-off H in place; finishes from H compared."""
@@ -754,7 +756,8 @@ def main():
     mixed = mcg.Params(tol=1e-10, max_sweeps=30000, check_every=25, reunit_every=50, fp32_sweeps=30000,
                        fp32_tol=float(os.environ.get("MCG_FP32_TOL", "5e-11")), fp32_window=25,
                        fp32_overrelax=OMEGA, fp64_solve32=1, fp64_df=int(os.environ.get("MCG_FP64_DF", "1")),
-                       fp32_restart=RESTART, fp32_restart_domega=RESTART_DOMEGA)
+                       fp32_restart=RESTART, fp32_restart_domega=RESTART_DOMEGA,
+                       fp32_restart_random=RESTART_RANDOM)
     stream = torch.cuda.current_stream(dev)
 
     def step(params, smear_prec):
@@ -1016,7 +1019,9 @@ def main():
                 "config": config_of(args, f"batched levels, FP32 smearing, FP32 sweeps (over-relaxed, omega="
                                           f"{mixed.fp32_overrelax}, until the 25-sweep mean dV_U < "
                                           f"{mixed.fp32_tol:g}; a field still running after "
-                                          f"{mixed.fp32_restart} sweeps restarts from its input with omega -+ k*"
+                                          f"{mixed.fp32_restart} sweeps restarts from "
+                                          + ("a random gauge copy of " if mixed.fp32_restart_random else "")
+                                          + f"its input with omega -+ k*"
                                           f"{mixed.fp32_restart_domega:g}) then FP64-class plain relaxation ("
                                           + ("double-float moves, local 4x4 solve in FP32, transform applied in "
                                              "FP64" if mixed.fp64_df else

@@ -118,7 +118,17 @@ typedef struct {
                        /* approach to a lower maximum that some over-relaxed  */
                        /* trajectories take.                                  */
     double fp32_restart_domega; /* >= 0 */
+    int fp32_restart_random; /* 1: the k-th restart begins from a random gauge */
+                       /* copy of the field it restarts from: the Haar-random */
+                       /* transform W0 of mcg_random_gauge(seed =             */
+                       /* MCG_RESTART_SEED, seq = k) is applied to the call's */
+                       /* FP64 links and left-multiplies its transform G (the */
+                       /* output stays U_out = G_out U_in).  0: from the same */
+                       /* links.                                               */
 } mcg_params;
+
+/* Seed of the random gauge copies of mcg_params.fp32_restart_random. */
+#define MCG_RESTART_SEED 0x4D434752ull
 
 /* One field of a heterogeneous batch: device pointers to its links and its
  * gauge transform (layout above) and its dims. */
@@ -268,6 +278,20 @@ int mcg_fix(void* U, void* G, const mcg_lattice* lat, const mcg_params* params, 
  */
 int mcg_local_solve(const double* A, const double* b, double* a_out, int* fallback_out, int n, int precision,
                     cudaStream_t stream);
+
+/*
+ * Haar-random gauge transforms (a random Gribov copy U -> G U G^dag(x+mu)
+ * with mcg_apply_gauge; Gribov copies: Sec. I and II.B): G(x) in
+ * SU(3) for every site x of each of lat->nfields fields (FP64 only; the same
+ * matrices in every field).  Site x (lexicographic, x0 fastest) draws
+ * Philox4x64-10 (Salmon et al., SC'11) at counters (x, seq, j, 0), j = 0..2,
+ * under key (seed, 0x52414E44); u = (w >> 11) 2^-53; Box-Muller on the pairs
+ * (1 - u_2i, u_2i+1) gives two complex Gaussian rows, Gram-Schmidt rows 0
+ * and 1, row 2 = conj(row0 x row1).  Asynchronous on `stream`.  MCG_BAD_ARG
+ * for MCG_F32 fields or a NULL G.
+ */
+int mcg_random_gauge(void* G, const mcg_lattice* lat, unsigned long long seed, unsigned long long seq,
+                     cudaStream_t stream);
 
 /*
  * Simulated annealing of the gauge transform: a Gribov-copy search variant

@@ -243,6 +243,8 @@ static int check_params(const mcg_params* p) {
     if (!(p->tol == p->tol)) return fail(MCG_BAD_ARG, "tol is NaN");
     if (p->fp32_restart < 0 || !(p->fp32_restart_domega >= 0.0 && p->fp32_restart_domega < 2.0))
         return fail(MCG_BAD_ARG, "fp32_restart must be >= 0 and fp32_restart_domega in [0, 2)");
+    if (p->fp32_restart_random != 0 && p->fp32_restart_random != 1)
+        return fail(MCG_BAD_ARG, "fp32_restart_random must be 0 or 1");
     return 0;
 }
 
@@ -320,8 +322,23 @@ static int fix_fields(const std::vector<FieldSpec>& fs, int prec, const mcg_para
         rs.after = prm->fp32_restart;
         rs.domega = prm->fp32_restart_domega;
         rs.count = nrs.data();
-        rs.reset = [&](int f, cudaStream_t s) -> int {
-            int r = launch_to_c12(fs[f].U, MCG_F64, fds[f].U, fs[f].g, 4, 1, s);
+        void* W0 = nullptr;
+        if (prm->fp32_restart > 0 && prm->fp32_restart_random) {
+            size_t ge_max = 0;
+            for (const auto& f : fs) ge_max = std::max(ge_max, gauge_elems(f.g));
+            W0 = scratch_device("fix.restart.W0", 16 * ge_max, &rc);
+            if (rc) return rc;
+        }
+        rs.reset = [&](int f, int k, cudaStream_t s) -> int {
+            int r = 0;
+            if (W0) {
+                // a random gauge copy of the field: W0 applied to the FP64
+                // links, the call's transform left-multiplied by it
+                r = launch_random_gauge(W0, fs[f].g, 1, MCG_RESTART_SEED, (unsigned long long)k, s);
+                if (!r) r = launch_apply_gauge(fs[f].U, W0, MCG_F64, fs[f].g, 1, s);
+                if (!r) r = launch_gauge_left_mul(fs[f].G, W0, fs[f].g, 1, s);
+            }
+            if (!r) r = launch_to_c12(fs[f].U, MCG_F64, fds[f].U, fs[f].g, 4, 1, s);
             if (!r) r = launch_identity_c12(fds[f].G, fs[f].g, 1, s);
             return r;
         };
@@ -605,6 +622,17 @@ int mcg_local_solve(const double* A, const double* b, double* a_out, int* fallba
     if (n == 0) return MCG_OK;
     if (!A || !b || !a_out) return fail(MCG_BAD_ARG, "null pointer");
     return launch_local_solve(A, b, a_out, fallback_out, n, precision, stream);
+}
+
+int mcg_random_gauge(void* G, const mcg_lattice* lat, unsigned long long seed, unsigned long long seq,
+                     cudaStream_t stream) {
+    NvtxRange nvtx_range_("mcg_random_gauge");
+    Geom g;
+    int rc = check_lat(lat, &g);
+    if (rc) return rc;
+    if (!G) return fail(MCG_BAD_ARG, "null pointer");
+    if (lat->precision != MCG_F64) return fail(MCG_BAD_ARG, "mcg_random_gauge takes FP64 fields");
+    return launch_random_gauge(G, g, lat->nfields, seed, seq, stream);
 }
 
 int mcg_anneal(void* U, void* G, const mcg_lattice* lat, const double* T, int nsweeps, long long first_sweep,

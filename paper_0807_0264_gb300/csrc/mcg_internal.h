@@ -108,9 +108,17 @@ struct SweepBatch {
     int solve32;   // FP64 sweeps: local problem built and solved in FP32
 };
 
+// Haar-random SU(3) transforms (FP64 gauge layout, the same in each of the
+// nfields; Philox4x64-10 with key (seed, 0x52414E44), counter (x, seq, j, 0)),
+// and G <- W G per site (FP64; W one field).
+int launch_random_gauge(void* G, const Geom& g, int nfields, unsigned long long seed, unsigned long long seq,
+                        cudaStream_t st);
+int launch_gauge_left_mul(void* G, const void* W, const Geom& g, int nfields, cudaStream_t st);
+
 // Restarts of the FP32 (compact) phase: a field that has run `after` sweeps
 // since its last (re)start without stopping gets its working copies reset by
-// reset(f, stream) (enqueued on the phase's stream) and continues with the
+// reset(f, k, stream) (k its restart count, from 1; enqueued on the phase's
+// stream) and continues with the
 // over-relaxation omega_k of its k-th restart, k = 1, 2, ...: omega - d,
 // omega + d, omega - 2d, omega + 2d, ... (d = domega); no restart once
 // omega_k leaves (0, 2).  Its sweeps keep counting toward the phase's cap.
@@ -118,7 +126,7 @@ struct SweepBatch {
 struct PhaseRestart {
     int after = 0;
     double domega = 0.0;
-    std::function<int(int, cudaStream_t)> reset;
+    std::function<int(int, int, cudaStream_t)> reset;
     int* count = nullptr;
 };
 

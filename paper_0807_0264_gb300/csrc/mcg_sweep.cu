@@ -320,6 +320,131 @@ __device__ __forceinline__ void philox4x64_10(unsigned long long (&c)[4], unsign
 // top 53 bits -> [0, 1), exact
 __device__ __forceinline__ double unit_interval(unsigned long long w) { return (double)(w >> 11) * 0x1p-53; }
 
+// Haar-random SU(3) matrix of the site with lexicographic index x: Philox4x64-10
+// at counters (x, seq, j, 0), j = 0, 1, 2, under key (seed, 0x52414E44) gives
+// twelve numbers u in [0, 1); Box-Muller on the pairs (1 - u_2i, u_2i+1)
+// gives twelve standard normals, the real and imaginary parts of two complex
+// Gaussian rows z0, z1.  Gram-Schmidt makes them rows 0 and 1 of a Haar
+// unitary matrix; row 2 = conj(row0 x row1) sets det = 1.
+__device__ __noinline__ void haar_su3_site(unsigned long long x, unsigned long long seed, unsigned long long seq,
+                                           cplx<double>* m) {
+    double u[12];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        unsigned long long c[4] = {x, seq, (unsigned long long)j, 0ull};
+        philox4x64_10(c, seed, 0x52414E44ull);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) u[4 * j + q] = unit_interval(c[q]);
+    }
+    double n[12];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const double r = sqrt(-2.0 * log(1.0 - u[2 * i]));
+        double sn, cs;
+        sincospi(2.0 * u[2 * i + 1], &sn, &cs);
+        n[2 * i] = r * cs;
+        n[2 * i + 1] = r * sn;
+    }
+    cplx<double> r0[3], r1[3];
+    double n0 = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        r0[k] = mk(n[2 * k], n[2 * k + 1]);
+        r1[k] = mk(n[6 + 2 * k], n[6 + 2 * k + 1]);
+        n0 += r0[k].x * r0[k].x + r0[k].y * r0[k].y;
+    }
+    const double i0 = 1.0 / sqrt(n0);
+    // <r0, z1> = sum conj(r0_k) z1_k
+    double pr = 0.0, pi = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        r0[k] = mk(r0[k].x * i0, r0[k].y * i0);
+        pr += r0[k].x * r1[k].x + r0[k].y * r1[k].y;
+        pi += r0[k].x * r1[k].y - r0[k].y * r1[k].x;
+    }
+    double n1 = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        r1[k] = mk(r1[k].x - (pr * r0[k].x - pi * r0[k].y), r1[k].y - (pr * r0[k].y + pi * r0[k].x));
+        n1 += r1[k].x * r1[k].x + r1[k].y * r1[k].y;
+    }
+    const double i1 = 1.0 / sqrt(n1);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r1[k] = mk(r1[k].x * i1, r1[k].y * i1);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        m[k] = r0[k];
+        m[3 + k] = r1[k];
+        const int a = (k + 1) % 3, b = (k + 2) % 3;
+        // conj(r0_a r1_b - r0_b r1_a)
+        const double re = (r0[a].x * r1[b].x - r0[a].y * r1[b].y) - (r0[b].x * r1[a].x - r0[b].y * r1[a].y);
+        const double im = (r0[a].x * r1[b].y + r0[a].y * r1[b].x) - (r0[b].x * r1[a].y + r0[b].y * r1[a].x);
+        m[6 + k] = mk(re, -im);
+    }
+}
+
+// G (FP64, nfields transforms) <- Haar-random SU(3) per site, the same matrices
+// in every field (the counter holds the site, not the field)
+__global__ void __launch_bounds__(128) k_random_gauge(cplx<double>* __restrict__ G, Geom g, int nfields,
+                                                      unsigned long long seed, unsigned long long seq) {
+    const long long n = 2LL * g.vh * nfields;
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n) return;
+    const int f = (int)(id / (2LL * g.vh));
+    const int r = (int)(id - (long long)f * 2 * g.vh);
+    const int p = r / g.vh, s = r - p * g.vh;
+    int c[4];
+    eo_coords(g, p, s, c);
+    const unsigned long long x =
+        (unsigned long long)c[0] + (unsigned long long)g.n[0] * (c[1] + (unsigned long long)g.n[1] * (c[2] + (unsigned long long)g.n[2] * c[3]));
+    cplx<double> m[9];
+    haar_su3_site(x, seed, seq, m);
+    cplx<double>* Gf = G + (size_t)f * 18 * g.vh;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) Gf[gidx(g, p, e, s)] = m[e];
+}
+
+// G <- W G per site (FP64; W one field, applied to each of the nfields)
+__global__ void __launch_bounds__(128) k_gauge_left_mul(cplx<double>* __restrict__ G, const cplx<double>* __restrict__ W,
+                                                        Geom g, int nfields) {
+    const long long n = 2LL * g.vh * nfields;
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n) return;
+    const int f = (int)(id / (2LL * g.vh));
+    const int r = (int)(id - (long long)f * 2 * g.vh);
+    const int p = r / g.vh, s = r - p * g.vh;
+    cplx<double>* Gf = G + (size_t)f * 18 * g.vh;
+    cplx<double> a[9], b[9], o[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+        a[e] = W[gidx(g, p, e, s)];
+        b[e] = Gf[gidx(g, p, e, s)];
+    }
+    m3_mul(a, b, o);
+#pragma unroll
+    for (int e = 0; e < 9; ++e) Gf[gidx(g, p, e, s)] = o[e];
+}
+
+int launch_random_gauge(void* G, const Geom& g, int nfields, unsigned long long seed, unsigned long long seq,
+                        cudaStream_t st) {
+    const long long n = 2LL * g.vh * nfields;
+    if (n <= 0) return 0;
+    k_random_gauge<<<(unsigned)((n + 127) / 128), 128, 0, st>>>((cplx<double>*)G, g, nfields, seed, seq);
+    MCG_CK(cudaGetLastError());
+    note_launches(1);
+    return 0;
+}
+
+int launch_gauge_left_mul(void* G, const void* W, const Geom& g, int nfields, cudaStream_t st) {
+    const long long n = 2LL * g.vh * nfields;
+    if (n <= 0) return 0;
+    k_gauge_left_mul<<<(unsigned)((n + 127) / 128), 128, 0, st>>>((cplx<double>*)G, (const cplx<double>*)W, g,
+                                                                  nfields);
+    MCG_CK(cudaGetLastError());
+    note_launches(1);
+    return 0;
+}
+
 // a^T A a + 2 b^T a
 __device__ __forceinline__ double local_quadratic(const double (&A)[4][4], const double (&b)[4], const double (&a)[4]) {
     double f = 0.0;
@@ -866,7 +991,7 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
     }
     // enqueue the reset of field f after the chunk in flight (stream order)
     auto restart_field = [&](int f, double om) -> int {
-        int r = restart->reset(f, stream);
+        int r = restart->reset(f, nrestart[f] + 1, stream);
         if (r) return r;
         h_omega[f] = om;
         const size_t off = offsetof(FieldDesc, omega);

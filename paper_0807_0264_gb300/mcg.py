@@ -44,7 +44,7 @@ class mcg_params(ctypes.Structure):
                 ("reunit_every", ctypes.c_int), ("fp32_sweeps", ctypes.c_int), ("fp32_tol", ctypes.c_double),
                 ("fp32_window", ctypes.c_int), ("fp32_overrelax", ctypes.c_double),
                 ("fp64_solve32", ctypes.c_int), ("fp64_df", ctypes.c_int), ("fp32_restart", ctypes.c_int),
-                ("fp32_restart_domega", ctypes.c_double)]
+                ("fp32_restart_domega", ctypes.c_double), ("fp32_restart_random", ctypes.c_int)]
 
 
 class mcg_field(ctypes.Structure):
@@ -90,6 +90,7 @@ def _load() -> ctypes.CDLL:
         "mcg_fix": ([P, P, L, PR, P, P, P, P], I),
         "mcg_anneal": ([P, P, L, P, I, ctypes.c_longlong, I, D, ctypes.c_ulonglong, P, P], I),
         "mcg_local_solve": ([P, P, P, P, I, I, P], I),
+        "mcg_random_gauge": ([P, L, ctypes.c_ulonglong, ctypes.c_ulonglong, P], I),
         "mcg_center_project": ([P, P, P, L, P], I),
         "mcg_vortex_remove": ([P, P, P, P, L, P], I),
         "mcg_wilson_loops": ([P, L, I, I, P, P], I),
@@ -133,7 +134,10 @@ EXPORTS = ("mcg_version", "mcg_last_error", "mcg_release", "mcg_pack_links", "mc
            "mcg_gribov_search", "mcg_smear_backward_step", "mcg_functional_matrix_grad", "mcg_grad_R",
            "mcg_ascent_step", "mcg_vortex_remove", "mcg_wilson_loops",
            "mcg_wilson_loops_offaxis", "mcg_anneal", "mcg_phase_stats",
-           "mcg_halfsweep_slab", "mcg_slab_face", "mcg_bounds_violations", "mcg_probe_peaks", "mcg_local_solve")
+           "mcg_halfsweep_slab", "mcg_slab_face", "mcg_bounds_violations", "mcg_probe_peaks", "mcg_local_solve",
+           "mcg_random_gauge")
+#: seed of the random gauge copies of Params.fp32_restart_random
+RESTART_SEED = 0x4D434752
 
 
 def library() -> ctypes.CDLL:
@@ -162,12 +166,13 @@ class Params:
     fp64_df: int = 0
     fp32_restart: int = 0
     fp32_restart_domega: float = 0.0
+    fp32_restart_random: int = 0
 
     def c(self) -> mcg_params:
         return mcg_params(self.tol, self.max_sweeps, self.check_every, self.reunit_every, self.fp32_sweeps,
                           self.fp32_tol, self.fp32_window, self.fp32_overrelax,
                           int(self.fp64_solve32), int(self.fp64_df), int(self.fp32_restart),
-                          float(self.fp32_restart_domega))
+                          float(self.fp32_restart_domega), int(self.fp32_restart_random))
 
 
 def lattice(dims, nfields: int = 1, precision: int = F64) -> mcg_lattice:
@@ -406,6 +411,17 @@ def mcg_anneal(U: torch.Tensor, G: torch.Tensor, dims, T, nhit: int = 4, eps: fl
                                          _stream(stream)))
     hits = len(T) * 3 * int(nhit) * 2 * vh_of(dims)
     return dict(accepted=list(acc), acceptance=[a / hits if hits else 0.0 for a in acc])
+
+
+def mcg_random_gauge(dims, nfields: int = 1, seed: int = 0, seq: int = 0, device="cuda", stream=None) -> torch.Tensor:
+    """Haar-random SU(3) gauge transforms (FP64 library layout), drawn on
+    the device from Philox4x64-10 (see include/mcg.h); the same in each of the
+    nfields fields."""
+    G = empty_gauge(dims, nfields, F64, device)
+    _check("mcg_random_gauge", _lib.mcg_random_gauge(_ptr(G), lattice(dims, nfields, F64),
+                                                     int(seed) & ((1 << 64) - 1), int(seq) & ((1 << 64) - 1),
+                                                     _stream(stream)))
+    return G
 
 
 def mcg_local_solve(A: torch.Tensor, b: torch.Tensor, precision: int = F64, stream=None):

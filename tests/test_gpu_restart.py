@@ -86,3 +86,47 @@ def test_restart_off_changes_nothing(mcg):
     b, gb = packed(mcg, U, dims), mcg.identity_gauge(dims)
     rb = mcg.mcg_fix(b, gb, dims, params(mcg, 1.9, restart=0, domega=0.3))
     assert ra["sweeps"] == rb["sweeps"] and torch.equal(a, b) and torch.equal(ga, gb)
+
+
+def test_random_restart_is_a_fresh_run_from_the_random_copy(mcg):
+    """fp32_restart_random = 1: the k-th restart applies the transform W0 of
+    mcg_random_gauge(seed MCG_RESTART_SEED, seq k) to the links and
+    left-multiplies the transform by it; from there the phase is a fresh run
+    with the next over-relaxation, bit for bit."""
+    dims = (6, 4, 4, 6)
+    U = synth.make_field(dims, 0.5, 12)
+    p = params(mcg, 1.9, restart=30, domega=0.15)
+    p.fp32_restart_random = 1
+    Ur, Gr = packed(mcg, U, dims), mcg.identity_gauge(dims)
+    rr = mcg.mcg_fix(Ur, Gr, dims, p)
+    W0 = mcg.mcg_random_gauge(dims, seed=mcg.RESTART_SEED, seq=1)
+    Uf = packed(mcg, U, dims)
+    mcg.mcg_apply_gauge(Uf, W0, dims)
+    Gf = W0.clone()
+    rf = mcg.mcg_fix(Uf, Gf, dims, params(mcg, 1.75))
+    assert rr["converged"] and rf["converged"]
+    assert torch.equal(Ur, Uf) and torch.equal(Gr, Gf)
+    assert 30 <= rr["sweeps"][0] - rf["sweeps"][0] <= 50
+
+
+def test_random_gauge_is_haar_su3(mcg):
+    """mcg_random_gauge: every matrix in SU(3) to rounding, the same in each
+    field, reproducible, another sequence another draw; the first two moments
+    of the trace are those of the Haar measure on SU(3): E tr G = 0 and
+    E |tr G|^2 = 1 (one irreducible representation), within 5 standard
+    errors over the 2 * 8^3 * 16 sites."""
+    dims = (8, 8, 8, 16)
+    G = mcg.mcg_random_gauge(dims, nfields=2, seed=5, seq=3)
+    M = mcg.mcg_unpack_gauge(G, dims).cpu().numpy()
+    assert np.array_equal(M[0], M[1])
+    assert torch.equal(G, mcg.mcg_random_gauge(dims, nfields=2, seed=5, seq=3))
+    assert not torch.equal(G, mcg.mcg_random_gauge(dims, nfields=2, seed=5, seq=4))
+    m = M[0]
+    eye = np.eye(3)
+    assert np.abs(np.einsum("nji,njk->nik", m.conj(), m) - eye).max() < 1e-14
+    assert np.abs(np.linalg.det(m) - 1.0).max() < 1e-14
+    tr = np.einsum("nii->n", m)
+    n = len(tr)
+    assert abs(tr.mean()) < 5.0 / np.sqrt(n)
+    a2 = np.abs(tr) ** 2
+    assert abs(a2.mean() - 1.0) < 5.0 * a2.std() / np.sqrt(n)
