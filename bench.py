@@ -61,6 +61,10 @@ OMEGA = float(os.environ.get("MCG_OMEGA", "1.9"))
 RESTART = int(os.environ.get("MCG_FP32_RESTART", "10000"))
 RESTART_DOMEGA = float(os.environ.get("MCG_RESTART_DOMEGA", "0.03"))
 RESTART_RANDOM = int(os.environ.get("MCG_RESTART_RANDOM", "1"))
+# ... and once its per-chunk dV_U has stayed within [2, 20] x fp32_tol without
+# decaying for this many sweeps (the creeping approach to a lower maximum;
+# on the three 20^3 x 40 workloads only the creeping fixes meet it)
+RESTART_CREEP = int(os.environ.get("MCG_RESTART_CREEP", "3000"))
 
 
 def hbm_peak():
@@ -357,7 +361,8 @@ def run_gribov(args, mcg, dev, rank):
     nconf_tot = c
     p = mcg.Params(tol=1e-10, max_sweeps=20000, check_every=25, reunit_every=50, fp32_sweeps=20000, fp32_tol=5e-11,
                    fp32_window=25, fp32_overrelax=OMEGA, fp64_solve32=1, fp32_restart=RESTART,
-                   fp32_restart_domega=RESTART_DOMEGA, fp32_restart_random=RESTART_RANDOM)
+                   fp32_restart_domega=RESTART_DOMEGA, fp32_restart_random=RESTART_RANDOM,
+                   fp32_restart_creep=RESTART_CREEP)
     tune = mcg.autotune_schedule(Us, dims_list, p, trial_sweeps=20, chunks=(25, 50))
     print(f"gribov: autotuned {tune['block']} x {tune['check_every']}", file=sys.stderr, flush=True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -598,7 +603,8 @@ def mixed_error_block(args, mcg, U, dims, levels, mixed, dev):
                          fp32_window=mixed.fp32_window, fp32_overrelax=mixed.fp32_overrelax,
                          fp64_solve32=mixed.fp64_solve32, fp64_df=mixed.fp64_df, fp32_restart=mixed.fp32_restart,
                          fp32_restart_domega=mixed.fp32_restart_domega,
-                         fp32_restart_random=mixed.fp32_restart_random)
+                         fp32_restart_random=mixed.fp32_restart_random,
+                         fp32_restart_creep=mixed.fp32_restart_creep)
 
     def compare(F):
         """F (device, FP64) -> hand-off H in place; finishes from H compared."""
@@ -757,7 +763,7 @@ def main():
                        fp32_tol=float(os.environ.get("MCG_FP32_TOL", "5e-11")), fp32_window=25,
                        fp32_overrelax=OMEGA, fp64_solve32=1, fp64_df=int(os.environ.get("MCG_FP64_DF", "1")),
                        fp32_restart=RESTART, fp32_restart_domega=RESTART_DOMEGA,
-                       fp32_restart_random=RESTART_RANDOM)
+                       fp32_restart_random=RESTART_RANDOM, fp32_restart_creep=RESTART_CREEP)
     stream = torch.cuda.current_stream(dev)
 
     def step(params, smear_prec):
@@ -1019,7 +1025,7 @@ def main():
                 "config": config_of(args, f"batched levels, FP32 smearing, FP32 sweeps (over-relaxed, omega="
                                           f"{mixed.fp32_overrelax}, until the 25-sweep mean dV_U < "
                                           f"{mixed.fp32_tol:g}; a field still running after "
-                                          f"{mixed.fp32_restart} sweeps restarts from "
+                                          f"{mixed.fp32_restart} sweeps, or creeping for {mixed.fp32_restart_creep}, restarts from "
                                           + ("a random gauge copy of " if mixed.fp32_restart_random else "")
                                           + f"its input with omega -+ k*"
                                           f"{mixed.fp32_restart_domega:g}) then FP64-class plain relaxation ("

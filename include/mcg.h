@@ -125,6 +125,12 @@ typedef struct {
                        /* FP64 links and left-multiplies its transform G (the */
                        /* output stays U_out = G_out U_in).  0: from the same */
                        /* links.                                               */
+    int fp32_restart_creep; /* FP32 phase: also restart (as above) a field that */
+                       /* creeps: over the last fp32_restart_creep sweeps the  */
+                       /* mean dV_U per sweep of every check_every chunk stayed */
+                       /* within [2, 20] x fp32_tol and the last quarter of    */
+                       /* those chunks averages more than half the first     */
+                       /* quarter (no decay).  0 = off.                        */
 } mcg_params;
 
 /* Seed of the random gauge copies of mcg_params.fp32_restart_random. */

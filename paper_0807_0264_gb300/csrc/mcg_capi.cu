@@ -245,6 +245,7 @@ static int check_params(const mcg_params* p) {
         return fail(MCG_BAD_ARG, "fp32_restart must be >= 0 and fp32_restart_domega in [0, 2)");
     if (p->fp32_restart_random != 0 && p->fp32_restart_random != 1)
         return fail(MCG_BAD_ARG, "fp32_restart_random must be 0 or 1");
+    if (p->fp32_restart_creep < 0) return fail(MCG_BAD_ARG, "fp32_restart_creep must be >= 0");
     return 0;
 }
 
@@ -323,7 +324,11 @@ static int fix_fields(const std::vector<FieldSpec>& fs, int prec, const mcg_para
         rs.domega = prm->fp32_restart_domega;
         rs.count = nrs.data();
         void* W0 = nullptr;
-        if (prm->fp32_restart > 0 && prm->fp32_restart_random) {
+        rs.creep = prm->fp32_restart_creep;
+        rs.creep_lo = 2.0 * prm->fp32_tol;
+        rs.creep_hi = 20.0 * prm->fp32_tol;
+        const bool any_restart = prm->fp32_restart > 0 || prm->fp32_restart_creep > 0;
+        if (any_restart && prm->fp32_restart_random) {
             size_t ge_max = 0;
             for (const auto& f : fs) ge_max = std::max(ge_max, gauge_elems(f.g));
             W0 = scratch_device("fix.restart.W0", 16 * ge_max, &rc);
@@ -344,7 +349,7 @@ static int fix_fields(const std::vector<FieldSpec>& fs, int prec, const mcg_para
         };
         rc = run_fix_phase<float>(fds, d_state, h_state, d_hist, hist_len, prm->fp32_tol, prm->fp32_window,
                                   prm->fp32_overrelax, 0, cap, prm->check_every, true, st, false,
-                                  prm->fp32_restart > 0 ? &rs : nullptr);
+                                  any_restart ? &rs : nullptr);
         if (rc) return rc;
         if (restarts_out)
             for (int f = 0; f < nf; ++f) restarts_out[f] = nrs[f];

@@ -123,12 +123,31 @@ int launch_gauge_left_mul(void* G, const void* W, const Geom& g, int nfields, cu
 // omega + d, omega - 2d, omega + 2d, ... (d = domega); no restart once
 // omega_k leaves (0, 2).  Its sweeps keep counting toward the phase's cap.
 // count (nf entries, may be null): restarts per field.
+// A field also restarts when it creeps: over the last `creep` sweeps (0:
+// off) the mean dV_U per sweep of every check_every chunk stayed within
+// [creep_lo, creep_hi] and the mean of the last quarter of those chunks is
+// more than half the mean of the first quarter (no decay); see creeping().
 struct PhaseRestart {
     int after = 0;
     double domega = 0.0;
     std::function<int(int, int, cudaStream_t)> reset;
     int* count = nullptr;
+    int creep = 0;
+    double creep_lo = 0.0, creep_hi = 0.0;
 };
+
+// The creep test on the per-chunk dV_U of the last m chunks, oldest first.
+inline bool creeping(const double* dv, int m, double lo, double hi) {
+    if (m < 4) return false;
+    const int q = m / 4;
+    double first = 0.0, last = 0.0;
+    for (int i = 0; i < m; ++i) {
+        if (!(dv[i] >= lo && dv[i] <= hi)) return false;
+        if (i < q) first += dv[i];
+        if (i >= m - q) last += dv[i];
+    }
+    return last > 0.5 * first;
+}
 
 // Over-relaxation of a field's k-th restart (k = 0: the phase's own), or a
 // value outside (0, 2) when there is none.

@@ -819,7 +819,7 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
         fd.omega = omega;
         total += fd.nblk;
     }
-    const bool restarts = restart && restart->after > 0 && std::is_same<T, float>::value;
+    const bool restarts = restart && (restart->after > 0 || restart->creep > 0) && std::is_same<T, float>::value;
     int rc = 0;
     FieldDesc* d_desc = (FieldDesc*)scratch_device("fix.desc", sizeof(FieldDesc) * nf, &rc);
     if (rc) return rc;
@@ -984,6 +984,11 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
     // over-relaxation written to its descriptors.  A field's (re)start is its
     // state's phase_start.
     std::vector<int> nrestart(nf, 0), valid_from(nf, 0);
+    // the creep test: per field, the per-chunk dV_U since its (re)start (a
+    // ring of the last m chunks) and the R and sweep count of its last read
+    const int creep_m = (restarts && restart->creep > 0) ? std::max(4, restart->creep / chunk) : 0;
+    std::vector<double> creep_dv((size_t)nf * std::max(creep_m, 1), 0.0), last_R(nf, 0.0);
+    std::vector<int> creep_n(nf, 0), last_sweep(nf, -1);
     double* h_omega = nullptr;
     if (restarts) {
         h_omega = (double*)scratch_host("fix.restart.omega", sizeof(double) * nf, &rc);
@@ -1047,7 +1052,24 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
                 all = false;  // a reset is pending behind the chunk read here
                 continue;
             }
-            if (restarts && hs[f].done == 0 && hs[f].sweep - hs[f].phase_start >= restart->after) {
+            bool creeps = false;
+            if (creep_m > 0 && hs[f].done == 0) {
+                if (last_sweep[f] >= 0 && hs[f].sweep > last_sweep[f]) {
+                    double* ring = creep_dv.data() + (size_t)f * creep_m;
+                    ring[creep_n[f] % creep_m] =
+                        (hs[f].R_last - last_R[f]) * fields[f].norm / (hs[f].sweep - last_sweep[f]);
+                    ++creep_n[f];
+                    if (creep_n[f] >= creep_m) {
+                        std::vector<double> w(creep_m);
+                        for (int i = 0; i < creep_m; ++i) w[i] = ring[(creep_n[f] + i) % creep_m];
+                        creeps = creeping(w.data(), creep_m, restart->creep_lo, restart->creep_hi);
+                    }
+                }
+                last_R[f] = hs[f].R_last;
+                last_sweep[f] = hs[f].sweep;
+            }
+            if (restarts && hs[f].done == 0 &&
+                ((restart->after > 0 && hs[f].sweep - hs[f].phase_start >= restart->after) || creeps)) {
                 const double om = restart_omega(omega, restart->domega, nrestart[f] + 1);
                 if (om > 0.0 && om < 2.0 && in_flight == c + 1) {
                     if ((rc = restart_field(f, om))) {
@@ -1056,6 +1078,8 @@ int run_fix_phase(const std::vector<FieldDesc>& fields_in, FieldState* d_state, 
                     }
                     ++nrestart[f];
                     valid_from[f] = c + 2;
+                    creep_n[f] = 0;
+                    last_sweep[f] = -1;
                     all = false;
                     continue;
                 }

@@ -130,3 +130,24 @@ def test_random_gauge_is_haar_su3(mcg):
     assert abs(tr.mean()) < 5.0 / np.sqrt(n)
     a2 = np.abs(tr) ** 2
     assert abs(a2.mean() - 1.0) < 5.0 * a2.std() / np.sqrt(n)
+
+
+def test_creep_detector_restarts_only_the_creeping_fix(mcg):
+    """The benchmark workload (20^3 x 40, stout rho = 0.1, n = 0, 4, 10, 20,
+    omega 1.9): the preconditioned fix of level 20 creeps toward the lower
+    maximum (per-chunk dV_U ~2e-10, flat for 20 000 sweeps) while every other
+    fix's dV_U decays to the FP32 drift floor (~3e-11).  With the creep test
+    alone (3 000 sweeps, no sweep-count restart) only that fix restarts, early,
+    and every level converges."""
+    dims = (20, 20, 20, 40)
+    U = mcg.mcg_pack_links(torch.from_numpy(synth.make_field(dims, synth.W_PLAQ_06, 0)).unsqueeze(0).cuda(), dims)
+    p = mcg.Params(tol=1e-10, max_sweeps=30000, check_every=25, reunit_every=50, fp32_sweeps=30000, fp32_tol=5e-11,
+                   fp32_window=25, fp32_overrelax=1.9, fp64_solve32=1, fp64_df=1, fp32_restart=0,
+                   fp32_restart_domega=0.03, fp32_restart_random=1, fp32_restart_creep=3000)
+    res = mcg.mcg_precondition_levels(U, dims, [0, 4, 10, 20], p, rho=0.1, eps=1.0, smear_precision=mcg.F32)[3]
+    print([(r["sweeps_smeared"], r["sweeps_fixed"], r["fp32_restarts"], r["status"]) for r in res])
+    assert [r["status"] for r in res] == [0, 0, 0, 0]
+    assert [r["fp32_restarts"] for r in res[:3]] == [0, 0, 0]
+    assert res[3]["fp32_restarts"] >= 1
+    # the creeping fix gave up after ~3 400 sweeps, not after the 30 000 cap
+    assert res[3]["sweeps_fixed"] < 15000
