@@ -73,7 +73,23 @@ def main():
                                                                       fp64_solve32=1, fp64_df=1),
                                          rho=0.1, eps=1.0, smear_precision=mcg.F32)[3]
         r["levels"] = [[x["V_smeared"], x["V_fixed"], x["sweeps_fixed"], x["vortices"]] for x in lv]
+        # restarts of the FP32 phase from random gauge copies, and the random transforms themselves
+        U, G = U0.clone(), mcg.identity_gauge(dims, 1, mcg.F64, dev)
+        rr = mcg.mcg_fix(U, G, dims, mcg.Params(tol=1e-10, max_sweeps=3000, check_every=10, fp32_sweeps=3000,
+                                                fp32_tol=5e-11, fp32_window=25, fp32_overrelax=1.9, fp64_df=1,
+                                                fp32_restart=30, fp32_restart_domega=0.15, fp32_restart_random=1,
+                                                fp32_restart_creep=200))
+        r["R_restarted"] = rr["R"][0]
+        r["random_gauge"] = float(mcg.mcg_random_gauge(dims, seed=3, seq=1).abs().sum())
         out[key] = r
+    # the local solve entry point, both precisions, on a few seeded problems
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((70, 4, 4))
+    A = torch.from_numpy(A + A.transpose(0, 2, 1)).to(dev)
+    b = torch.from_numpy(rng.standard_normal((70, 4))).to(dev)
+    for name, prec in (("local_f64", mcg.F64), ("local_f32", mcg.F32)):
+        a, fb = mcg.mcg_local_solve(A, b, prec)
+        out[name] = [float(a.abs().sum()), int(fb.sum())]
     torch.cuda.synchronize()
     print(json.dumps({"violations": mcg.mcg_bounds_violations(), "results": out}), flush=True)
 
