@@ -568,7 +568,23 @@ def profile_kernels(mcg, U, dims, dev):
     mcg.mcg_grad_R(Uf, dims)
     Gout = torch_randn_like_links(U)
     mcg.mcg_smear_backward_step(U, Gout, dims, 0.1, 1.0)
+    # a restart of the FP32 phase from a random gauge copy (random transform,
+    # applied to the links, left-multiplied into the transform), and the local
+    # solve on its own for one half-sweep's worth of problems, both precisions
+    Ur, Gr = U.clone(), Gi.clone()
+    mcg.mcg_fix(Ur, Gr, dims, mcg.Params(tol=-1e300, max_sweeps=6, check_every=2, fp32_sweeps=6, fp32_tol=-1e300,
+                                         fp32_window=1, fp32_overrelax=OMEGA, fp32_restart=2,
+                                         fp32_restart_domega=0.03, fp32_restart_random=1))
+    import numpy as np
     import torch
+
+    rng = np.random.default_rng(0)
+    n = int(np.prod(dims)) // 2
+    A = rng.standard_normal((n, 4, 4))
+    A = torch.from_numpy(A + A.transpose(0, 2, 1)).to(dev)
+    b = torch.from_numpy(rng.standard_normal((n, 4))).to(dev)
+    for prec in (mcg.F64, mcg.F32):
+        mcg.mcg_local_solve(A, b, prec)
 
     torch.cuda.synchronize(dev)
     print(json.dumps({"profile_kernels": True, "dims": dims, "launches": mcg.mcg_kernel_launches()}), flush=True)
