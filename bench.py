@@ -65,6 +65,9 @@ RESTART_RANDOM = int(os.environ.get("MCG_RESTART_RANDOM", "1"))
 # decaying for this many sweeps (the creeping approach to a lower maximum;
 # on the three 20^3 x 40 workloads only the creeping fixes meet it)
 RESTART_CREEP = int(os.environ.get("MCG_RESTART_CREEP", "3000"))
+# plain FP32 sweeps after the over-relaxed ones, before the hand-off (they
+# remove the over-relaxation's oscillating residue at FP32 cost)
+PLAIN_FINISH = int(os.environ.get("MCG_FP32_PLAIN_FINISH", "1"))
 
 
 def hbm_peak():
@@ -362,7 +365,8 @@ def run_gribov(args, mcg, dev, rank):
     p = mcg.Params(tol=1e-10, max_sweeps=20000, check_every=25, reunit_every=50, fp32_sweeps=20000, fp32_tol=5e-11,
                    fp32_window=25, fp32_overrelax=OMEGA, fp64_solve32=1, fp32_restart=RESTART,
                    fp32_restart_domega=RESTART_DOMEGA, fp32_restart_random=RESTART_RANDOM,
-                   fp32_restart_creep=RESTART_CREEP)
+                   fp32_restart_creep=RESTART_CREEP,
+                   fp32_plain_finish=PLAIN_FINISH)
     tune = mcg.autotune_schedule(Us, dims_list, p, trial_sweeps=20, chunks=(25, 50))
     print(f"gribov: autotuned {tune['block']} x {tune['check_every']}", file=sys.stderr, flush=True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -620,7 +624,8 @@ def mixed_error_block(args, mcg, U, dims, levels, mixed, dev):
                          fp64_solve32=mixed.fp64_solve32, fp64_df=mixed.fp64_df, fp32_restart=mixed.fp32_restart,
                          fp32_restart_domega=mixed.fp32_restart_domega,
                          fp32_restart_random=mixed.fp32_restart_random,
-                         fp32_restart_creep=mixed.fp32_restart_creep)
+                         fp32_restart_creep=mixed.fp32_restart_creep,
+                         fp32_plain_finish=mixed.fp32_plain_finish)
 
     def compare(F):
         """F (device, FP64) -> hand-off H in place; finishes from H compared."""
@@ -779,7 +784,8 @@ def main():
                        fp32_tol=float(os.environ.get("MCG_FP32_TOL", "5e-11")), fp32_window=25,
                        fp32_overrelax=OMEGA, fp64_solve32=1, fp64_df=int(os.environ.get("MCG_FP64_DF", "1")),
                        fp32_restart=RESTART, fp32_restart_domega=RESTART_DOMEGA,
-                       fp32_restart_random=RESTART_RANDOM, fp32_restart_creep=RESTART_CREEP)
+                       fp32_restart_random=RESTART_RANDOM, fp32_restart_creep=RESTART_CREEP,
+                       fp32_plain_finish=PLAIN_FINISH)
     stream = torch.cuda.current_stream(dev)
 
     def step(params, smear_prec):
@@ -1041,10 +1047,14 @@ def main():
                 "config": config_of(args, f"batched levels, FP32 smearing, FP32 sweeps (over-relaxed, omega="
                                           f"{mixed.fp32_overrelax}, until the 25-sweep mean dV_U < "
                                           f"{mixed.fp32_tol:g}; a field still running after "
-                                          f"{mixed.fp32_restart} sweeps, or creeping for {mixed.fp32_restart_creep}, restarts from "
+                                          f"{mixed.fp32_restart} sweeps, or creeping for "
+                                          f"{mixed.fp32_restart_creep}, restarts from "
                                           + ("a random gauge copy of " if mixed.fp32_restart_random else "")
                                           + f"its input with omega -+ k*"
-                                          f"{mixed.fp32_restart_domega:g}) then FP64-class plain relaxation ("
+                                          f"{mixed.fp32_restart_domega:g}"
+                                          + ("; then plain FP32 sweeps to the same criterion" if mixed.fp32_plain_finish
+                                             else "")
+                                          + ") then FP64-class plain relaxation ("
                                           + ("double-float moves, local 4x4 solve in FP32, transform applied in "
                                              "FP64" if mixed.fp64_df else
                                              "local 4x4 solve in FP32, G normalised and applied in FP64")

@@ -131,6 +131,12 @@ typedef struct {
                        /* within [2, 20] x fp32_tol and the last quarter of    */
                        /* those chunks averages more than half the first     */
                        /* quarter (no decay).  0 = off.                        */
+    int fp32_plain_finish; /* 1: after the over-relaxed FP32 phase, plain    */
+                       /* FP32 sweeps (omega = 1) until the same fp32_tol      */
+                       /* criterion, before the hand-off: over-relaxation near */
+                       /* a maximum leaves an oscillating residue that the     */
+                       /* plain relaxation removes, cheaper in FP32 than in    */
+                       /* the FP64-class phase.  0 = off.                      */
 } mcg_params;
 
 /* Seed of the random gauge copies of mcg_params.fp32_restart_random. */

@@ -246,6 +246,8 @@ static int check_params(const mcg_params* p) {
     if (p->fp32_restart_random != 0 && p->fp32_restart_random != 1)
         return fail(MCG_BAD_ARG, "fp32_restart_random must be 0 or 1");
     if (p->fp32_restart_creep < 0) return fail(MCG_BAD_ARG, "fp32_restart_creep must be >= 0");
+    if (p->fp32_plain_finish != 0 && p->fp32_plain_finish != 1)
+        return fail(MCG_BAD_ARG, "fp32_plain_finish must be 0 or 1");
     return 0;
 }
 
@@ -353,6 +355,12 @@ static int fix_fields(const std::vector<FieldSpec>& fs, int prec, const mcg_para
         if (rc) return rc;
         if (restarts_out)
             for (int f = 0; f < nf; ++f) restarts_out[f] = nrs[f];
+        if (prm->fp32_plain_finish && prm->fp32_overrelax != 1.0) {
+            // plain FP32 sweeps from where the over-relaxed ones stopped
+            rc = run_fix_phase<float>(fds, d_state, h_state, d_hist, hist_len, prm->fp32_tol, prm->fp32_window, 1.0,
+                                      0, cap, prm->check_every, false, st);
+            if (rc) return rc;
+        }
         for (int f = 0; f < nf; ++f) s32[f] = h_state[f].sweep;
         // hand-off: FP64 re-unitarised transform applied to the FP64 links
         for (int f = 0; f < nf; ++f)

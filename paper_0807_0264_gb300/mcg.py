@@ -45,7 +45,7 @@ class mcg_params(ctypes.Structure):
                 ("fp32_window", ctypes.c_int), ("fp32_overrelax", ctypes.c_double),
                 ("fp64_solve32", ctypes.c_int), ("fp64_df", ctypes.c_int), ("fp32_restart", ctypes.c_int),
                 ("fp32_restart_domega", ctypes.c_double), ("fp32_restart_random", ctypes.c_int),
-                ("fp32_restart_creep", ctypes.c_int)]
+                ("fp32_restart_creep", ctypes.c_int), ("fp32_plain_finish", ctypes.c_int)]
 
 
 class mcg_field(ctypes.Structure):
@@ -169,13 +169,14 @@ class Params:
     fp32_restart_domega: float = 0.0
     fp32_restart_random: int = 0
     fp32_restart_creep: int = 0
+    fp32_plain_finish: int = 0
 
     def c(self) -> mcg_params:
         return mcg_params(self.tol, self.max_sweeps, self.check_every, self.reunit_every, self.fp32_sweeps,
                           self.fp32_tol, self.fp32_window, self.fp32_overrelax,
                           int(self.fp64_solve32), int(self.fp64_df), int(self.fp32_restart),
                           float(self.fp32_restart_domega), int(self.fp32_restart_random),
-                          int(self.fp32_restart_creep))
+                          int(self.fp32_restart_creep), int(self.fp32_plain_finish))
 
 
 def lattice(dims, nfields: int = 1, precision: int = F64) -> mcg_lattice:

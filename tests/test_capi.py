@@ -215,6 +215,20 @@ def test_slab_face_validation_without_gpu(mcg):
     code(lib.mcg_slab_face(U, buf, ctypes.byref(mcg.lattice((4, 3, 4, 6))), 0, 0, 0, None), 2, "")
 
 
+def test_restart_and_finish_parameters_are_validated_without_gpu(mcg):
+    lib = mcg.library()
+    one, two = ctypes.c_void_p(1 << 20), ctypes.c_void_p(1 << 40)
+    good = mcg.lattice((4, 4, 4, 6))
+    for field, value, why in (("fp32_restart", -1, "fp32_restart"), ("fp32_restart_domega", -0.1, "domega"),
+                              ("fp32_restart_domega", 2.0, "domega"), ("fp32_restart_random", 2, "random"),
+                              ("fp32_restart_creep", -5, "creep"), ("fp32_plain_finish", 3, "plain_finish")):
+        p = mcg.Params(fp32_sweeps=10)
+        setattr(p, field, value)
+        cp = p.c()
+        assert lib.mcg_fix(one, two, ctypes.byref(good), ctypes.byref(cp), None, None, None, None) == 3
+        assert why.encode() in lib.mcg_last_error(), lib.mcg_last_error()
+
+
 def test_local_solve_validation_without_gpu(mcg):
     """The batched local solve checks its count, precision and pointers on the
     host; n = 0 is a no-op that touches no device memory."""

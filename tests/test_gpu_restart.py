@@ -151,3 +151,31 @@ def test_creep_detector_restarts_only_the_creeping_fix(mcg):
     assert res[3]["fp32_restarts"] >= 1
     # the creeping fix gave up after ~3 400 sweeps, not after the 30 000 cap
     assert res[3]["sweeps_fixed"] < 15000
+
+
+def test_plain_fp32_finish_converges_by_the_oracle_criterion(mcg):
+    """fp32_plain_finish = 1: plain FP32 sweeps follow the over-relaxed ones
+    before the hand-off; the fix still ends on the paper's criterion (one more
+    exact FP64 sweep of the oracle raises V_U by less than 1e-10) and on the
+    input's gauge orbit.  With omega = 1 the flag changes nothing."""
+    import oracle
+
+    dims = (8, 8, 8, 8)
+    U = synth.make_field(dims, synth.W_PLAQ_06, 1)
+    p = params(mcg, 1.9)
+    p.fp32_plain_finish = 1
+    Ud, Gd = packed(mcg, U, dims), mcg.identity_gauge(dims)
+    res = mcg.mcg_fix(Ud, Gd, dims, p)
+    assert res["converged"]
+    Uf = mcg.mcg_unpack_links(Ud, dims)[0].cpu().numpy()
+    Gf = mcg.mcg_unpack_gauge(Gd, dims)[0].cpu().numpy()
+    assert np.abs(oracle.apply_gauge(dims, U, Gf) - Uf).max() < 1e-12
+    r = oracle.fix(dims, Uf, Gf, tol=-1e300, max_sweeps=1, reunit_every=0)
+    assert (r["R_hist"][1] - r["R_hist"][0]) / (36 * 4096) < 1e-10
+    a, ga = packed(mcg, U, dims), mcg.identity_gauge(dims)
+    b, gb = packed(mcg, U, dims), mcg.identity_gauge(dims)
+    q = params(mcg, 1.0)
+    ra = mcg.mcg_fix(a, ga, dims, q)
+    q.fp32_plain_finish = 1
+    rb = mcg.mcg_fix(b, gb, dims, q)
+    assert ra["sweeps"] == rb["sweeps"] and torch.equal(a, b) and torch.equal(ga, gb)
