@@ -106,7 +106,8 @@ typedef struct {
                        /* in FP64 and applied to the FP64 links at the end, so */
                        /* the result is exactly on its gauge orbit.  GB300     */
                        /* runs FP64 at ~1/60 of its FP32 rate.  0 = FP64.      */
-    int fp32_restart;  /* FP32 phase: a field that has run this many sweeps   */
+    int fp32_restart;  /* FP32 phase (MCG_F64 fields, fp32_sweeps > 0): a    */
+                       /* field that has run this many sweeps                  */
                        /* since its last (re)start without reaching fp32_tol  */
                        /* restarts the phase from the call's input links and  */
                        /* the identity transform with the next              */
