@@ -605,7 +605,7 @@ def torch_randn_like_links(U):
 def mixed_error_block(args, mcg, U, dims, levels, mixed, dev):
     """Error of the mixed schedule against the oracle, per level, on the
     preconditioned fix (the one that yields the level's fixed field): the
-    level's preconditioned field (the smeared field, FP64 smearing, fixed with
+    level's preconditioned field (the smeared field, FP32 smearing as in the step, fixed with
     the mixed schedule; its transform applied to the input) runs the mixed
     schedule up to its hand-off and first FP64 sweep; from that same field
     H the GPU's FP64 finish (the bench's, local solve in FP32) and the GPU's
@@ -655,16 +655,22 @@ def mixed_error_block(args, mcg, U, dims, levels, mixed, dev):
             r["vortices_equal"] = r["vortices"] == no
         return row, Gh
 
+    def smeared(n):
+        """The step's smeared field of level n: FP32 smearing, back to FP64,
+        re-unitarised (as mcg_precondition_levels does it)."""
+        S = mcg.mcg_convert(mcg.mcg_smear(mcg.mcg_convert(U, mcg.F32), dims, args.rho, args.eps, n), mcg.F64)
+        mcg.mcg_reunitarise(S, 0, dims)
+        return S
+
     out = []
     for n in levels:
         t0 = time.perf_counter()
         row = {"level": n}
         Up = U.clone()
         if n > 0:
-            S = mcg.mcg_smear(U, dims, args.rho, args.eps, n)
-            row["smeared_fix"], _ = compare(S)
+            row["smeared_fix"], _ = compare(smeared(n))
             # the preconditioning transform: the mixed fix of the smeared field
-            S = mcg.mcg_smear(U, dims, args.rho, args.eps, n)
+            S = smeared(n)
             G1 = mcg.identity_gauge(dims, 1, mcg.F64, dev)
             mcg.mcg_fix(S, G1, dims, mixed)
             mcg.mcg_reunitarise(G1, 1, dims)
@@ -677,7 +683,7 @@ def mixed_error_block(args, mcg, U, dims, levels, mixed, dev):
     return {"method": "per level and per fix (the smeared field's, then the preconditioned field's): the mixed "
                       "schedule runs to its hand-off and first FP64 sweep (field H); from H the GPU's FP64 finish "
                       "(the bench's: double-float moves, local solve in FP32) and the GPU's exact FP64 finish run to dV_U<1e-10, and "
-                      "so does the oracle's plain FP64 relaxation on the host cores; FP64 smearing",
+                      "so does the oracle's plain FP64 relaxation on the host cores; the step's FP32 smearing",
             "levels": out}
 
 
