@@ -282,10 +282,16 @@ static void jacobi4(const double* Ain, double* V, double* al) {
  * (A symmetric 4x4 row-major, b in R^4).  The global maximiser satisfies
  * (mu I - A) a = b with mu >= alpha_max (the trust-region optimality
  * condition).  Easy case: mu is the root right of alpha_max of
- * ||a(mu)|| = 1, a(mu) = sum_i beta_i / (mu - alpha_i) v_i, beta_i = v_i . b,
- * found by Newton on 1/||a(mu)|| - 1 from the left end of the bracket
- * [alpha_max + |beta_top|, alpha_max + ||b||] (beta_top: the component of b
- * in the top eigenspace) with bisection as a safeguard.
+ * ||a(mu)|| = 1, a(mu) = sum_i beta_i / (mu - alpha_i) v_i, beta_i = v_i . b.
+ * It is solved for the offset d = mu - alpha_max, with the gaps
+ * alpha_max - alpha_i formed once, so that d keeps full relative precision
+ * when it is tiny (beta_top, the component of b in the top eigenspace, near
+ * zero): Newton on 1/||a|| - 1 (Moré and Sorensen), which is concave and
+ * increasing in d and so climbs monotonically to the root from any point
+ * with ||a|| >= 1, inside the bracket [|beta_top|, ||b||] with bisection as a
+ * safeguard.  When the weights off the top eigenspace alone give ||a|| >= 1
+ * at d = 0 the root lies beyond the root of their equation, which is solved
+ * first the same way and starts the full iteration.
  * Hard case (b has no component along the top eigenspace and the rest of the
  * solution has norm < 1): mu = alpha_max and a = partial + t v_max with t > 0
  * after fixing the sign of v_max so that its largest-magnitude component is
@@ -345,37 +351,60 @@ int orc_trs_solve(const double* A, const double* b, double* a) {
         }
     }
 
-    /* bracket: ||a(mu)|| >= btop / (mu - alpha_max), so mu = alpha_max + btop
-     * lies left of the root; ||a(mu)|| <= ||b|| / (mu - alpha_max), so
-     * mu = alpha_max + ||b|| lies right of it */
-    double lo = amax + btop, hi = amax + bn;
-    double mu = lo;
+    /* gaps to the largest eigenvalue (0 on the top eigenspace) and the norm
+     * of the solution without the top weights at d = 0 */
+    double gap[4], rest2 = 0;
+    for (int i = 0; i < 4; ++i) {
+        gap[i] = top[i] ? 0.0 : amax - al[i];
+        if (!top[i]) rest2 += beta[i] * beta[i] / (gap[i] * gap[i]);
+    }
+    /* bracket: ||a|| >= btop / d, so d = btop lies left of the root;
+     * ||a|| <= ||b|| / d, so d = ||b|| lies right of it */
+    double lo = btop, hi = bn, d = btop;
+    if (rest2 >= 1.0) {
+        double dr = 0;
+        for (int it = 0; it < 200; ++it) {
+            double s2 = 0, s3 = 0;
+            for (int i = 0; i < 4; ++i) {
+                if (top[i]) continue;
+                double e = dr + gap[i];
+                double q = beta[i] * beta[i] / (e * e);
+                s2 += q;
+                s3 += q / e;
+            }
+            if (!(s3 > 0)) break;
+            double step = (sqrt(s2) - 1.0) * s2 / s3;
+            dr += step;
+            if (!(step > 1e-15 * dr)) break;
+        }
+        if (dr > d) d = fmin(dr, hi);
+    }
     for (int it = 0; it < 200; ++it) {
         double s2 = 0, s3 = 0;
         for (int i = 0; i < 4; ++i) {
-            if (beta[i] == 0.0) continue; /* a zero weight contributes nothing, also at mu = al[i] */
-            double d = mu - al[i];
-            double q = beta[i] * beta[i] / (d * d);
+            if (beta[i] == 0.0) continue; /* a zero weight contributes nothing, also where d + gap is 0 */
+            double e = d + gap[i];
+            double q = beta[i] * beta[i] / (e * e);
             s2 += q;
-            s3 += q / d;
+            s3 += q / e;
         }
         double n = sqrt(s2);
-        if (n >= 1.0) lo = fmax(lo, mu);
-        else hi = fmin(hi, mu);
-        double next = mu + (n - 1.0) * s2 / s3; /* Newton on 1/n - 1 */
+        if (n >= 1.0) lo = fmax(lo, d);
+        else hi = fmin(hi, d);
+        double next = d + (n - 1.0) * s2 / s3; /* Newton on 1/n - 1 */
         if (!(next > lo && next < hi)) next = 0.5 * (lo + hi);
-        if (next == mu || fabs(next - mu) <= 1e-16 * fabs(mu)) {
-            mu = next;
+        if (next == d || fabs(next - d) <= 1e-15 * d) {
+            d = next;
             break;
         }
-        mu = next;
-        if (hi - lo <= 4e-16 * fabs(mu)) break;
+        d = next;
+        if (hi - lo <= 4e-16 * d) break;
     }
     double an2 = 0;
     for (int k = 0; k < 4; ++k) {
         double s = 0;
         for (int i = 0; i < 4; ++i)
-            if (beta[i] != 0.0) s += V[4 * k + i] * beta[i] / (mu - al[i]);
+            if (beta[i] != 0.0) s += V[4 * k + i] * beta[i] / (d + gap[i]);
         a[k] = s;
         an2 += s * s;
     }

@@ -143,3 +143,38 @@ def test_zero_weight_on_the_top_eigenvector():
     X /= np.linalg.norm(X, axis=1, keepdims=True)
     F = np.einsum("ni,ij,nj->n", X, A, X) + 2 * X @ b
     assert a @ A @ a + 2 * b @ a >= F.max() - 1e-12
+
+
+def near_hard_problem(rng, inside):
+    """A = V diag(lam) V^T, b = V beta with a small weight on the top
+    eigenvector (|beta_top| = 10^U(-12, -2)) and the other weights scaled so
+    that p = sum_i beta_i / (lam_top - lam_i) v_i has |p| in (0.3, 0.95)
+    (inside: the multiplier sits just above lam_top) or in (1.05, 2)."""
+    q, r = np.linalg.qr(rng.standard_normal((4, 4)))
+    V = q * np.sign(np.diag(r))
+    lam = np.sort(rng.uniform(0.0, 12.0, 4))
+    beta = np.zeros(4)
+    beta[:3] = rng.standard_normal(3)
+    target = rng.uniform(0.3, 0.95) if inside else rng.uniform(1.05, 2.0)
+    beta[:3] *= target / np.linalg.norm(beta[:3] / (lam[3] - lam[:3]))
+    beta[3] = rng.choice([-1.0, 1.0]) * 10.0 ** rng.uniform(-12.0, -2.0)
+    A = (V * lam) @ V.T
+    return 0.5 * (A + A.T), V @ beta
+
+
+@pytest.mark.parametrize("inside", [True, False])
+def test_global_optimality_near_the_hard_case(inside):
+    """The same conditions on problems near the hard case, where the
+    multiplier lies within |beta_top| / sqrt(1 - |p|^2) of lambda_max (inside)
+    or the top weight is negligible (outside): a secular iteration that stops
+    on a step small against mu itself, rather than against mu - lambda_max,
+    fails the residual here."""
+    rng = np.random.default_rng(23)
+    for _ in range(2000):
+        A, b = near_hard_problem(rng, inside)
+        a, _ = oracle.trs_solve(A, b)
+        mu = a @ A @ a + a @ b
+        scale = max(np.abs(A).max(), np.abs(b).max())
+        assert abs(np.linalg.norm(a) - 1) < 1e-14
+        assert np.linalg.norm((mu * np.eye(4) - A) @ a - b) < 1e-10 * scale
+        assert mu >= np.linalg.eigvalsh(A)[-1] - 1e-12 * scale
